@@ -1,0 +1,43 @@
+/*
+ * kpo_internal.h -- oracle planner state (TEST INFRASTRUCTURE ONLY, see
+ * kpo.h).  The tree is stored node-major in double precision.
+ */
+#ifndef KPO_INTERNAL_H
+#define KPO_INTERNAL_H
+
+#include "kpo.h"
+
+struct kpo {
+  kpo_config cfg;
+  int d, N;                /* state and control dimension                 */
+  int R;                   /* regions                                     */
+  int n_sub_per;           /* sub-regions per region (n')                 */
+  int n_sub;               /* R * n'                                      */
+  double vol;              /* workspace volume of one region (Eq. 3)      */
+  double *boxes;           /* [nb][6]: lo xyz, hi xyz                     */
+  int nb;
+
+  /* tree T, capacity t_e */
+  int n;                   /* |T|                                         */
+  double *x;               /* [t_e][d]                                    */
+  int *parent;
+  double *u;               /* [t_e][N] control of the edge into the node  */
+  int *steps;              /* integration steps of that edge              */
+  int *region, *sub;
+  unsigned char *in_ve;    /* 1: V_E, 0: V_O                              */
+
+  /* decomposition R */
+  uint64_t *n_valid, *n_invalid;
+  uint32_t *cov;
+  unsigned char *avail;
+  unsigned char *visited;  /* [R * n']                                    */
+  double *score, *p_accept;
+  uint64_t *thr;           /* Bernoulli threshold: accept iff word < thr  */
+  double score_sum;
+
+  int iteration;
+  int status;
+  int goal_node;
+};
+
+#endif

@@ -1,0 +1,332 @@
+/*
+ * model.c -- dynamics, validity check and region binning (oracle side).
+ *
+ * TEST INFRASTRUCTURE ONLY (see kpo.h).  Everything is double precision and
+ * written for clarity, not speed.
+ *
+ * Dynamics (Sec. II, Eq. 1-2; the paper names the three systems in Sec. VI
+ * without giving their equations, so the equations below are the textbook
+ * forms the paper cites):
+ *   double integrator (6D):  p' = v, v' = u                   (explicit Euler)
+ *   Dubins airplane (6D, Chitsaz & LaValle 2007):
+ *        x' = v cos(psi) cos(theta), y' = v sin(psi) cos(theta),
+ *        z' = v sin(theta), psi' = u1, theta' = u2, v' = u3  (classic RK4)
+ *   quadrotor (12D, Newton-Euler, plus configuration):
+ *        p' = v,  eta' = W(phi, theta) omega,
+ *        m v' = R(phi, theta, psi) [0 0 sum T]^T - m g e3,
+ *        I omega' = tau - omega x (I omega),
+ *        tau = [l (T2 - T4), l (T3 - T1), c (T1 - T2 + T3 - T4)]   (RK4)
+ *
+ * Validity (Sec. II valid set; Algorithm 2, validity of the segment): after
+ * every integrator step the state must lie in the state box, and the
+ * axis-aligned box spanned by the positions before and after the step must
+ * not meet any obstacle.  Obstacles are closed sets (Sec. II), so touching
+ * counts as a collision.
+ *
+ * Binning (Sec. III, decomposition R and sub-regions R_i^k): a uniform grid
+ * over the workspace position, optionally with speed bins in the region
+ * index; each region holds a uniform sub-grid.
+ */
+#include <math.h>
+#include <string.h>
+
+#include "kpo_internal.h"
+
+/* ------------------------------------------------------------------ */
+/* vector fields                                                        */
+/* ------------------------------------------------------------------ */
+
+static void f_dubins(const double *x, const double *u, double *dx) {
+  double psi = x[3], theta = x[4], v = x[5];
+  dx[0] = v * cos(psi) * cos(theta);
+  dx[1] = v * sin(psi) * cos(theta);
+  dx[2] = v * sin(theta);
+  dx[3] = u[0];
+  dx[4] = u[1];
+  dx[5] = u[2];
+}
+
+static void f_quad(const double *phys, const double *x, const double *u,
+                   double *dx) {
+  double m = phys[0], g = phys[1], l = phys[2], c = phys[3];
+  double Ix = phys[4], Iy = phys[5], Iz = phys[6];
+  double phi = x[3], theta = x[4], psi = x[5];
+  double vx = x[6], vy = x[7], vz = x[8];
+  double p = x[9], q = x[10], r = x[11];
+  double T1 = u[0], T2 = u[1], T3 = u[2], T4 = u[3];
+
+  /* position */
+  dx[0] = vx;
+  dx[1] = vy;
+  dx[2] = vz;
+  /* Euler-angle rates from body rates (ZYX angles) */
+  double sphi = sin(phi), cphi = cos(phi);
+  double ttheta = tan(theta), ctheta = cos(theta);
+  dx[3] = p + sphi * ttheta * q + cphi * ttheta * r;
+  dx[4] = cphi * q - sphi * r;
+  dx[5] = (sphi * q + cphi * r) / ctheta;
+  /* translational: thrust along the body z axis, rotated to the world */
+  double stheta = sin(theta), spsi = sin(psi), cpsi = cos(psi);
+  double thrust = T1 + T2 + T3 + T4;
+  double bz_x = cphi * stheta * cpsi + sphi * spsi;
+  double bz_y = cphi * stheta * spsi - sphi * cpsi;
+  double bz_z = cphi * ctheta;
+  dx[6] = thrust / m * bz_x;
+  dx[7] = thrust / m * bz_y;
+  dx[8] = thrust / m * bz_z - g;
+  /* rotational: Euler's equations with a diagonal inertia */
+  double tau_x = l * (T2 - T4);
+  double tau_y = l * (T3 - T1);
+  double tau_z = c * (T1 - T2 + T3 - T4);
+  double Lx = Ix * p, Ly = Iy * q, Lz = Iz * r; /* I omega */
+  double gx = q * Lz - r * Ly;                 /* omega x (I omega) */
+  double gy = r * Lx - p * Lz;
+  double gz = p * Ly - q * Lx;
+  dx[9] = (tau_x - gx) / Ix;
+  dx[10] = (tau_y - gy) / Iy;
+  dx[11] = (tau_z - gz) / Iz;
+}
+
+static void vector_field(const kpo_config *cfg, const double *x,
+                         const double *u, double *dx) {
+  switch (cfg->system) {
+  case KPO_DUBINS:
+    f_dubins(x, u, dx);
+    break;
+  case KPO_QUAD:
+    f_quad(cfg->phys, x, u, dx);
+    break;
+  default: /* double integrator */
+    for (int i = 0; i < 3; ++i) {
+      dx[i] = x[3 + i];
+      dx[3 + i] = u[i];
+    }
+  }
+}
+
+static int state_dim(int system) { return system == KPO_QUAD ? 12 : 6; }
+
+void kpo_step(const kpo_config *cfg, const double *x, const double *u,
+              double h, double *x_out) {
+  int d = state_dim(cfg->system);
+  if (cfg->system == KPO_DI) {
+    /* explicit Euler: x_{i+1} = x_i + h f(x_i, u) */
+    double dx[12];
+    vector_field(cfg, x, u, dx);
+    for (int i = 0; i < d; ++i) x_out[i] = x[i] + h * dx[i];
+    return;
+  }
+  /* classic fourth-order Runge-Kutta */
+  double k1[12], k2[12], k3[12], k4[12], tmp[12];
+  vector_field(cfg, x, u, k1);
+  for (int i = 0; i < d; ++i) tmp[i] = x[i] + 0.5 * h * k1[i];
+  vector_field(cfg, tmp, u, k2);
+  for (int i = 0; i < d; ++i) tmp[i] = x[i] + 0.5 * h * k2[i];
+  vector_field(cfg, tmp, u, k3);
+  for (int i = 0; i < d; ++i) tmp[i] = x[i] + h * k3[i];
+  vector_field(cfg, tmp, u, k4);
+  for (int i = 0; i < d; ++i)
+    x_out[i] = x[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+void kpo_propagate(const kpo_config *cfg, const double *x0, const double *u,
+                   int32_t k, double *traj) {
+  int d = state_dim(cfg->system);
+  memcpy(traj, x0, sizeof(double) * d);
+  for (int i = 0; i < k; ++i)
+    kpo_step(cfg, traj + (size_t)i * d, u, cfg->dt, traj + (size_t)(i + 1) * d);
+}
+
+/* ------------------------------------------------------------------ */
+/* validity                                                            */
+/* ------------------------------------------------------------------ */
+
+/* Returns 1 when the state lies in the closed state box.  *margin is the
+ * smallest normalised distance to a bound (negative when violated: the
+ * largest normalised violation). */
+static int bounds_ok(const kpo *o, const double *x, double *margin) {
+  double worst_in = INFINITY, worst_out = 0.0;
+  int ok = 1;
+  for (int i = 0; i < o->d; ++i) {
+    double lo = o->cfg.x_lo[i], hi = o->cfg.x_hi[i];
+    double scale = (isfinite(lo) && isfinite(hi)) ? (hi - lo) : 1.0;
+    if (!(lo <= x[i] && x[i] <= hi)) { /* NaN is invalid too */
+      ok = 0;
+      double depth = isnan(x[i]) ? INFINITY
+                                 : (x[i] < lo ? lo - x[i] : x[i] - hi) / scale;
+      if (depth > worst_out) worst_out = depth;
+    } else {
+      double m = fmin(x[i] - lo, hi - x[i]) / scale;
+      if (m < worst_in) worst_in = m;
+    }
+  }
+  *margin = ok ? worst_in : -worst_out;
+  return ok;
+}
+
+int32_t kpo_step_valid(const kpo *o, const double *x0, const double *x1,
+                       double *margin) {
+  double bmargin;
+  int ok = bounds_ok(o, x1, &bmargin);
+  /* axis-aligned box of the two positions */
+  double slo[3], shi[3];
+  for (int a = 0; a < 3; ++a) {
+    slo[a] = fmin(x0[a], x1[a]);
+    shi[a] = fmax(x0[a], x1[a]);
+  }
+  double min_sep = INFINITY; /* over boxes that are separated */
+  double max_pen = 0.0;      /* over boxes that are hit       */
+  int hit = 0;
+  for (int b = 0; b < o->nb; ++b) {
+    const double *bx = o->boxes + 6 * (size_t)b;
+    /* per-axis gap between the two closed intervals; the boxes meet
+     * exactly when no axis has a positive gap */
+    double sep = -INFINITY;
+    for (int a = 0; a < 3; ++a) {
+      double scale = o->cfg.ws_hi[a] - o->cfg.ws_lo[a];
+      double gap = fmax(bx[a] - shi[a], slo[a] - bx[3 + a]) / scale;
+      if (gap > sep) sep = gap;
+    }
+    if (sep <= 0.0) {
+      hit = 1;
+      if (-sep > max_pen) max_pen = -sep;
+    } else if (sep < min_sep) {
+      min_sep = sep;
+    }
+  }
+  if (ok && !hit) {
+    *margin = fmin(bmargin, min_sep);
+    return 1;
+  }
+  /* invalid: how far inside the invalid side the strongest violation is */
+  double v = 0.0;
+  if (!ok) v = fmax(v, -bmargin);
+  if (hit) v = fmax(v, max_pen);
+  *margin = v;
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* binning                                                              */
+/* ------------------------------------------------------------------ */
+
+/* Cell of coordinate t (already scaled to cell units) among n cells,
+ * clamped to [0, n-1]; *margin = distance (in cell units) to the nearest
+ * interior face, i.e. a face whose crossing changes the cell. */
+static int cell_of(double t, int n, double *margin) {
+  int i;
+  if (!(t >= 0.0)) /* also NaN */
+    i = 0;
+  else if (t >= (double)n)
+    i = n - 1;
+  else
+    i = (int)floor(t);
+  double m = INFINITY;
+  if (isnan(t)) {
+    m = 0.0;
+  } else {
+    for (int f = 1; f < n; ++f) {
+      double dist = fabs(t - (double)f);
+      if (dist < m) m = dist;
+    }
+  }
+  *margin = m;
+  return i;
+}
+
+static double speed_of(const kpo *o, const double *x) {
+  switch (o->cfg.system) {
+  case KPO_DUBINS:
+    return fabs(x[5]);
+  case KPO_QUAD:
+    return sqrt(x[6] * x[6] + x[7] * x[7] + x[8] * x[8]);
+  default:
+    return sqrt(x[3] * x[3] + x[4] * x[4] + x[5] * x[5]);
+  }
+}
+
+void kpo_bin(const kpo *o, const double *x, int32_t *region, int32_t *sub,
+             double *margin) {
+  int cell[3], fine[3];
+  double worst = INFINITY;
+  for (int a = 0; a < 3; ++a) {
+    int n = o->cfg.grid[a] * o->cfg.sub[a]; /* fine cells along the axis */
+    double t = (x[a] - o->cfg.ws_lo[a]) *
+               ((double)n / (o->cfg.ws_hi[a] - o->cfg.ws_lo[a]));
+    double m;
+    fine[a] = cell_of(t, n, &m);
+    m /= (double)n; /* to normalised workspace units */
+    if (m < worst) worst = m;
+    cell[a] = fine[a] / o->cfg.sub[a];
+    fine[a] = fine[a] % o->cfg.sub[a];
+  }
+  int sb = 0;
+  if (o->cfg.speed_bins > 1) {
+    double m;
+    double t = speed_of(o, x) * ((double)o->cfg.speed_bins / o->cfg.speed_hi);
+    sb = cell_of(t, o->cfg.speed_bins, &m);
+    m /= (double)o->cfg.speed_bins;
+    if (m < worst) worst = m;
+  }
+  int gx = o->cfg.grid[0], gy = o->cfg.grid[1], gz = o->cfg.grid[2];
+  int r = cell[0] + gx * (cell[1] + gy * (cell[2] + gz * sb));
+  int k = fine[0] + o->cfg.sub[0] * (fine[1] + o->cfg.sub[1] * fine[2]);
+  *region = r;
+  *sub = r * o->n_sub_per + k;
+  if (margin) *margin = worst;
+}
+
+/* ------------------------------------------------------------------ */
+/* dense re-validation of an edge                                       */
+/* ------------------------------------------------------------------ */
+
+/* Violation depth of a single state: bounds and point-in-closed-box. */
+static double point_violation(const kpo *o, const double *x) {
+  double bm;
+  double v = 0.0;
+  if (!bounds_ok(o, x, &bm)) v = -bm;
+  for (int b = 0; b < o->nb; ++b) {
+    const double *bx = o->boxes + 6 * (size_t)b;
+    double pen = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+      double scale = o->cfg.ws_hi[a] - o->cfg.ws_lo[a];
+      double in = fmin(x[a] - bx[a], bx[3 + a] - x[a]) / scale;
+      if (in < pen) pen = in;
+    }
+    /* pen >= 0 means inside the closed box; report a touch as a tiny
+     * positive depth so that it is never mistaken for 'valid' */
+    if (pen >= 0.0) v = fmax(v, fmax(pen, 1e-300));
+  }
+  return v;
+}
+
+double kpo_dense_check(const kpo *o, const double *x0, const double *u,
+                       int32_t k, int32_t sub, double *x_end) {
+  double x[12], nx[12], y[12];
+  int d = o->d;
+  memcpy(x, x0, sizeof(double) * d);
+  double worst = 0.0;
+  for (int i = 0; i < k; ++i) {
+    kpo_step(&o->cfg, x, u, o->cfg.dt, nx); /* the integrator's own step */
+    if (o->cfg.system == KPO_DI) {
+      /* the Euler step is a straight segment in position: sample it */
+      for (int s = 1; s <= sub; ++s) {
+        double w = (double)s / (double)sub;
+        for (int j = 0; j < d; ++j) y[j] = x[j] + w * (nx[j] - x[j]);
+        worst = fmax(worst, point_violation(o, y));
+      }
+    } else {
+      /* re-integrate the step with 'sub' RK4 sub-steps */
+      memcpy(y, x, sizeof(double) * d);
+      for (int s = 1; s <= sub; ++s) {
+        double z[12];
+        kpo_step(&o->cfg, y, u, o->cfg.dt / (double)sub, z);
+        memcpy(y, z, sizeof(double) * d);
+        worst = fmax(worst, point_violation(o, y));
+      }
+    }
+    memcpy(x, nx, sizeof(double) * d);
+  }
+  if (x_end) memcpy(x_end, x, sizeof(double) * d);
+  return worst;
+}
