@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Kino-PAX planning throughput on one GB300 (or N, as independent replicas).
+
+One step = one complete planning query (Problem 1) on a fresh seeded
+synthetic layout: reset, the device-resident loop of Propagate /
+UpdateEstimates / UpdateNodeSets until a goal node is appended, and the
+trajectory read-back.  Default workload: 6D Dubins airplane in a forest of
+200 vertical boxes, 16^3 regions x 4^3 sub-regions, lambda_max 64, t_e 2^20.
+
+Printed (rank 0, one JSON line): samples propagated+checked per second over
+the device time of the queries (inputs resident, L2 flushed before every
+step), p50/p99 time-to-solution, the end-to-end figure through the public
+API with host buffers, the roofline of the persistent loop kernel against
+the FP32/INT lane-issue peak, the CPU oracle baseline and SM clocks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2409_06807_gb300 import workloads as W  # noqa: E402
+
+METRIC = "samples propagated+checked/s"
+MAX_ITERS = 400
+KCTL_BYTES = 512
+
+# Algorithmic lane operations per unit of work (see the design notes):
+# per sample: two Philox4x32-10 blocks (10 rounds x 10 integer ops each),
+# the control and duration maps, binning, counters and flags;
+# per integrator step: the integrator itself plus the state-box test;
+# per step hull: its 6 min/max plus 8 ops for every obstacle box tested.
+OPS_PER_SAMPLE = {W.DI: 200 + 11 + 30, W.DUBINS: 200 + 11 + 30, W.QUAD: 200 + 14 + 34}
+OPS_PER_STEP = {W.DI: 6 + 18, W.DUBINS: 222 + 18, W.QUAD: 688 + 36}
+OPS_PER_BOX = 8
+OPS_PER_HULL = 6
+
+
+def alg_ops(system, n_boxes, samples, steps, hulls):
+    return (OPS_PER_SAMPLE[system] * samples + OPS_PER_STEP[system] * steps
+            + (OPS_PER_HULL + OPS_PER_BOX * n_boxes) * hulls)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2409_06807_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.traffic")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def workload_config(w):
+    return {
+        "workload": f"{w.name}: system {w.system} (6D Dubins airplane RK4 dt 0.05, 1-20 steps)"
+        if w.system == W.DUBINS else w.name,
+        "boxes": int(len(w.boxes)),
+        "regions": f"{w.grid[0]}x{w.grid[1]}x{w.grid[2]}x{w.speed_bins} x sub "
+                   f"{w.sub[0]}x{w.sub[1]}x{w.sub[2]}",
+        "lambda_max": w.lambda_max, "t_e": w.t_e, "delta": w.delta, "eps": w.eps,
+        "layouts": "one seeded synthetic layout per step (rank-offset seeds)",
+        "l2": "flushed before every timed step (256 MiB device write)",
+        "max_iters": MAX_ITERS,
+    }
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle
+# ---------------------------------------------------------------------------
+
+def oracle_sample(make, seed, passes):
+    """Samples and seconds of the oracle's first 'passes' loop passes."""
+    from oracle.kpo import Oracle
+    o = Oracle(make(seed))
+    o.reset()
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(passes):
+        status, st, _ = o.iterate()
+        n += st.get("n_samples", 0) if st else 0
+        if status != 0:
+            break
+    return n, time.perf_counter() - t0
+
+
+def cpu_baseline(make, budget_s=15.0):
+    n_tot, t_tot, seeds = 0, 0.0, []
+    seed = 0
+    while t_tot < budget_s and seed < 8:
+        n, t = oracle_sample(make, 10_000 + seed, 3)
+        n_tot += n
+        t_tot += t
+        seeds.append(10_000 + seed)
+        seed += 1
+    return {"value": n_tot / t_tot, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": f"first 3 loop passes of {len(seeds)} seeded layouts "
+                      f"(seeds {seeds[0]}..{seeds[-1]}), {n_tot} samples, single thread"}
+
+
+def run_reference(args, world, rank):
+    """The FP64 oracle timed on this host as the reference arm."""
+    if rank != 0:
+        return
+    make = W.BY_NAME[args.workload]
+    for i in range(args.warmup):
+        oracle_sample(make, 20_000 + i, 3)
+    n_tot, t_tot, times = 0, 0.0, []
+    for i in range(args.steps):
+        n, t = oracle_sample(make, 30_000 + i, 3)
+        n_tot += n
+        t_tot += t
+        times.append(t)
+    v = n_tot / t_tot
+    w = make(0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(w),
+        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: first 3 loop passes of one seeded layout"},
+        "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2409_06807_gb300.build import build_planner
+    build_planner()
+    from paper_2409_06807_gb300 import planner as P
+
+    torch.cuda.set_device(local)
+    make = W.BY_NAME[args.workload]
+    n_total = args.warmup + args.steps
+    seeds = [rank * 100_000 + i for i in range(n_total)]
+    layouts = [make(s) for s in seeds]
+    w0 = layouts[0]
+    pl = P.Planner(w0, device=f"cuda:{local}")
+    stream = pl.stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    cap = 4096
+
+    def one_query(w):
+        pl.set_obstacles(w.boxes)
+        pl.w = w
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pl.plan_async(max_iters=MAX_ITERS, capacity=cap)
+        e1.record(stream)
+        st, traj = pl.plan_result()
+        step_ms = e0.elapsed_time(e1)
+        loop_ms = pl.last_launch_ms()
+        info = pl.info()
+        return st, step_ms, loop_ms, info
+
+    for i in range(args.warmup):
+        one_query(layouts[i])
+
+    barrier(world)
+    torch.cuda.synchronize()
+    rows = []
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for i in range(args.warmup, n_total):
+            rows.append(one_query(layouts[i]))
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier(world)
+
+    step_ms = [r[1] for r in rows]
+    loop_ms = [r[2] for r in rows]
+    samples = sum(r[3]["n_samples"] for r in rows)
+    solved = sum(1 for r in rows if r[0] == P.OK)
+    total_ms = sum(step_ms)
+    total_ms_max = max_over_ranks(total_ms, world)
+    samples_all = sum_over_ranks(float(samples), world)
+    value = samples_all / (total_ms_max / 1e3)
+
+    # roofline of the persistent loop kernel (dominant kernel)
+    ops = sum(alg_ops(w0.system, len(layouts[args.warmup + j].boxes), r[3]["n_samples"],
+                      r[3]["n_steps"], r[3]["n_hull_checks"]) for j, r in enumerate(rows))
+    pk, pk_kind = peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_ops = n_sm * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12  # Top/s
+    achieved = ops / (sum(loop_ms) / 1e3) / 1e12
+    traffic = profiled_traffic(f"kp_loop_kernel_{args.workload}")
+
+    # end to end through the public API with host buffers: obstacle upload
+    # from pinned staging, the query, the trajectory read-back
+    torch.cuda.synchronize()
+    e2e_samples = 0
+    t0 = time.perf_counter()
+    for i in range(args.warmup, n_total):
+        w = layouts[i]
+        pl.set_obstacles(w.boxes)
+        pl.w = w
+        st, traj = pl.plan(max_iters=MAX_ITERS, capacity=cap)
+        e2e_samples += pl.info()["n_samples"]
+    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(t_e2e, world)
+    e2e_all = sum_over_ranks(float(e2e_samples), world)
+    h2d = int(np.mean([((len(layouts[i].boxes) + 7) // 8 * 8) * 32
+                       for i in range(args.warmup, n_total)]))
+    d2h = KCTL_BYTES + 256 * 17 * 4  # header + first trajectory rows
+
+    if rank != 0:
+        return
+    cpu = cpu_baseline(make) if world == 1 and not args.no_cpu else None
+    pct = np.percentile(step_ms, [50, 99])
+    line = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**workload_config(w0), "parallelism": f"replicas x{world}"},
+        "solve_ms": {"p50": float(pct[0]), "p99": float(pct[1]),
+                     "mean": float(np.mean(step_ms))},
+        "success_rate": solved / len(rows),
+        "loop_kernel_ms": {"mean": float(np.mean(loop_ms))},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
+                     "frac": achieved / peak_ops, "traffic": traffic,
+                     "peak_source": f"{n_sm} SMs x 128 lanes x {pk.get('sm_max_mhz')} MHz "
+                                    f"({pk_kind} max SM clock)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_all / t_e2e, "unit": "samples/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+        "wall_s": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(W.BY_NAME))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,287 @@
+/*
+ * kp.h -- C ABI of the GB300 Kino-PAX planner.
+ *
+ * Kino-PAX (Perrault, Ho, Lahijanian, "Kino-PAX: Highly Parallel
+ * Kinodynamic Sampling-based Planner", RA-L 2025) grows a tree of
+ * trajectory segments in three data-parallel subroutines per iteration:
+ * Propagate (Algorithm 2), UpdateEstimates (Algorithm 3, Eq. 3-5) and
+ * UpdateNodeSets (Algorithm 4), with the branching factor of Eq. 6.  This
+ * library runs that loop on one GPU, entirely on the device, and answers
+ * the planning query of Problem 1 (Sec. II): given x_init and a goal set,
+ * return a control trajectory whose induced state trajectory is valid and
+ * reaches the goal.
+ *
+ * Conventions for every entry point:
+ *  - Memory.  The library allocates no device memory.  All device state
+ *    lives in one caller-owned arena of kp_required_bytes() bytes (for
+ *    example a uint8 CUDA tensor); it must stay alive and untouched by the
+ *    caller until kp_destroy().  Host inputs are copied during the call and
+ *    may be freed when it returns.  Host outputs go to caller buffers.
+ *  - Streams.  All device work is enqueued on the stream given to
+ *    kp_create (NULL = the legacy default stream).  Calls that return host
+ *    results synchronise that stream before returning.
+ *  - Errors.  Every call returns a kp_status; nothing else crosses the ABI.
+ *    KP_NO_SOLUTION is a normal outcome.  After KP_ERR_CUDA or
+ *    KP_ERR_TIMEOUT the context is poisoned: every later call except
+ *    kp_last_error and kp_destroy returns KP_ERR_STATE.
+ *  - Threads.  A context belongs to one host thread at a time.
+ *  - Units.  States, controls and boxes are in the units of kp_system and
+ *    kp_workspace; all real inputs are float32.
+ */
+#ifndef KP_H
+#define KP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KP_OK = 0,            /* call succeeded (kp_plan: a solution was found)   */
+  KP_NO_SOLUTION = 1,   /* budget spent or tree full (Eq. 6 gave lambda 0)  */
+  KP_ERR_ARG = -1,      /* invalid argument; nothing was changed            */
+  KP_ERR_OOM = -2,      /* arena smaller than kp_required_bytes()           */
+  KP_ERR_CUDA = -3,     /* a CUDA call failed; context poisoned             */
+  KP_ERR_TIMEOUT = -4,  /* a bounded device wait expired; context poisoned  */
+  KP_ERR_STATE = -5     /* call not allowed in the context's current state  */
+} kp_status;
+
+typedef enum {
+  KP_DOUBLE_INTEGRATOR_6D = 0, /* x = (p, v), u = a; explicit Euler         */
+  KP_DUBINS_AIRPLANE_6D = 1,   /* x = (x,y,z,yaw,pitch,speed),
+                                  u = (yaw rate, pitch rate, accel); RK4    */
+  KP_QUADROTOR_12D = 2         /* x = (p, roll,pitch,yaw, v_world,
+                                  omega_body), u = 4 rotor thrusts; RK4     */
+} kp_system_id;
+
+/* Dynamics (Sec. II, Eq. 1-2) and the state/control boxes of the valid set.
+ * A sample's duration is k integrator steps of dt, k uniform in
+ * [k_min, k_max] (Algorithm 2 draws dt in (0, T_prop]).  Entries of
+ * x_lo/x_hi beyond the state dimension are ignored; +-inf leaves a state
+ * unbounded.  phys: quadrotor m, g, l, c, Ixx, Iyy, Izz (others unused). */
+typedef struct {
+  int32_t id;                 /* kp_system_id                              */
+  float dt;                   /* integrator step, > 0                      */
+  int32_t k_min, k_max;       /* 1 <= k_min <= k_max <= 255                 */
+  float x_lo[12], x_hi[12];
+  float u_lo[4], u_hi[4];
+  float phys[16];
+} kp_system;
+
+/* Workspace W (Sec. II) and the decomposition R (Sec. III): a uniform grid
+ * of grid[0]*grid[1]*grid[2] position cells times speed_bins speed bins over
+ * [0, speed_hi]; every region holds sub[0]*sub[1]*sub[2] sub-regions. */
+typedef struct {
+  float lo[3], hi[3];
+  int32_t grid[3];
+  int32_t speed_bins;         /* >= 1 (1: no speed bins)                    */
+  float speed_hi;
+  int32_t sub[3];
+} kp_workspace;
+
+/* Obstacle set O (Sec. II): closed axis-aligned boxes, host pointer to
+ * n_boxes rows of {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z}; copied. */
+typedef struct {
+  const float *boxes;
+  int32_t n_boxes;            /* 0 .. KP_MAX_BOXES                          */
+} kp_obstacles;
+
+#define KP_MAX_BOXES 4096
+
+/* Goal set X_goal: the closed ball of positions |p - center| <= radius. */
+typedef struct {
+  float center[3];
+  float radius;
+} kp_goal;
+
+/* Planner constants: t_e node cap (Sec. IV-A), lambda_max (Eq. 6), delta
+ * (Eq. 3), eps (Eq. 5, Lemma 1), 64-bit seed of the Philox stream. */
+typedef struct {
+  int32_t t_e;                /* 2 .. 2^28                                  */
+  int32_t lambda_max;         /* 1 .. 1024                                   */
+  double delta;               /* > 0                                         */
+  double eps;                 /* (0, 1)                                      */
+  uint64_t seed;
+} kp_params;
+
+/* Loop budget for kp_plan: stop after max_iters passes or max_ms of device
+ * time (<= 0: no time limit), whichever comes first. */
+typedef struct {
+  int32_t max_iters;
+  double max_ms;
+} kp_budget;
+
+/* Trajectory out: root-to-goal edges.  Caller buffers of 'capacity' rows:
+ * states [capacity][12] (state at the end of each edge), ctrls
+ * [capacity][4] (constant control of the edge), steps [capacity]
+ * (integrator steps of the edge).  n_edges is set on return. */
+typedef struct {
+  int32_t capacity;
+  int32_t n_edges;
+  float *states;
+  float *ctrls;
+  int32_t *steps;
+} kp_traj;
+
+/* One loop pass (Algorithm 1 body). */
+typedef struct {
+  int32_t iteration;   /* pass index, from 0 after kp_reset                */
+  int32_t n_ve;        /* |V_E| expanded in this pass                      */
+  int32_t lambda;      /* branching factor of this pass (Eq. 6)            */
+  int32_t n_samples;   /* |V_E| * lambda                                   */
+  int32_t n_valid;     /* samples whose segment was valid                  */
+  int32_t n_accepted;  /* |V_U| appended to the tree                       */
+  int32_t n_nodes;     /* |T| after the pass                               */
+  int32_t goal_node;   /* smallest new goal node id, -1 if none            */
+} kp_iter_stats;
+
+/* Context status snapshot.  The work counters cover every pass since the
+ * last kp_reset / kp_plan. */
+typedef struct {
+  int32_t n_nodes, n_ve, iteration, goal_node;
+  int32_t state;       /* 0 running, 1 solved, 2 tree full, -1 error      */
+  int32_t n_regions, n_subregions, state_dim, control_dim;
+  int32_t n_boxes;     /* obstacle slots in use (padded to a multiple of 8) */
+  int32_t grid_blocks; /* blocks of the persistent loop launch             */
+  int64_t n_samples;   /* samples propagated and checked                   */
+  int64_t n_steps;     /* integrator steps run (each one checked)          */
+  int64_t n_hull_checks; /* step hulls tested against the obstacle set     */
+} kp_info;
+
+/* Host-side copy of the tree and decomposition (tests, checkpoints).
+ * State rows are node-major: state[v * 12 + i], ctrl[v * 4 + i].  Arrays
+ * must hold 'capacity' nodes / n_regions regions / n_subregions entries. */
+typedef struct {
+  int32_t capacity;
+  int32_t n_nodes;      /* out (export) / in (import)                      */
+  int32_t iteration;    /* out / in: next pass index                       */
+  float *state;         /* [capacity][12]                                   */
+  int32_t *parent;      /* -1 for the root                                  */
+  float *ctrl;          /* [capacity][4]                                    */
+  int32_t *steps;
+  int32_t *region;
+  int32_t *sub;         /* global sub-region index                          */
+  uint8_t *in_ve;       /* 1: V_E, 0: V_O                                    */
+  uint32_t *n_valid;    /* [n_regions] cumulative counters (Algorithm 2)    */
+  uint32_t *n_invalid;
+  uint32_t *cov;        /* [n_regions] visited sub-regions (export only)    */
+  uint8_t *avail;       /* [n_regions] R_avail membership (export only)     */
+  uint64_t *thr;        /* [n_regions] accept threshold: draw w < thr       */
+  uint8_t *visited;     /* [n_subregions]                                    */
+} kp_tree_view;
+
+/* Per-sample record of the most recent pass (parity checks).  DEVICE
+ * pointers, each with room for 'capacity' samples (uraw: 4 per sample,
+ * state: 12 per sample, sample-major).  Sample key = position of the
+ * expanded node in V_E (ascending node id) * lambda + j.  flags: bit0
+ * valid, bit1 reached an unvisited sub-region, bit2 accept draw passed,
+ * bit3 representative of its sub-region, bit4 appended, bit5 goal. */
+typedef struct {
+  int32_t capacity;
+  int32_t *node;
+  int32_t *k;
+  uint32_t *uraw;
+  uint8_t *flags;
+  int32_t *fail_step;   /* 0 valid, else first invalid integrator step     */
+  int32_t *region;
+  int32_t *sub;
+  float *state;         /* state at the end or at the first invalid step   */
+} kp_sample_log;
+
+typedef struct kp_ctx kp_ctx;
+
+/* Bytes of device arena a context needs (room for KP_MAX_BOXES obstacles
+ * is always reserved).  Returns 0 for invalid inputs. */
+size_t kp_required_bytes(const kp_system *sys, const kp_workspace *ws,
+                         int32_t n_boxes, const kp_params *prm);
+
+/* Creates a context on the current CUDA device over the caller's arena
+ * (256-byte aligned device pointer).  Copies the obstacles.  The tree is
+ * empty until kp_reset.  Errors: KP_ERR_ARG (bad inputs, misaligned
+ * arena), KP_ERR_OOM (arena too small), KP_ERR_CUDA. */
+kp_status kp_create(const kp_system *sys, const kp_workspace *ws,
+                    const kp_obstacles *obs, const kp_params *prm,
+                    void *dev_arena, size_t arena_bytes, void *cuda_stream,
+                    kp_ctx **out);
+
+/* Replaces the obstacle set (up to KP_MAX_BOXES boxes).  Resets the tree
+ * to empty. */
+kp_status kp_set_obstacles(kp_ctx *ctx, const kp_obstacles *obs);
+
+/* Algorithm 1, lines 1-3: tree = {x_init}, V_E = {x_init}, counters zero,
+ * P_accept = 1 everywhere; the Philox key becomes 'seed'.  x_init is a
+ * host array of the state dimension.  KP_ERR_ARG if x_init is not valid
+ * (Problem 1 requires x_init in X_valid).  If x_init already lies in the
+ * goal set the query is solved with zero edges. */
+kp_status kp_reset(kp_ctx *ctx, const float *x_init, const kp_goal *goal,
+                   uint64_t seed);
+
+/* Runs up to n_iters passes of the Algorithm 1 loop body on the device
+ * (fewer when a goal node is appended or Eq. 6 gives lambda = 0), in one
+ * launch with no host synchronisation between passes.  Writes one record
+ * per pass run to 'out' (nullable, room for n_iters).  Returns KP_OK. */
+kp_status kp_expand_step(kp_ctx *ctx, int32_t n_iters, kp_iter_stats *out,
+                         int32_t *n_run);
+
+/* Problem 1 end to end: kp_reset, the loop until a goal node is appended or
+ * the budget or the tree is exhausted, then the root-to-goal edge list.
+ * Returns KP_OK with traj filled, KP_NO_SOLUTION, or KP_ERR_ARG when
+ * traj->capacity is too small (traj->n_edges then holds the size needed). */
+kp_status kp_plan(kp_ctx *ctx, const float *x_init, const kp_goal *goal,
+                  const kp_budget *budget, kp_traj *traj);
+
+/* kp_plan in two halves.  kp_plan_async validates its arguments and
+ * enqueues the whole query (reset, loop, trajectory extraction) on the
+ * context's stream without waiting; traj_capacity is the number of
+ * trajectory rows kp_plan_result will read back.  kp_plan_result waits
+ * for that work and fills traj as kp_plan does (KP_ERR_STATE when no
+ * kp_plan_async is pending). */
+kp_status kp_plan_async(kp_ctx *ctx, const float *x_init, const kp_goal *goal,
+                        const kp_budget *budget, int32_t traj_capacity);
+kp_status kp_plan_result(kp_ctx *ctx, kp_traj *traj);
+
+/* Device duration, in milliseconds, of the most recent launch of the
+ * persistent loop kernel, from CUDA events the library records on the
+ * context's stream around that launch (waits for it to finish). */
+kp_status kp_last_launch_ms(kp_ctx *ctx, float *ms);
+
+/* Status snapshot (synchronises the stream). */
+kp_status kp_get_info(kp_ctx *ctx, kp_info *out);
+
+/* Copies the tree and decomposition to host buffers. */
+kp_status kp_export_tree(kp_ctx *ctx, kp_tree_view *host_out);
+
+/* Loads a tree and decomposition from host buffers (n_nodes, iteration,
+ * state, parent, ctrl, steps, region, sub, in_ve, n_valid, n_invalid, thr,
+ * visited are read; cov and R_avail are recomputed from visited and the
+ * node regions).  The loop continues from there. */
+kp_status kp_import_tree(kp_ctx *ctx, const kp_tree_view *host_in);
+
+/* Enables (log != NULL) or disables per-sample records of each pass.  A
+ * pass with more samples than log->capacity records only the first
+ * capacity samples. */
+kp_status kp_set_sample_log(kp_ctx *ctx, const kp_sample_log *log);
+
+/* Upper bound, in nanoseconds, of every device-side wait (grid barrier,
+ * bulk-copy completion).  On expiry the launch stops, the call returns
+ * KP_ERR_TIMEOUT and the context is poisoned.  Default 2e9 (2 s). */
+kp_status kp_set_wait_limit(kp_ctx *ctx, uint64_t ns);
+
+/* Test hook for the bounded-wait path: one block waits on a device flag
+ * that nothing ever sets, for at most the context's wait limit, then
+ * reports.  Returns KP_ERR_TIMEOUT (and poisons the context) when the wait
+ * expired as designed. */
+kp_status kp_selftest_wait_timeout(kp_ctx *ctx);
+
+/* Last error message of the context (never NULL). */
+const char *kp_last_error(const kp_ctx *ctx);
+
+/* Frees the context's host memory; the arena stays the caller's. */
+void kp_destroy(kp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

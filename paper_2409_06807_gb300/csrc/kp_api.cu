@@ -1,0 +1,911 @@
+// kp_api.cu -- host driver behind the C ABI of include/kp.h: arena layout,
+// context lifetime, launches of the loop kernel, tree import/export, and the
+// small generic kernels (trajectory extraction, import fix-up, wait self
+// test).  The library allocates no device memory: every device array is a
+// slice of the caller's arena.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/kp.h"
+#include "kp_device.cuh"
+
+namespace kp {
+// launchers defined in kp_sys_*.cu
+#define KP_DECLARE_SYS(name)                                                                   \
+  cudaError_t loop_occupancy_##name(bool log, size_t smem, int* blocks_per_sm);                \
+  cudaError_t launch_loop_##name(const KParams& P, int grid, size_t smem, int max_iters,        \
+                                 uint64_t max_ns, bool log, cudaStream_t stream);              \
+  cudaError_t launch_reset_##name(const KParams& P, const RootState& root, cudaStream_t stream);
+KP_DECLARE_SYS(di)
+KP_DECLARE_SYS(dubins)
+KP_DECLARE_SYS(quad)
+#undef KP_DECLARE_SYS
+
+// ---------------------------------------------------------------------------
+// generic kernels
+// ---------------------------------------------------------------------------
+
+// Root-to-goal chain into P.traj rows (state 12, ctrl 4, steps), root first.
+__global__ void kp_extract_kernel(KParams P) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  KCtl* ctl = P.ctl;
+  const int g = ctl->goal_node;
+  if (g == KP_NO_GOAL || g < 0 || g >= P.t_e) {
+    ctl->n_edges = -1;
+    return;
+  }
+  int len = 0;
+  for (int v = g; v > 0 && len <= P.t_e; v = P.parent[v]) ++len;
+  ctl->n_edges = len;
+  if (len > KP_TRAJ_ROWS) return;
+  const int D = P.sys == KP_SYS_QUAD ? 12 : 6;
+  const int N = P.sys == KP_SYS_QUAD ? 4 : 3;
+  int row = len - 1;
+  for (int v = g; v > 0 && row >= 0; v = P.parent[v], --row) {
+    float* out = P.traj + (size_t)row * 17;
+    for (int i = 0; i < 12; ++i) out[i] = i < D ? P.st[(size_t)i * P.t_e + v] : 0.0f;
+    for (int i = 0; i < 4; ++i) out[12 + i] = i < N ? P.ctrl[(size_t)i * P.t_e + v] : 0.0f;
+    out[16] = (float)P.steps[v];
+  }
+}
+
+// Import fix-up: Cov from the visited flags, R_avail cleared.
+__global__ void kp_import_regions_kernel(KParams P) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.R; r += gridDim.x * blockDim.x) {
+    uint32_t c = 0;
+    for (int k = 0; k < P.n_sub_per; ++k) c += P.visited[(size_t)r * P.n_sub_per + k] ? 1u : 0u;
+    P.cov[r] = c;
+    P.avail[r] = 0;
+  }
+}
+
+// Import fix-up: R_avail from the node regions.
+__global__ void kp_import_avail_kernel(KParams P, int n) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    P.avail[P.region[v]] = 1;
+}
+
+// Bounded wait on a flag that nothing sets; records the timeout.
+__global__ void kp_wait_selftest_kernel(KParams P) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  KCtl* ctl = P.ctl;
+  const uint64_t t0 = global_ns();
+  while (ld_acquire(&ctl->never_set) == 0) {
+    if (global_ns() - t0 > P.wait_ns) {
+      raise_error(ctl, KP_DEV_ERR_TIMEOUT, 99);
+      return;
+    }
+  }
+}
+
+}  // namespace kp
+
+using namespace kp;
+
+// ---------------------------------------------------------------------------
+// arena layout
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kStatsCap = 4096;
+constexpr int kFirstRows = 256;  // trajectory rows read with the header
+
+struct Dims {
+  int sys, D, N, R, R_pad, n_sub_per, t_e, boxes_pad;
+  size_t n_sub;
+};
+
+struct Layout {
+  size_t ctl, boxes, st, parent, ctrl, steps, region, sub, in_ve, cst, cctrl, ck, cr, cs, flags,
+      n_valid, n_invalid, cov, avail, visited, claim, score, thr, ve, blk_a, blk_b, chunk_sum,
+      stats, traj, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout make_layout(const Dims& d) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  const size_t te = (size_t)d.t_e;
+  L.ctl = take(sizeof(KCtl));
+  L.boxes = take((size_t)KP_MAX_BOXES * 32);  // room for any obstacle set
+  L.st = take(te * d.D * 4);
+  L.parent = take(te * 4);
+  L.ctrl = take(te * d.N * 4);
+  L.steps = take(te);
+  L.region = take(te * 4);
+  L.sub = take(te * 4);
+  L.in_ve = take(te);
+  L.cst = take(te * d.D * 4);
+  L.cctrl = take(te * d.N * 4);
+  L.ck = take(te);
+  L.cr = take(te * 4);
+  L.cs = take(te * 4);
+  L.flags = take(te);
+  L.n_valid = take((size_t)d.R * 4);
+  L.n_invalid = take((size_t)d.R * 4);
+  L.cov = take((size_t)d.R * 4);
+  L.avail = take((size_t)d.R);
+  L.visited = take(d.n_sub);
+  L.claim = take(d.n_sub * 4);
+  L.score = take((size_t)d.R * 8);
+  L.thr = take((size_t)d.R * 8);
+  L.ve = take(te * 4);
+  L.blk_a = take((size_t)KP_MAX_GRID * 4);
+  L.blk_b = take((size_t)KP_MAX_GRID * 4);
+  L.chunk_sum = take((size_t)KP_MAX_GRID * 8);
+  L.stats = take((size_t)kStatsCap * sizeof(KStats));
+  L.traj = take((size_t)KP_TRAJ_ROWS * 17 * 4);
+  L.total = off;
+  return L;
+}
+
+bool finite_or_inf(float v) { return !std::isnan(v); }
+
+// Validates the inputs; fills dims.  Returns an error message or nullptr.
+const char* check_inputs(const kp_system* sys, const kp_workspace* ws, int32_t n_boxes,
+                         const kp_params* prm, Dims* d) {
+  if (!sys || !ws || !prm) return "null argument";
+  if (sys->id < 0 || sys->id > 2) return "unknown system id";
+  if (!(sys->dt > 0.0f) || !std::isfinite(sys->dt)) return "dt must be positive";
+  if (sys->k_min < 1 || sys->k_max < sys->k_min || sys->k_max > 255) return "bad k range";
+  d->sys = sys->id;
+  d->D = sys->id == KP_QUADROTOR_12D ? 12 : 6;
+  d->N = sys->id == KP_QUADROTOR_12D ? 4 : 3;
+  for (int i = 0; i < d->D; ++i)
+    if (!finite_or_inf(sys->x_lo[i]) || !finite_or_inf(sys->x_hi[i]) ||
+        !(sys->x_lo[i] <= sys->x_hi[i]))
+      return "bad state bounds";
+  for (int i = 0; i < d->N; ++i)
+    if (!std::isfinite(sys->u_lo[i]) || !std::isfinite(sys->u_hi[i]) ||
+        !(sys->u_lo[i] <= sys->u_hi[i]))
+      return "bad control bounds";
+  for (int a = 0; a < 3; ++a) {
+    if (!std::isfinite(ws->lo[a]) || !std::isfinite(ws->hi[a]) || !(ws->lo[a] < ws->hi[a]))
+      return "bad workspace";
+    if (ws->grid[a] < 1 || ws->sub[a] < 1 || ws->grid[a] > 4096 || ws->sub[a] > 4096)
+      return "bad grid";
+  }
+  if (ws->speed_bins < 1 || ws->speed_bins > 4096) return "bad speed bins";
+  if (ws->speed_bins > 1 && !(ws->speed_hi > 0.0f)) return "bad speed range";
+  if (n_boxes < 0 || n_boxes > KP_MAX_BOXES) return "bad box count";
+  if (prm->t_e < 2 || prm->t_e > (1 << 28)) return "t_e out of range";
+  if (prm->lambda_max < 1 || prm->lambda_max > 1024) return "lambda_max out of range";
+  if (!(prm->delta > 0.0) || !(prm->eps > 0.0) || !(prm->eps < 1.0)) return "bad delta/eps";
+  const long long R = (long long)ws->grid[0] * ws->grid[1] * ws->grid[2] * ws->speed_bins;
+  const long long nsp = (long long)ws->sub[0] * ws->sub[1] * ws->sub[2];
+  if (R > (1 << 24) || R * nsp > (1ll << 30)) return "decomposition too large";
+  d->R = (int)R;
+  d->R_pad = 1;
+  while (d->R_pad < d->R) d->R_pad *= 2;
+  d->n_sub_per = (int)nsp;
+  d->n_sub = (size_t)(R * nsp);
+  d->t_e = prm->t_e;
+  d->boxes_pad = (n_boxes + 7) / 8 * 8;
+  return nullptr;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+struct kp_ctx {
+  Dims dims;
+  Layout lay;
+  kp_system sys;
+  kp_workspace ws;
+  kp_params prm;
+  int n_boxes_cap;
+  char* arena;
+  size_t arena_bytes;
+  cudaStream_t stream;
+  int device;
+  int num_sms;
+  KParams P;  // pointers and constants; goal/seed/log per launch
+  kp_goal goal;
+  uint64_t seed;
+  bool have_tree;
+  bool poisoned;
+  bool log_on;
+  KLog log;
+  uint64_t wait_ns;
+  int grid[2];
+  size_t smem;
+  std::string err;
+  void* pinned;
+  size_t pinned_bytes;
+  cudaEvent_t ev_loop0, ev_loop1;  // bracket every loop-kernel launch
+  bool loop_timed;
+  bool plan_pending;               // kp_plan_async issued, result not read
+  int plan_rows;
+};
+
+namespace {
+
+kp_status fail(kp_ctx* c, kp_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+    if (s == KP_ERR_CUDA || s == KP_ERR_TIMEOUT) c->poisoned = true;
+  }
+  return s;
+}
+
+#define KP_CUDA(call)                                                                        \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(ctx, KP_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                 \
+  } while (0)
+
+cudaError_t occupancy(int sys, bool log, size_t smem, int* bps) {
+  switch (sys) {
+    case KP_SYS_DI: return loop_occupancy_di(log, smem, bps);
+    case KP_SYS_DUBINS: return loop_occupancy_dubins(log, smem, bps);
+    default: return loop_occupancy_quad(log, smem, bps);
+  }
+}
+
+cudaError_t launch_loop(kp_ctx* c, const KParams& P, int max_iters, uint64_t max_ns) {
+  const bool log = c->log_on;
+  const int g = c->grid[log ? 1 : 0];
+  cudaError_t e = cudaEventRecord(c->ev_loop0, c->stream);
+  if (e != cudaSuccess) return e;
+  switch (c->dims.sys) {
+    case KP_SYS_DI: e = launch_loop_di(P, g, c->smem, max_iters, max_ns, log, c->stream); break;
+    case KP_SYS_DUBINS:
+      e = launch_loop_dubins(P, g, c->smem, max_iters, max_ns, log, c->stream);
+      break;
+    default: e = launch_loop_quad(P, g, c->smem, max_iters, max_ns, log, c->stream);
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(c->ev_loop1, c->stream);
+  c->loop_timed = e == cudaSuccess;
+  return e;
+}
+
+cudaError_t launch_reset(kp_ctx* c, const KParams& P, const RootState& root) {
+  switch (c->dims.sys) {
+    case KP_SYS_DI: return launch_reset_di(P, root, c->stream);
+    case KP_SYS_DUBINS: return launch_reset_dubins(P, root, c->stream);
+    default: return launch_reset_quad(P, root, c->stream);
+  }
+}
+
+template <class T>
+T* at(kp_ctx* c, size_t off) {
+  return reinterpret_cast<T*>(c->arena + off);
+}
+
+// Launch parameters for the context's current goal, seed and log.
+KParams params_now(kp_ctx* c) {
+  KParams P = c->P;
+  for (int a = 0; a < 3; ++a) P.goal_c[a] = c->goal.center[a];
+  P.goal_r2 = (float)((double)c->goal.radius * (double)c->goal.radius);
+  P.seed_lo = (uint32_t)(c->seed & 0xffffffffu);
+  P.seed_hi = (uint32_t)(c->seed >> 32);
+  P.log = c->log_on ? c->log : KLog{};
+  P.wait_ns = c->wait_ns;
+  return P;
+}
+
+kp_status check_ctx(kp_ctx* c) {
+  if (!c) return KP_ERR_ARG;
+  if (c->poisoned) return KP_ERR_STATE;
+  return KP_OK;
+}
+
+kp_status ensure_pinned(kp_ctx* ctx, size_t bytes) {
+  if (ctx->pinned_bytes >= bytes) return KP_OK;
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  ctx->pinned = nullptr;
+  ctx->pinned_bytes = 0;
+  KP_CUDA(cudaHostAlloc(&ctx->pinned, bytes, cudaHostAllocDefault));
+  ctx->pinned_bytes = bytes;
+  return KP_OK;
+}
+
+// Reads the control block back (synchronises the stream).
+kp_status read_ctl(kp_ctx* ctx, KCtl* out) {
+  kp_status s = ensure_pinned(ctx, sizeof(KCtl));
+  if (s != KP_OK) return s;
+  KP_CUDA(cudaMemcpyAsync(ctx->pinned, at<KCtl>(ctx, ctx->lay.ctl), sizeof(KCtl),
+                          cudaMemcpyDeviceToHost, ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(out, ctx->pinned, sizeof(KCtl));
+  return KP_OK;
+}
+
+kp_status configure_launch(kp_ctx* ctx);
+
+kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
+  const int nb = obs ? obs->n_boxes : 0;
+  if (nb < 0 || nb > ctx->n_boxes_cap) return fail(ctx, KP_ERR_ARG, "box count above capacity");
+  if (nb > 0 && !obs->boxes) return fail(ctx, KP_ERR_ARG, "null boxes");
+  const int pad = (nb + 7) / 8 * 8;
+  // stage the padded rows in pinned host memory, then one async copy
+  kp_status ps = ensure_pinned(ctx, (size_t)pad * 32 + sizeof(KCtl));
+  if (ps != KP_OK) return ps;
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));  // the staging buffer is free
+  float* host = static_cast<float*>(ctx->pinned);
+  for (int b = 0; b < pad; ++b) {
+    float* o = host + (size_t)b * 8;
+    if (b < nb) {
+      const float* in = obs->boxes + (size_t)b * 6;
+      for (int i = 0; i < 6; ++i)
+        if (std::isnan(in[i])) return fail(ctx, KP_ERR_ARG, "NaN in box %d", b);
+      o[0] = in[0]; o[1] = in[1]; o[2] = in[2]; o[3] = 0.0f;
+      o[4] = in[3]; o[5] = in[4]; o[6] = in[5]; o[7] = 0.0f;
+    } else {  // padding: an empty box no hull can meet
+      o[0] = o[1] = o[2] = INFINITY;
+      o[4] = o[5] = o[6] = -INFINITY;
+      o[3] = o[7] = 0.0f;
+    }
+  }
+  if (pad > 0)
+    KP_CUDA(cudaMemcpyAsync(ctx->arena + ctx->lay.boxes, host, (size_t)pad * 32,
+                            cudaMemcpyHostToDevice, ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->P.n_boxes_pad = pad;
+  ctx->dims.boxes_pad = pad;
+  ctx->have_tree = false;
+  return configure_launch(ctx);
+}
+
+kp_status configure_launch(kp_ctx* ctx) {
+  const Dims& d = ctx->dims;
+  // shared memory: boxes + the double scratch of the region-score sums
+  const int min_ch = d.R_pad / (d.R_pad < 128 ? d.R_pad : 128);
+  const int sd = min_ch > 1024 ? min_ch : 1024;
+  ctx->smem = (size_t)d.boxes_pad * 32 + (size_t)sd * 8;
+  for (int log = 0; log < 2; ++log) {
+    int bps = 0;
+    KP_CUDA(occupancy(d.sys, log != 0, ctx->smem, &bps));
+    if (bps < 1) return fail(ctx, KP_ERR_ARG, "loop kernel cannot be resident");
+    int g = bps * ctx->num_sms;
+    if (g > KP_MAX_GRID) g = KP_MAX_GRID;
+    ctx->grid[log] = g;
+  }
+  // region chunks: a power of two <= the smaller grid, <= R_pad, <= 1024
+  const int gmin = ctx->grid[0] < ctx->grid[1] ? ctx->grid[0] : ctx->grid[1];
+  int nch = 1;
+  while (nch * 2 <= gmin && nch * 2 <= d.R_pad && nch * 2 <= 1024) nch *= 2;
+  ctx->P.nch = nch;
+  return KP_OK;
+}
+
+kp_status clear_tables(kp_ctx* ctx) {
+  const Dims& d = ctx->dims;
+  const Layout& L = ctx->lay;
+  KP_CUDA(cudaMemsetAsync(ctx->arena + L.visited, 0, d.n_sub, ctx->stream));
+  KP_CUDA(cudaMemsetAsync(ctx->arena + L.claim, 0xff, d.n_sub * 4, ctx->stream));
+  KP_CUDA(cudaMemsetAsync(ctx->arena + L.n_valid, 0, (size_t)d.R * 4, ctx->stream));
+  KP_CUDA(cudaMemsetAsync(ctx->arena + L.n_invalid, 0, (size_t)d.R * 4, ctx->stream));
+  KP_CUDA(cudaMemsetAsync(ctx->arena + L.cov, 0, (size_t)d.R * 4, ctx->stream));
+  KP_CUDA(cudaMemsetAsync(ctx->arena + L.avail, 0, (size_t)d.R, ctx->stream));
+  return KP_OK;
+}
+
+kp_status enqueue_reset(kp_ctx* ctx, const float* x_init) {
+  for (int i = 0; i < ctx->dims.D; ++i)
+    if (std::isnan(x_init[i])) return fail(ctx, KP_ERR_ARG, "NaN in x_init");
+  kp_status s = clear_tables(ctx);
+  if (s != KP_OK) return s;
+  RootState root{};
+  for (int i = 0; i < ctx->dims.D; ++i) root.x[i] = x_init[i];
+  KParams P = params_now(ctx);
+  KP_CUDA(launch_reset(ctx, P, root));
+  ctx->have_tree = true;
+  return KP_OK;
+}
+
+kp_status check_launch(kp_ctx* ctx, const KCtl& h) {
+  if (h.err == KP_DEV_ERR_TIMEOUT)
+    return fail(ctx, KP_ERR_TIMEOUT, "device wait exceeded %llu ns (site %d)",
+                (unsigned long long)ctx->wait_ns, h.err_where);
+  if (h.err != 0) return fail(ctx, KP_ERR_CUDA, "device error %d", h.err);
+  return KP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t kp_required_bytes(const kp_system* sys, const kp_workspace* ws, int32_t n_boxes,
+                         const kp_params* prm) {
+  Dims d{};
+  if (check_inputs(sys, ws, n_boxes, prm, &d)) return 0;
+  return make_layout(d).total;
+}
+
+kp_status kp_create(const kp_system* sys, const kp_workspace* ws, const kp_obstacles* obs,
+                    const kp_params* prm, void* dev_arena, size_t arena_bytes, void* cuda_stream,
+                    kp_ctx** out) {
+  if (!out) return KP_ERR_ARG;
+  *out = nullptr;
+  Dims d{};
+  const int nb = obs ? obs->n_boxes : 0;
+  if (check_inputs(sys, ws, nb, prm, &d)) return KP_ERR_ARG;
+  if (!dev_arena || ((uintptr_t)dev_arena & 255u)) return KP_ERR_ARG;
+  const Layout lay = make_layout(d);
+  if (arena_bytes < lay.total) return KP_ERR_OOM;
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, dev_arena) != cudaSuccess ||
+      attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return KP_ERR_ARG;
+  }
+
+  kp_ctx* ctx = new (std::nothrow) kp_ctx();
+  if (!ctx) return KP_ERR_OOM;
+  ctx->dims = d;
+  ctx->lay = lay;
+  ctx->sys = *sys;
+  ctx->ws = *ws;
+  ctx->prm = *prm;
+  ctx->n_boxes_cap = KP_MAX_BOXES;
+  ctx->arena = static_cast<char*>(dev_arena);
+  ctx->arena_bytes = arena_bytes;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->device = attr.device;
+  ctx->seed = prm->seed;
+  ctx->wait_ns = 2000000000ull;
+  ctx->goal = kp_goal{{0, 0, 0}, 0};
+  kp_status s = KP_OK;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != ctx->device ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      delete ctx;
+      return KP_ERR_CUDA;
+    }
+  }
+
+  KParams& P = ctx->P;
+  P = KParams{};
+  P.sys = d.sys;
+  P.dt = sys->dt;
+  P.k_min = sys->k_min;
+  P.k_span = (uint32_t)(sys->k_max - sys->k_min + 1);
+  for (int i = 0; i < 12; ++i) {
+    P.x_lo[i] = i < d.D ? sys->x_lo[i] : -INFINITY;
+    P.x_hi[i] = i < d.D ? sys->x_hi[i] : INFINITY;
+  }
+  for (int i = 0; i < 4; ++i) {
+    P.u_lo[i] = sys->u_lo[i];
+    P.u_scale[i] = sys->u_hi[i] - sys->u_lo[i];
+  }
+  for (int i = 0; i < 16; ++i) P.phys[i] = sys->phys[i];
+  double vol = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    P.ws_lo[a] = ws->lo[a];
+    P.n_fine[a] = ws->grid[a] * ws->sub[a];
+    P.fine_scale[a] = (float)((double)P.n_fine[a] / ((double)ws->hi[a] - (double)ws->lo[a]));
+    P.sub[a] = ws->sub[a];
+    P.grid[a] = ws->grid[a];
+    vol *= ((double)ws->hi[a] - (double)ws->lo[a]) / (double)ws->grid[a];
+  }
+  P.speed_bins = ws->speed_bins;
+  P.speed_scale = ws->speed_bins > 1 ? (float)((double)ws->speed_bins / (double)ws->speed_hi) : 0.0f;
+  P.n_sub_per = d.n_sub_per;
+  P.R = d.R;
+  P.R_pad = d.R_pad;
+  P.t_e = d.t_e;
+  P.lambda_max = prm->lambda_max;
+  P.delta = prm->delta;
+  P.eps = prm->eps;
+  P.vol = vol;
+  char* A = ctx->arena;
+  P.boxes = reinterpret_cast<const float*>(A + lay.boxes);
+  P.st = reinterpret_cast<float*>(A + lay.st);
+  P.parent = reinterpret_cast<int32_t*>(A + lay.parent);
+  P.ctrl = reinterpret_cast<float*>(A + lay.ctrl);
+  P.steps = reinterpret_cast<uint8_t*>(A + lay.steps);
+  P.region = reinterpret_cast<int32_t*>(A + lay.region);
+  P.node_sub = reinterpret_cast<int32_t*>(A + lay.sub);
+  P.in_ve = reinterpret_cast<uint8_t*>(A + lay.in_ve);
+  P.cst = reinterpret_cast<float*>(A + lay.cst);
+  P.cctrl = reinterpret_cast<float*>(A + lay.cctrl);
+  P.ck = reinterpret_cast<uint8_t*>(A + lay.ck);
+  P.cr = reinterpret_cast<int32_t*>(A + lay.cr);
+  P.cs = reinterpret_cast<int32_t*>(A + lay.cs);
+  P.flags = reinterpret_cast<uint8_t*>(A + lay.flags);
+  P.n_valid = reinterpret_cast<uint32_t*>(A + lay.n_valid);
+  P.n_invalid = reinterpret_cast<uint32_t*>(A + lay.n_invalid);
+  P.cov = reinterpret_cast<uint32_t*>(A + lay.cov);
+  P.avail = reinterpret_cast<uint8_t*>(A + lay.avail);
+  P.visited = reinterpret_cast<uint8_t*>(A + lay.visited);
+  P.claim = reinterpret_cast<uint32_t*>(A + lay.claim);
+  P.score = reinterpret_cast<double*>(A + lay.score);
+  P.thr = reinterpret_cast<uint64_t*>(A + lay.thr);
+  P.ve = reinterpret_cast<int32_t*>(A + lay.ve);
+  P.blk_a = reinterpret_cast<uint32_t*>(A + lay.blk_a);
+  P.blk_b = reinterpret_cast<uint32_t*>(A + lay.blk_b);
+  P.chunk_sum = reinterpret_cast<double*>(A + lay.chunk_sum);
+  P.ctl = reinterpret_cast<KCtl*>(A + lay.ctl);
+  P.stats = reinterpret_cast<KStats*>(A + lay.stats);
+  P.stats_cap = kStatsCap;
+  P.traj = reinterpret_cast<float*>(A + lay.traj);
+
+  {
+    cudaError_t e = cudaMemsetAsync(A + lay.ctl, 0, sizeof(KCtl), ctx->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev_loop0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev_loop1);
+    if (e != cudaSuccess) s = fail(ctx, KP_ERR_CUDA, "create: %s", cudaGetErrorString(e));
+  }
+  if (s == KP_OK) s = upload_boxes(ctx, obs);
+  if (s != KP_OK) {
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->ev_loop0) cudaEventDestroy(ctx->ev_loop0);
+    if (ctx->ev_loop1) cudaEventDestroy(ctx->ev_loop1);
+    delete ctx;
+    return s;
+  }
+  *out = ctx;
+  return KP_OK;
+}
+
+kp_status kp_set_obstacles(kp_ctx* ctx, const kp_obstacles* obs) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  return upload_boxes(ctx, obs);
+}
+
+kp_status kp_reset(kp_ctx* ctx, const float* x_init, const kp_goal* goal, uint64_t seed) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (!x_init || !goal) return fail(ctx, KP_ERR_ARG, "null argument");
+  if (!(goal->radius >= 0.0f) || std::isnan(goal->center[0]) || std::isnan(goal->center[1]) ||
+      std::isnan(goal->center[2]))
+    return fail(ctx, KP_ERR_ARG, "bad goal");
+  ctx->goal = *goal;
+  ctx->seed = seed;
+  s = enqueue_reset(ctx, x_init);
+  if (s != KP_OK) return s;
+  KCtl h;
+  s = read_ctl(ctx, &h);
+  if (s != KP_OK) return s;
+  if (h.state == KP_DEV_BAD_ROOT) {
+    ctx->have_tree = false;
+    return fail(ctx, KP_ERR_ARG, "x_init is not a valid state");
+  }
+  return KP_OK;
+}
+
+kp_status kp_expand_step(kp_ctx* ctx, int32_t n_iters, kp_iter_stats* out, int32_t* n_run) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (n_run) *n_run = 0;
+  if (!ctx->have_tree) return fail(ctx, KP_ERR_STATE, "no tree: call kp_reset first");
+  if (n_iters < 1 || n_iters > kStatsCap) return fail(ctx, KP_ERR_ARG, "n_iters out of range");
+  KParams P = params_now(ctx);
+  KP_CUDA(launch_loop(ctx, P, n_iters, 0));
+  KCtl h;
+  s = read_ctl(ctx, &h);
+  if (s != KP_OK) return s;
+  s = check_launch(ctx, h);
+  if (s != KP_OK) return s;
+  if (n_run) *n_run = h.n_run;
+  if (out && h.n_run > 0) {
+    static_assert(sizeof(KStats) == sizeof(kp_iter_stats), "stats layout");
+    KP_CUDA(cudaMemcpyAsync(out, ctx->arena + ctx->lay.stats, sizeof(KStats) * h.n_run,
+                            cudaMemcpyDeviceToHost, ctx->stream));
+    KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  return KP_OK;
+}
+
+kp_status kp_plan_async(kp_ctx* ctx, const float* x_init, const kp_goal* goal,
+                        const kp_budget* budget, int32_t traj_capacity) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (!x_init || !goal || !budget) return fail(ctx, KP_ERR_ARG, "null argument");
+  if (budget->max_iters < 1) return fail(ctx, KP_ERR_ARG, "max_iters must be >= 1");
+  if (traj_capacity < 0) return fail(ctx, KP_ERR_ARG, "negative capacity");
+  if (!(goal->radius >= 0.0f) || std::isnan(goal->center[0]) || std::isnan(goal->center[1]) ||
+      std::isnan(goal->center[2]))
+    return fail(ctx, KP_ERR_ARG, "bad goal");
+  const int rows = traj_capacity < KP_TRAJ_ROWS ? traj_capacity : KP_TRAJ_ROWS;
+  const size_t traj_bytes = (size_t)rows * 17 * 4;
+  // every copy through the staging buffer completes before its call
+  // returns, so it is free here
+  if (ctx->plan_pending) return fail(ctx, KP_ERR_STATE, "kp_plan_result not called");
+  s = ensure_pinned(ctx, sizeof(KCtl) + traj_bytes);
+  if (s != KP_OK) return s;
+  ctx->goal = *goal;
+  s = enqueue_reset(ctx, x_init);
+  if (s != KP_OK) return s;
+  KParams P = params_now(ctx);
+  const uint64_t max_ns = budget->max_ms > 0.0 ? (uint64_t)(budget->max_ms * 1e6) : 0ull;
+  KP_CUDA(launch_loop(ctx, P, budget->max_iters, max_ns));
+  kp_extract_kernel<<<1, 32, 0, ctx->stream>>>(P);
+  KP_CUDA(cudaGetLastError());
+  ctx->plan_pending = true;
+  ctx->plan_rows = rows;
+  return KP_OK;
+}
+
+kp_status kp_plan_result(kp_ctx* ctx, kp_traj* traj) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (!traj) return fail(ctx, KP_ERR_ARG, "null argument");
+  if (!ctx->plan_pending) return fail(ctx, KP_ERR_STATE, "no kp_plan_async pending");
+  const int rows = ctx->plan_rows < traj->capacity ? ctx->plan_rows : traj->capacity;
+  if (rows > 0 && (!traj->states || !traj->ctrls || !traj->steps))
+    return fail(ctx, KP_ERR_ARG, "bad trajectory buffers");
+  ctx->plan_pending = false;
+  // header and the first rows in one round trip; longer chains in a second
+  const int first = rows < kFirstRows ? rows : kFirstRows;
+  char* pin = static_cast<char*>(ctx->pinned);
+  float* prow = reinterpret_cast<float*>(pin + sizeof(KCtl));
+  KP_CUDA(cudaMemcpyAsync(pin, ctx->arena + ctx->lay.ctl, sizeof(KCtl), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  if (first > 0)
+    KP_CUDA(cudaMemcpyAsync(prow, ctx->arena + ctx->lay.traj, (size_t)first * 17 * 4,
+                            cudaMemcpyDeviceToHost, ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  KCtl h;
+  std::memcpy(&h, pin, sizeof(KCtl));
+  if (h.state == KP_DEV_SOLVED && h.n_edges > first && h.n_edges <= rows) {
+    KP_CUDA(cudaMemcpyAsync(prow + (size_t)first * 17,
+                            ctx->arena + ctx->lay.traj + (size_t)first * 17 * 4,
+                            (size_t)(h.n_edges - first) * 17 * 4, cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  s = check_launch(ctx, h);
+  if (s != KP_OK) return s;
+  if (h.state == KP_DEV_BAD_ROOT) {
+    ctx->have_tree = false;
+    return fail(ctx, KP_ERR_ARG, "x_init is not a valid state");
+  }
+  traj->n_edges = 0;
+  if (h.state != KP_DEV_SOLVED || h.n_edges < 0) return KP_NO_SOLUTION;
+  traj->n_edges = h.n_edges;
+  if (h.n_edges > rows) return fail(ctx, KP_ERR_ARG, "trajectory needs %d rows", h.n_edges);
+  const float* src = prow;
+  for (int e = 0; e < h.n_edges; ++e) {
+    std::memcpy(traj->states + (size_t)e * 12, src + (size_t)e * 17, 12 * 4);
+    std::memcpy(traj->ctrls + (size_t)e * 4, src + (size_t)e * 17 + 12, 4 * 4);
+    traj->steps[e] = (int32_t)src[(size_t)e * 17 + 16];
+  }
+  return KP_OK;
+}
+
+kp_status kp_plan(kp_ctx* ctx, const float* x_init, const kp_goal* goal, const kp_budget* budget,
+                  kp_traj* traj) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (!traj || traj->capacity < 0) return fail(ctx, KP_ERR_ARG, "bad trajectory");
+  s = kp_plan_async(ctx, x_init, goal, budget, traj->capacity);
+  if (s != KP_OK) return s;
+  return kp_plan_result(ctx, traj);
+}
+
+kp_status kp_get_info(kp_ctx* ctx, kp_info* out) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (!out) return KP_ERR_ARG;
+  KCtl h;
+  s = read_ctl(ctx, &h);
+  if (s != KP_OK) return s;
+  out->n_nodes = ctx->have_tree ? h.n_nodes : 0;
+  out->n_ve = ctx->have_tree ? h.n_ve : 0;
+  out->iteration = h.iteration;
+  out->goal_node = h.goal_node == KP_NO_GOAL ? -1 : h.goal_node;
+  out->state = ctx->have_tree ? (h.state == KP_DEV_BAD_ROOT ? -1 : h.state) : -1;
+  out->n_regions = ctx->dims.R;
+  out->n_subregions = (int32_t)ctx->dims.n_sub;
+  out->state_dim = ctx->dims.D;
+  out->control_dim = ctx->dims.N;
+  out->n_samples = ctx->have_tree ? (int64_t)h.tot_samples : 0;
+  out->n_steps = ctx->have_tree ? (int64_t)h.tot_steps : 0;
+  out->n_hull_checks = ctx->have_tree ? (int64_t)h.tot_hull : 0;
+  out->n_boxes = ctx->P.n_boxes_pad;
+  out->grid_blocks = ctx->grid[ctx->log_on ? 1 : 0];
+  return KP_OK;
+}
+
+kp_status kp_export_tree(kp_ctx* ctx, kp_tree_view* v) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (!v) return KP_ERR_ARG;
+  if (!ctx->have_tree) return fail(ctx, KP_ERR_STATE, "no tree");
+  KCtl h;
+  s = read_ctl(ctx, &h);
+  if (s != KP_OK) return s;
+  const int n = h.n_nodes, D = ctx->dims.D, N = ctx->dims.N, te = ctx->dims.t_e;
+  v->n_nodes = n;
+  v->iteration = h.iteration;
+  if (n > v->capacity) return fail(ctx, KP_ERR_ARG, "view holds %d nodes, tree has %d", v->capacity, n);
+  const Layout& L = ctx->lay;
+  auto d2h = [&](void* dst, size_t off, size_t bytes) -> kp_status {
+    if (!dst || !bytes) return KP_OK;
+    KP_CUDA(cudaMemcpyAsync(dst, ctx->arena + off, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    return KP_OK;
+  };
+  std::vector<float> st((size_t)D * n), ct((size_t)N * n);
+  std::vector<uint8_t> steps(n);
+  for (int i = 0; i < D; ++i)
+    if ((s = d2h(st.data() + (size_t)i * n, L.st + (size_t)i * te * 4, (size_t)n * 4)) != KP_OK) return s;
+  for (int i = 0; i < N; ++i)
+    if ((s = d2h(ct.data() + (size_t)i * n, L.ctrl + (size_t)i * te * 4, (size_t)n * 4)) != KP_OK) return s;
+  if ((s = d2h(steps.data(), L.steps, n)) != KP_OK) return s;
+  if ((s = d2h(v->parent, L.parent, (size_t)n * 4)) != KP_OK) return s;
+  if ((s = d2h(v->region, L.region, (size_t)n * 4)) != KP_OK) return s;
+  if ((s = d2h(v->sub, L.sub, (size_t)n * 4)) != KP_OK) return s;
+  if ((s = d2h(v->in_ve, L.in_ve, (size_t)n)) != KP_OK) return s;
+  const size_t R = ctx->dims.R;
+  if ((s = d2h(v->n_valid, L.n_valid, R * 4)) != KP_OK) return s;
+  if ((s = d2h(v->n_invalid, L.n_invalid, R * 4)) != KP_OK) return s;
+  if ((s = d2h(v->cov, L.cov, R * 4)) != KP_OK) return s;
+  if ((s = d2h(v->avail, L.avail, R)) != KP_OK) return s;
+  if ((s = d2h(v->thr, L.thr, R * 8)) != KP_OK) return s;
+  if ((s = d2h(v->visited, L.visited, ctx->dims.n_sub)) != KP_OK) return s;
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int u = 0; u < n; ++u) {
+    if (v->state)
+      for (int i = 0; i < 12; ++i) v->state[(size_t)u * 12 + i] = i < D ? st[(size_t)i * n + u] : 0.0f;
+    if (v->ctrl)
+      for (int i = 0; i < 4; ++i) v->ctrl[(size_t)u * 4 + i] = i < N ? ct[(size_t)i * n + u] : 0.0f;
+    if (v->steps) v->steps[u] = steps[u];
+  }
+  return KP_OK;
+}
+
+kp_status kp_import_tree(kp_ctx* ctx, const kp_tree_view* v) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (!v || !v->state || !v->parent || !v->ctrl || !v->steps || !v->region || !v->sub ||
+      !v->in_ve || !v->n_valid || !v->n_invalid || !v->thr || !v->visited)
+    return fail(ctx, KP_ERR_ARG, "null array in tree view");
+  const int n = v->n_nodes, D = ctx->dims.D, N = ctx->dims.N, te = ctx->dims.t_e;
+  if (n < 1 || n > te || v->iteration < 0) return fail(ctx, KP_ERR_ARG, "bad node count");
+  const int R = ctx->dims.R;
+  for (int u = 0; u < n; ++u) {
+    if (v->region[u] < 0 || v->region[u] >= R || v->sub[u] < 0 ||
+        (size_t)v->sub[u] >= ctx->dims.n_sub || v->parent[u] >= u || (u > 0 && v->parent[u] < 0) ||
+        v->steps[u] < 0 || v->steps[u] > 255)
+      return fail(ctx, KP_ERR_ARG, "bad node %d", u);
+  }
+  const Layout& L = ctx->lay;
+  std::vector<float> st((size_t)D * n), ct((size_t)N * n);
+  std::vector<uint8_t> steps(n), inve(n);
+  for (int u = 0; u < n; ++u) {
+    for (int i = 0; i < D; ++i) st[(size_t)i * n + u] = v->state[(size_t)u * 12 + i];
+    for (int i = 0; i < N; ++i) ct[(size_t)i * n + u] = v->ctrl[(size_t)u * 4 + i];
+    steps[u] = (uint8_t)v->steps[u];
+    inve[u] = v->in_ve[u] ? 1 : 0;
+  }
+  auto h2d = [&](size_t off, const void* src, size_t bytes) -> kp_status {
+    KP_CUDA(cudaMemcpyAsync(ctx->arena + off, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    return KP_OK;
+  };
+  for (int i = 0; i < D; ++i)
+    if ((s = h2d(L.st + (size_t)i * te * 4, st.data() + (size_t)i * n, (size_t)n * 4)) != KP_OK) return s;
+  for (int i = 0; i < N; ++i)
+    if ((s = h2d(L.ctrl + (size_t)i * te * 4, ct.data() + (size_t)i * n, (size_t)n * 4)) != KP_OK) return s;
+  if ((s = h2d(L.steps, steps.data(), n)) != KP_OK) return s;
+  if ((s = h2d(L.in_ve, inve.data(), n)) != KP_OK) return s;
+  if ((s = h2d(L.parent, v->parent, (size_t)n * 4)) != KP_OK) return s;
+  if ((s = h2d(L.region, v->region, (size_t)n * 4)) != KP_OK) return s;
+  if ((s = h2d(L.sub, v->sub, (size_t)n * 4)) != KP_OK) return s;
+  if ((s = h2d(L.n_valid, v->n_valid, (size_t)R * 4)) != KP_OK) return s;
+  if ((s = h2d(L.n_invalid, v->n_invalid, (size_t)R * 4)) != KP_OK) return s;
+  if ((s = h2d(L.thr, v->thr, (size_t)R * 8)) != KP_OK) return s;
+  if ((s = h2d(L.visited, v->visited, ctx->dims.n_sub)) != KP_OK) return s;
+  KP_CUDA(cudaMemsetAsync(ctx->arena + L.claim, 0xff, ctx->dims.n_sub * 4, ctx->stream));
+  KParams P = params_now(ctx);
+  kp_import_regions_kernel<<<(R + 255) / 256 < 1024 ? (R + 255) / 256 : 1024, 256, 0, ctx->stream>>>(P);
+  KP_CUDA(cudaGetLastError());
+  kp_import_avail_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, ctx->stream>>>(P, n);
+  KP_CUDA(cudaGetLastError());
+  KCtl h{};
+  h.n_nodes = n;
+  h.n_ve = 0;
+  h.iteration = v->iteration;
+  h.goal_node = KP_NO_GOAL;
+  h.state = KP_DEV_RUNNING;
+  // keep the barrier generation the device already holds
+  kp_status rs = ensure_pinned(ctx, sizeof(KCtl));
+  if (rs != KP_OK) return rs;
+  KP_CUDA(cudaMemcpyAsync(ctx->pinned, ctx->arena + L.ctl, sizeof(KCtl), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  KCtl cur;
+  std::memcpy(&cur, ctx->pinned, sizeof(KCtl));
+  h.bar_gen = cur.bar_gen;
+  std::memcpy(ctx->pinned, &h, sizeof(KCtl));
+  KP_CUDA(cudaMemcpyAsync(ctx->arena + L.ctl, ctx->pinned, sizeof(KCtl), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->have_tree = true;
+  return KP_OK;
+}
+
+kp_status kp_set_sample_log(kp_ctx* ctx, const kp_sample_log* log) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (!log) {
+    ctx->log_on = false;
+    ctx->log = KLog{};
+    return KP_OK;
+  }
+  if (log->capacity < 0 || !log->node || !log->k || !log->uraw || !log->flags ||
+      !log->fail_step || !log->region || !log->sub || !log->state)
+    return fail(ctx, KP_ERR_ARG, "bad sample log");
+  ctx->log = KLog{log->capacity, log->node, log->k, log->uraw, log->flags, log->fail_step,
+                  log->region, log->sub, log->state};
+  ctx->log_on = true;
+  return KP_OK;
+}
+
+kp_status kp_set_wait_limit(kp_ctx* ctx, uint64_t ns) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (ns < 1000) return fail(ctx, KP_ERR_ARG, "wait limit below 1 us");
+  ctx->wait_ns = ns;
+  return KP_OK;
+}
+
+kp_status kp_selftest_wait_timeout(kp_ctx* ctx) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  KP_CUDA(cudaMemsetAsync(ctx->arena + ctx->lay.ctl + offsetof(KCtl, never_set), 0, 4, ctx->stream));
+  KP_CUDA(cudaMemsetAsync(ctx->arena + ctx->lay.ctl + offsetof(KCtl, err), 0, 8, ctx->stream));
+  KParams P = params_now(ctx);
+  kp_wait_selftest_kernel<<<1, 32, 0, ctx->stream>>>(P);
+  KP_CUDA(cudaGetLastError());
+  KCtl h;
+  s = read_ctl(ctx, &h);
+  if (s != KP_OK) return s;
+  return check_launch(ctx, h);
+}
+
+const char* kp_last_error(const kp_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+void kp_destroy(kp_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->ev_loop0) cudaEventDestroy(ctx->ev_loop0);
+  if (ctx->ev_loop1) cudaEventDestroy(ctx->ev_loop1);
+  delete ctx;
+}
+
+kp_status kp_last_launch_ms(kp_ctx* ctx, float* ms) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (!ms) return KP_ERR_ARG;
+  if (!ctx->loop_timed) return fail(ctx, KP_ERR_STATE, "no loop launch recorded");
+  KP_CUDA(cudaEventSynchronize(ctx->ev_loop1));
+  KP_CUDA(cudaEventElapsedTime(ms, ctx->ev_loop0, ctx->ev_loop1));
+  return KP_OK;
+}
+
+}  // extern "C"

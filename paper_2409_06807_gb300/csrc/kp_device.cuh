@@ -1,0 +1,346 @@
+// kp_device.cuh -- device-side building blocks of the GB300 Kino-PAX planner:
+// launch parameters, the device control block, the Philox4x32-10 stream, the
+// bounded grid barrier, block scans and the three systems' integrators.
+#pragma once
+
+#include <cstdint>
+
+#include "kp_layout.h"
+
+namespace kp {
+
+// ---------------------------------------------------------------------------
+// time and bounded waits
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Records the first error of a launch (0 -> code).
+__device__ __forceinline__ void raise_error(KCtl* ctl, int code, int where) {
+  if (atomicCAS(&ctl->err, 0, code) == 0) ctl->err_where = where;
+}
+
+// Grid-wide barrier for a cooperative launch.  Every wait is bounded by
+// 'limit_ns' of device time; on expiry the block records KP_ERR_TIMEOUT and
+// all blocks leave at their next barrier.  Returns false when the launch
+// must stop.  Sense is carried by a generation counter: a block reads the
+// generation, arrives, and the last arriver resets the count and publishes
+// the next generation with release semantics.
+__device__ __forceinline__ bool grid_sync(KCtl* ctl, uint32_t nblocks, uint64_t limit_ns,
+                                          int where) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    uint32_t gen = ld_acquire(&ctl->bar_gen);
+    __threadfence();
+    uint32_t ticket = atomicAdd(&ctl->bar_count, 1u);
+    if (ticket == nblocks - 1) {
+      ctl->bar_count = 0;
+      __threadfence();
+      st_release(&ctl->bar_gen, gen + 1);
+    } else {
+      const uint64_t t0 = global_ns();
+      uint32_t spins = 0;
+      while (ld_acquire(&ctl->bar_gen) == gen) {
+        if ((++spins & 63u) == 0) {
+          if (*((volatile int*)&ctl->err) != 0) { ok = 0; break; }
+          if (global_ns() - t0 > limit_ns) {
+            raise_error(ctl, KP_DEV_ERR_TIMEOUT, where);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+    if (ok && *((volatile int*)&ctl->err) != 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// block-level scans over one flag per thread (blockDim.x multiple of 32)
+// ---------------------------------------------------------------------------
+
+struct ScanSmem {
+  int warp[33];
+};
+
+// Exclusive rank of 'flag' among the block's threads in thread order; total
+// set in *total.  Must be called by every thread of the block.
+__device__ __forceinline__ int block_rank(bool flag, ScanSmem& sm, int* total) {
+  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  int r = __popc(m & ((1u << lane) - 1u));
+  if (lane == 0) sm.warp[w] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) {
+      int c = sm.warp[i];
+      sm.warp[i] = acc;
+      acc += c;
+    }
+    sm.warp[32] = acc;
+  }
+  __syncthreads();
+  r += sm.warp[w];
+  *total = sm.warp[32];
+  __syncthreads();
+  return r;
+}
+
+// Block sum of two per-thread values.
+__device__ __forceinline__ void block_sum2(unsigned long long a, unsigned long long b,
+                                           unsigned long long* s /*[64]*/,
+                                           unsigned long long* ra, unsigned long long* rb) {
+  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
+    s[w] = a;
+    s[32 + w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long x = 0, y = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      x += s[i];
+      y += s[32 + i];
+    }
+    s[0] = x;
+    s[32] = y;
+  }
+  __syncthreads();
+  *ra = s[0];
+  *rb = s[32];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 bijection,
+// the key advanced by the Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// 24 high bits of a word as a float in [0, 1), exact.
+__device__ __forceinline__ float unit24(uint32_t w) {
+  return __uint2float_rn(w >> 8) * 5.9604644775390625e-08f;
+}
+
+// ---------------------------------------------------------------------------
+// systems (Sec. II, Eq. 1-2), FP32 in registers
+// ---------------------------------------------------------------------------
+
+template <int SYS>
+struct System;
+
+// 6D double integrator: p' = v, v' = u; explicit Euler.
+template <>
+struct System<KP_SYS_DI> {
+  static constexpr int D = 6, N = 3;
+  __device__ __forceinline__ static void step(float* x, const float* u, float h,
+                                              const KParams&) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float p = x[i] + h * x[3 + i];
+      const float v = x[3 + i] + h * u[i];
+      x[i] = p;
+      x[3 + i] = v;
+    }
+  }
+  __device__ __forceinline__ static float speed(const float* x) {
+    return sqrtf(x[3] * x[3] + x[4] * x[4] + x[5] * x[5]);
+  }
+};
+
+// 6D Dubins airplane (Chitsaz & LaValle 2007); classic RK4.
+template <>
+struct System<KP_SYS_DUBINS> {
+  static constexpr int D = 6, N = 3;
+  __device__ __forceinline__ static void f(const float* x, const float* u, float* dx) {
+    float sp, cp, st, ct;
+    sincosf(x[3], &sp, &cp);
+    sincosf(x[4], &st, &ct);
+    dx[0] = x[5] * cp * ct;
+    dx[1] = x[5] * sp * ct;
+    dx[2] = x[5] * st;
+    dx[3] = u[0];
+    dx[4] = u[1];
+    dx[5] = u[2];
+  }
+  __device__ __forceinline__ static void step(float* x, const float* u, float h,
+                                              const KParams&) {
+    float k1[6], k2[6], k3[6], k4[6], t[6];
+    f(x, u, k1);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = x[i] + 0.5f * h * k1[i];
+    f(t, u, k2);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = x[i] + 0.5f * h * k2[i];
+    f(t, u, k3);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = x[i] + h * k3[i];
+    f(t, u, k4);
+    const float h6 = h / 6.0f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] = x[i] + h6 * (k1[i] + 2.0f * k2[i] + 2.0f * k3[i] + k4[i]);
+  }
+  __device__ __forceinline__ static float speed(const float* x) { return fabsf(x[5]); }
+};
+
+// 12D quadrotor, Newton-Euler, plus configuration; classic RK4.
+// x = (p, phi theta psi, v_world, omega_body); u = rotor thrusts T1..T4.
+template <>
+struct System<KP_SYS_QUAD> {
+  static constexpr int D = 12, N = 4;
+  __device__ __forceinline__ static void f(const float* x, const float* u, const KParams& P,
+                                           float* dx) {
+    const float m = P.phys[0], g = P.phys[1], l = P.phys[2], c = P.phys[3];
+    const float Ix = P.phys[4], Iy = P.phys[5], Iz = P.phys[6];
+    float sphi, cphi, sth, cth, sps, cps;
+    sincosf(x[3], &sphi, &cphi);
+    sincosf(x[4], &sth, &cth);
+    sincosf(x[5], &sps, &cps);
+    const float tth = sth / cth;
+    const float p = x[9], q = x[10], r = x[11];
+    dx[0] = x[6];
+    dx[1] = x[7];
+    dx[2] = x[8];
+    dx[3] = p + sphi * tth * q + cphi * tth * r;
+    dx[4] = cphi * q - sphi * r;
+    dx[5] = (sphi * q + cphi * r) / cth;
+    const float thrust = u[0] + u[1] + u[2] + u[3];
+    const float a = thrust / m;
+    dx[6] = a * (cphi * sth * cps + sphi * sps);
+    dx[7] = a * (cphi * sth * sps - sphi * cps);
+    dx[8] = a * (cphi * cth) - g;
+    const float tx = l * (u[1] - u[3]);
+    const float ty = l * (u[2] - u[0]);
+    const float tz = c * (u[0] - u[1] + u[2] - u[3]);
+    const float Lx = Ix * p, Ly = Iy * q, Lz = Iz * r;
+    dx[9] = (tx - (q * Lz - r * Ly)) / Ix;
+    dx[10] = (ty - (r * Lx - p * Lz)) / Iy;
+    dx[11] = (tz - (p * Ly - q * Lx)) / Iz;
+  }
+  __device__ __forceinline__ static void step(float* x, const float* u, float h,
+                                              const KParams& P) {
+    float k1[12], k2[12], k3[12], k4[12], t[12];
+    f(x, u, P, k1);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) t[i] = x[i] + 0.5f * h * k1[i];
+    f(t, u, P, k2);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) t[i] = x[i] + 0.5f * h * k2[i];
+    f(t, u, P, k3);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) t[i] = x[i] + h * k3[i];
+    f(t, u, P, k4);
+    const float h6 = h / 6.0f;
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+      x[i] = x[i] + h6 * (k1[i] + 2.0f * k2[i] + 2.0f * k3[i] + k4[i]);
+  }
+  __device__ __forceinline__ static float speed(const float* x) {
+    return sqrtf(x[6] * x[6] + x[7] * x[7] + x[8] * x[8]);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// decomposition (Sec. III): fine cell per axis, then region and sub-region
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int fine_cell(float t, int n) {
+  // NaN and negatives go to cell 0, the far side is clamped to n - 1
+  return t >= 0.0f ? (t < (float)n ? (int)t : n - 1) : 0;
+}
+
+template <int SYS>
+__device__ __forceinline__ void bin_state(const float* x, const KParams& P, int* region,
+                                          int* sub) {
+  int cell[3], fine[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float t = __fmul_rn(__fsub_rn(x[a], P.ws_lo[a]), P.fine_scale[a]);
+    const int f = fine_cell(t, P.n_fine[a]);
+    cell[a] = f / P.sub[a];
+    fine[a] = f - cell[a] * P.sub[a];
+  }
+  int sb = 0;
+  if (P.speed_bins > 1)
+    sb = fine_cell(__fmul_rn(System<SYS>::speed(x), P.speed_scale), P.speed_bins);
+  const int r = cell[0] + P.grid[0] * (cell[1] + P.grid[1] * (cell[2] + P.grid[2] * sb));
+  const int k = fine[0] + P.sub[0] * (fine[1] + P.sub[1] * fine[2]);
+  *region = r;
+  *sub = r * P.n_sub_per + k;
+}
+
+// ---------------------------------------------------------------------------
+// validity (Sec. II valid set): state box and segment hull vs closed boxes
+// ---------------------------------------------------------------------------
+
+template <int D>
+__device__ __forceinline__ bool in_state_box(const float* x, const KParams& P) {
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < D; ++i) ok &= (P.x_lo[i] <= x[i]) & (x[i] <= P.x_hi[i]);
+  return ok;
+}
+
+// True when the hull [lo, hi] meets any box.  Boxes sit in shared memory as
+// float4 pairs (lo.xyz, hi.xyz), padded to a multiple of 8 with boxes that
+// can never be met.  Every lane reads the same box (broadcast); a lane
+// leaves after the group of 8 in which it found a hit, and the warp leaves
+// when all its lanes have.
+__device__ __forceinline__ bool hull_hits_boxes(const float4* __restrict__ sb, int n_pad,
+                                                float lx, float ly, float lz, float hx,
+                                                float hy, float hz) {
+  for (int b = 0; b < n_pad; b += 8) {
+    bool hit = false;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 bl = sb[2 * (b + q)];
+      const float4 bh = sb[2 * (b + q) + 1];
+      hit |= (lx <= bh.x) & (bl.x <= hx) & (ly <= bh.y) & (bl.y <= hy) & (lz <= bh.z) &
+             (bl.z <= hz);
+    }
+    if (hit) return true;
+  }
+  return false;
+}
+
+}  // namespace kp

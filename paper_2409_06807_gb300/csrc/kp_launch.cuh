@@ -1,0 +1,44 @@
+// kp_launch.cuh -- host launchers of one system's kernels.  Included once by
+// each kp_sys_*.cu with KP_SYS set, so the three systems compile in
+// parallel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kp_loop.cuh"
+
+#define KP_CAT2(a, b) a##b
+#define KP_CAT(a, b) KP_CAT2(a, b)
+
+namespace kp {
+
+cudaError_t KP_CAT(loop_occupancy_, KP_SYS_NAME)(bool log, size_t smem, int* blocks_per_sm) {
+  const void* f = log ? (const void*)kp_loop_kernel<KP_SYS, true>
+                      : (const void*)kp_loop_kernel<KP_SYS, false>;
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, KP_BLOCK, smem);
+}
+
+cudaError_t KP_CAT(launch_loop_, KP_SYS_NAME)(const KParams& P, int grid, size_t smem,
+                                             int max_iters, uint64_t max_ns, bool log,
+                                             cudaStream_t stream) {
+  KParams p = P;
+  int mi = max_iters;
+  uint64_t mn = max_ns;
+  void* args[] = {&p, &mi, &mn};
+  const void* f = log ? (const void*)kp_loop_kernel<KP_SYS, true>
+                      : (const void*)kp_loop_kernel<KP_SYS, false>;
+  return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(KP_BLOCK), args, smem, stream);
+}
+
+cudaError_t KP_CAT(launch_reset_, KP_SYS_NAME)(const KParams& P, const RootState& root,
+                                              cudaStream_t stream) {
+  int blocks = (P.R + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1024) blocks = 1024;
+  kp_reset_kernel<KP_SYS><<<blocks, 256, 0, stream>>>(P, root);
+  return cudaGetLastError();
+}
+
+}  // namespace kp

@@ -1,0 +1,153 @@
+// kp_layout.h -- layout shared by the host driver and the device kernels:
+// the launch parameter block (KParams), the device control block (KCtl)
+// and the per-sample log pointers (KLog).  Plain C++ (no CUDA types) so the
+// host driver compiles it too.
+#pragma once
+
+#include <cstdint>
+
+namespace kp {
+
+enum { KP_SYS_DI = 0, KP_SYS_DUBINS = 1, KP_SYS_QUAD = 2 };
+
+// planner state stored in KCtl::state
+enum { KP_DEV_RUNNING = 0, KP_DEV_SOLVED = 1, KP_DEV_FULL = 2, KP_DEV_BAD_ROOT = -1 };
+// launch errors stored in KCtl::err
+enum { KP_DEV_OK = 0, KP_DEV_ERR_TIMEOUT = 1 };
+// per-sample flag bits
+enum {
+  KP_F_VALID = 1,
+  KP_F_CONTENDER = 2,
+  KP_F_BERN = 4,
+  KP_F_WINNER = 8,
+  KP_F_ACCEPTED = 16,
+  KP_F_GOAL = 32
+};
+
+constexpr int KP_BLOCK = 256;          // threads per block of the loop kernel
+constexpr int KP_MAX_GRID = 8192;      // upper bound on loop-kernel blocks
+constexpr int KP_NO_GOAL = 0x7fffffff; // goal_node sentinel on the device
+constexpr int KP_TRAJ_ROWS = 16384;    // longest root-to-goal chain returned
+
+// Device control block (one per context, in the arena).
+struct KCtl {
+  // loop state, persistent across launches
+  int32_t n_nodes;     // |T|
+  int32_t n_ve;        // |V_E|
+  int32_t iteration;   // next pass index
+  int32_t goal_node;   // KP_NO_GOAL when none
+  int32_t state;       // KP_DEV_*
+  int32_t err;         // KP_DEV_ERR_* of the last launch
+  int32_t err_where;
+  int32_t n_run;       // passes run by the last launch
+  int32_t stop;        // loop stop flag inside a launch
+  uint32_t it_valid;   // valid samples of the current pass
+  int32_t n_edges;     // trajectory extraction: edges on the chain
+  int32_t pad0[1];
+  // work counters since the last reset (samples, integrator steps run,
+  // segment hulls tested against the obstacle set)
+  unsigned long long tot_samples;
+  unsigned long long tot_steps;
+  unsigned long long tot_hull;
+  // barrier words on their own 128-byte line
+  uint32_t bar_count;
+  uint32_t pad1[31];
+  uint32_t bar_gen;
+  uint32_t pad2[31];
+  // never set: target of the bounded-wait self test
+  uint32_t never_set;
+  uint32_t pad3[31];
+};
+
+struct KLog {
+  int32_t capacity;  // 0 = off
+  int32_t* node;
+  int32_t* k;
+  uint32_t* uraw;    // [cap][4]
+  uint8_t* flags;
+  int32_t* fail_step;
+  int32_t* region;
+  int32_t* sub;
+  float* state;      // [cap][12]
+};
+
+struct KStats {
+  int32_t iteration, n_ve, lambda, n_samples, n_valid, n_accepted, n_nodes, goal_node;
+};
+
+// x_init of a reset, passed by value.
+struct RootState {
+  float x[12];
+};
+
+// Launch parameters (passed by value; ~1 KB).
+struct KParams {
+  // system (Sec. II)
+  int32_t sys;
+  float dt;
+  int32_t k_min;
+  uint32_t k_span;  // k_max - k_min + 1
+  float x_lo[12], x_hi[12];
+  float u_lo[4], u_scale[4];  // u = u_lo + u_scale * r
+  float phys[16];
+  // decomposition (Sec. III)
+  float ws_lo[3];
+  float fine_scale[3];  // fine cells per unit length
+  int32_t n_fine[3];    // grid * sub per axis
+  int32_t sub[3];
+  int32_t grid[3];
+  int32_t speed_bins;
+  float speed_scale;    // speed_bins / speed_hi
+  int32_t n_sub_per;    // n'
+  int32_t R;            // regions
+  int32_t R_pad;        // next power of two >= R
+  int32_t nch;          // region chunks of the score sum (power of two)
+  // goal set
+  float goal_c[3];
+  float goal_r2;
+  // constants
+  int32_t t_e;
+  int32_t lambda_max;
+  double delta, eps, vol;
+  uint32_t seed_lo, seed_hi;
+  // obstacles: [n_boxes_pad][8] floats (lo.xyz, pad, hi.xyz, pad)
+  const float* boxes;
+  int32_t n_boxes_pad;
+  // tree, SoA over t_e nodes
+  float* st;          // [D][t_e]
+  int32_t* parent;
+  float* ctrl;        // [N][t_e]
+  uint8_t* steps;
+  int32_t* region;
+  int32_t* node_sub;  // global sub-region index of each node
+  uint8_t* in_ve;
+  // per-sample candidates, indexed by sample key (< t_e)
+  float* cst;         // [D][t_e]
+  float* cctrl;       // [N][t_e]
+  uint8_t* ck;
+  int32_t* cr;
+  int32_t* cs;
+  uint8_t* flags;
+  // decomposition tables
+  uint32_t* n_valid;
+  uint32_t* n_invalid;
+  uint32_t* cov;
+  uint8_t* avail;
+  uint8_t* visited;   // [R * n']
+  uint32_t* claim;    // [R * n'] smallest sample key, 0xffffffff = none
+  double* score;
+  uint64_t* thr;      // accept iff word < thr
+  // loop scratch
+  int32_t* ve;        // V_E list
+  uint32_t* blk_a;    // [KP_MAX_GRID]
+  uint32_t* blk_b;    // [KP_MAX_GRID]
+  double* chunk_sum;  // [KP_MAX_GRID]
+  KCtl* ctl;
+  KStats* stats;
+  int32_t stats_cap;
+  float* traj;        // [KP_TRAJ_ROWS][17]: state 12, ctrl 4, steps
+  KLog log;
+  uint64_t wait_ns;
+};
+
+}  // namespace kp

@@ -1,0 +1,568 @@
+// kp_loop.cuh -- the Kino-PAX loop as one persistent cooperative kernel, plus
+// the small reset / import / trajectory kernels.  Instantiated once per
+// system by kp_sys_*.cu.
+//
+// One pass of the loop body (Algorithm 1) runs as five grid phases separated
+// by bounded grid barriers, with no host involvement:
+//   E  Propagate (Algorithm 2): one thread per sample (V_E position, j);
+//      draw u and k, integrate k steps in FP32 registers, check each step
+//      against the state box and the obstacle boxes staged in shared memory,
+//      bin the end (or first invalid) state, count n_valid / n_invalid,
+//      claim newly reached sub-regions (smallest sample key wins) and keep
+//      the candidates' payload.
+//   A  accept flags per contiguous key chunk (representative or P_accept
+//      draw) and their per-block counts;
+//   S  Score per region (Eq. 3-4, FP64, rounded exactly as written) and
+//      pairwise partial sums per aligned region chunk (Eq. 5's sum).
+//   P  append the accepted samples in key order (Algorithm 4, new nodes to
+//      T and V_E) with goal test;
+//   T  P_accept and the integer accept threshold per region (Eq. 5).
+//   N  one selection draw per old node against its region's new threshold
+//      (Algorithm 4, V_E <-> V_O) and per-block V_E counts;
+//   L  V_E list in ascending node id, lambda for the next pass (Eq. 6),
+//      stop decision.
+// Phases A+S and P+T share a barrier interval.
+#pragma once
+
+#include <cstdint>
+
+#include "kp_device.cuh"
+
+namespace kp {
+
+struct LoopShared {
+  ScanSmem scan;
+  unsigned long long red[64];
+  uint64_t mbar;
+  int flag;
+};
+
+// Stage the obstacle boxes into shared memory with bulk asynchronous copies
+// (TMA engine) completing on one mbarrier.  Returns false on a wait timeout.
+__device__ __forceinline__ bool stage_boxes(const KParams& P, float4* sbox, LoopShared& sh) {
+  const uint32_t bytes = (uint32_t)P.n_boxes_pad * 32u;
+  if (bytes == 0) return true;
+  const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&sh.mbar);
+  const uint32_t dst0 = (uint32_t)__cvta_generic_to_shared(sbox);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
+                 : "memory");
+    const uint32_t piece = 16384u;  // several copies of <= 16 KB each
+    for (uint32_t off = 0; off < bytes; off += piece) {
+      const uint32_t n = bytes - off < piece ? bytes - off : piece;  // multiple of 32
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+          "[%3];" ::"r"(dst0 + off),
+          "l"(reinterpret_cast<const char*>(P.boxes) + off), "r"(n), "r"(mb)
+          : "memory");
+    }
+    // bounded wait for phase 0 of the mbarrier
+    int ok = 0;
+    const uint64_t t0 = global_ns();
+    for (uint32_t spin = 0;; ++spin) {
+      uint32_t done;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+          " selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(mb)
+          : "memory");
+      if (done) { ok = 1; break; }
+      if (global_ns() - t0 > P.wait_ns) break;
+    }
+    if (!ok) {
+      raise_error(P.ctl, KP_DEV_ERR_TIMEOUT, 1);
+      // wait once more, again bounded, for the copies still in flight
+      const uint64_t t1 = global_ns();
+      for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(mb)
+            : "memory");
+        if (done || global_ns() - t1 > P.wait_ns) break;
+      }
+    }
+    sh.flag = ok;
+  }
+  __syncthreads();
+  return sh.flag != 0;
+}
+
+__device__ __forceinline__ int eq6_lambda(int t_e, int n_tree, int n_ve, int lambda_max) {
+  if (n_ve <= 0) return lambda_max;
+  int room = t_e - n_tree;
+  if (room < 0) room = 0;
+  const int lam = room / n_ve;
+  return lam < lambda_max ? lam : lambda_max;
+}
+
+// Node chunk [v0, v1) of this block over n nodes.
+__device__ __forceinline__ void chunk_of(int n, int* c0, int* c1) {
+  const int per = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+  const long long a = (long long)blockIdx.x * per;
+  *c0 = (int)(a < n ? a : n);
+  *c1 = (int)(a + per < n ? a + per : n);
+}
+
+// Sum of blk[0..G) and of blk[0..blockIdx.x).
+__device__ __forceinline__ void block_prefix(const uint32_t* blk, LoopShared& sh,
+                                             unsigned long long* before,
+                                             unsigned long long* total) {
+  unsigned long long pre = 0, tot = 0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    const unsigned long long c = blk[i];
+    tot += c;
+    if (i < (int)blockIdx.x) pre += c;
+  }
+  block_sum2(pre, tot, sh.red, before, total);
+}
+
+// Phase N': count V_E members of this block's node chunk (no draws).
+__device__ __forceinline__ void count_ve(const KParams& P, int n, LoopShared& sh) {
+  int v0, v1;
+  chunk_of(n, &v0, &v1);
+  unsigned long long c = 0;
+  for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) c += P.in_ve[v] ? 1 : 0;
+  unsigned long long tot, dummy;
+  block_sum2(c, 0, sh.red, &tot, &dummy);
+  if (threadIdx.x == 0) P.blk_b[blockIdx.x] = (uint32_t)tot;
+}
+
+// Phase L: write the V_E list (ascending node id); returns |V_E|.
+__device__ __forceinline__ int write_ve(const KParams& P, int n, LoopShared& sh) {
+  int v0, v1;
+  chunk_of(n, &v0, &v1);
+  unsigned long long off, total;
+  block_prefix(P.blk_b, sh, &off, &total);
+  int base = (int)off;
+  for (int vb = v0; vb < v1; vb += blockDim.x) {
+    const int v = vb + threadIdx.x;
+    const bool e = v < v1 && P.in_ve[v];
+    int cnt;
+    const int rank = block_rank(e, sh.scan, &cnt);
+    if (e) P.ve[base + rank] = v;
+    base += cnt;
+  }
+  return (int)total;
+}
+
+// Phase E: Algorithm 2 for every sample key in [0, S).
+template <int SYS, bool LOG>
+__device__ __forceinline__ void phase_expand(const KParams& P, const float4* sbox, uint32_t it,
+                                             int lam, int S, LoopShared& sh) {
+  using Sys = System<SYS>;
+  constexpr int D = Sys::D, N = Sys::N;
+  const int stride = gridDim.x * blockDim.x;
+  unsigned long long n_steps = 0, n_hull = 0;
+  for (int key = blockIdx.x * blockDim.x + threadIdx.x; key < S; key += stride) {
+    const int p = key / lam;
+    const int j = key - p * lam;
+    const int v = P.ve[p];
+    float x[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) x[i] = P.st[(size_t)i * P.t_e + v];
+    // random control in U and duration k * dt (counter: it, node, j, purpose)
+    const uint4 w0 = philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 0u), P.seed_lo, P.seed_hi);
+    const uint4 w1 = philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 1u), P.seed_lo, P.seed_hi);
+    const uint32_t wr[4] = {w0.x, w0.y, w0.z, w0.w};
+    float u[4];
+#pragma unroll
+    for (int i = 0; i < N; ++i) u[i] = fmaf(P.u_scale[i], unit24(wr[i]), P.u_lo[i]);
+    const int k = P.k_min + (int)__umulhi(w1.x, P.k_span);
+    // PropagateODE with the validity check after every integrator step
+    bool valid = true;
+    int fail = 0, hulls = 0;
+    for (int i = 1; i <= k; ++i) {
+      const float px = x[0], py = x[1], pz = x[2];
+      Sys::step(x, u, P.dt, P);
+      bool ok = in_state_box<D>(x, P);
+      if (ok) {
+        ++hulls;
+        ok = !hull_hits_boxes(sbox, P.n_boxes_pad, fminf(px, x[0]), fminf(py, x[1]),
+                              fminf(pz, x[2]), fmaxf(px, x[0]), fmaxf(py, x[1]), fmaxf(pz, x[2]));
+      }
+      if (!ok) {
+        valid = false;
+        fail = i;
+        break;
+      }
+    }
+    n_steps += valid ? k : fail;
+    n_hull += hulls;
+    int r, s;
+    bin_state<SYS>(x, P, &r, &s);
+    uint32_t f = 0;
+    if (valid) {
+      atomicAdd(&P.n_valid[r], 1u);
+      f = KP_F_VALID;
+      const bool cont = P.visited[s] == 0;
+      const bool bern = (uint64_t)w1.y < P.thr[r];
+      if (cont) {
+        f |= KP_F_CONTENDER;
+        // the first claimant of a sub-region knows it is newly reached: it
+        // will get exactly one representative in region r
+        if (atomicMin(&P.claim[s], (uint32_t)key) == 0xffffffffu) {
+          atomicAdd(&P.cov[r], 1u);
+          P.avail[r] = 1;
+        }
+      }
+      if (bern) {
+        f |= KP_F_BERN;
+        P.avail[r] = 1;
+      }
+      if (cont || bern) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) P.cst[(size_t)i * P.t_e + key] = x[i];
+#pragma unroll
+        for (int i = 0; i < N; ++i) P.cctrl[(size_t)i * P.t_e + key] = u[i];
+        P.ck[key] = (uint8_t)k;
+        P.cr[key] = r;
+        P.cs[key] = s;
+      }
+    } else {
+      atomicAdd(&P.n_invalid[r], 1u);
+    }
+    P.flags[key] = (uint8_t)f;
+    if (LOG && key < P.log.capacity) {
+      P.log.node[key] = v;
+      P.log.k[key] = k;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) P.log.uraw[4 * (size_t)key + i] = wr[i];
+      P.log.fail_step[key] = fail;
+      P.log.region[key] = r;
+      P.log.sub[key] = s;
+#pragma unroll
+      for (int i = 0; i < 12; ++i) P.log.state[12 * (size_t)key + i] = i < D ? x[i] : 0.0f;
+    }
+  }
+  unsigned long long bs, bh;
+  block_sum2(n_steps, n_hull, sh.red, &bs, &bh);
+  if (threadIdx.x == 0 && bs) {
+    atomicAdd(&P.ctl->tot_steps, bs);
+    atomicAdd(&P.ctl->tot_hull, bh);
+  }
+}
+
+// Phase A: accept flags of this block's key chunk; returns the block count
+// of accepted samples (all threads) and adds the valid count to the pass.
+__device__ __forceinline__ void phase_accept(const KParams& P, int S, LoopShared& sh) {
+  int k0, k1;
+  chunk_of(S, &k0, &k1);
+  unsigned long long acc_n = 0, valid_n = 0;
+  for (int key = k0 + threadIdx.x; key < k1; key += blockDim.x) {
+    uint32_t f = P.flags[key];
+    if (f & KP_F_VALID) {
+      ++valid_n;
+      bool win = false;
+      if (f & KP_F_CONTENDER) win = P.claim[P.cs[key]] == (uint32_t)key;
+      const bool acc = win || (f & KP_F_BERN);
+      if (win) f |= KP_F_WINNER;
+      if (acc) {
+        f |= KP_F_ACCEPTED;
+        ++acc_n;
+      }
+      P.flags[key] = (uint8_t)f;
+    }
+  }
+  unsigned long long a, b;
+  block_sum2(acc_n, valid_n, sh.red, &a, &b);
+  if (threadIdx.x == 0) {
+    P.blk_a[blockIdx.x] = (uint32_t)a;
+    if (b) atomicAdd(&P.ctl->it_valid, (uint32_t)b);
+  }
+}
+
+// Pairwise sum of buf[0..n), n a power of two (bottom-up tree, which is the
+// same tree as recursive halving).  All threads; result in buf[0].
+__device__ __forceinline__ void smem_pairwise(double* buf, int n) {
+  for (int stride = 1; stride < n; stride <<= 1) {
+    __syncthreads();
+    for (int i = threadIdx.x * 2 * stride; i < n; i += blockDim.x * 2 * stride)
+      buf[i] = __dadd_rn(buf[i], buf[i + stride]);
+  }
+  __syncthreads();
+}
+
+// Phase S: Eq. 3-4 for this block's region chunk and its pairwise partial
+// sum.  Every operation is an explicitly rounded IEEE double operation in
+// the order FreeVol = ((delta + nv) vol) / ((delta + nv) + ni),
+// f4 = (FreeVol FreeVol)(FreeVol FreeVol),
+// Score = f4 / ((1 + Cov)(1 + (nv + ni)(nv + ni))).
+__device__ __forceinline__ void phase_scores(const KParams& P, int nch, double* sd) {
+  if ((int)blockIdx.x >= nch) return;
+  const int ch = P.R_pad / nch;
+  const int r0 = blockIdx.x * ch;
+  for (int i = threadIdx.x; i < ch; i += blockDim.x) {
+    const int r = r0 + i;
+    double sc = 0.0;
+    if (r < P.R && P.avail[r]) {
+      const double nv = (double)P.n_valid[r], ni = (double)P.n_invalid[r];
+      const double dn = __dadd_rn(P.delta, nv);
+      const double fv = __ddiv_rn(__dmul_rn(dn, P.vol), __dadd_rn(dn, ni));
+      const double f2 = __dmul_rn(fv, fv);
+      const double f4 = __dmul_rn(f2, f2);
+      const double na = __dadd_rn(nv, ni);
+      const double den =
+          __dmul_rn(__dadd_rn(1.0, (double)P.cov[r]), __dadd_rn(1.0, __dmul_rn(na, na)));
+      sc = __ddiv_rn(f4, den);
+    }
+    if (r < P.R) P.score[r] = sc;
+    sd[i] = sc;
+  }
+  smem_pairwise(sd, ch);
+  if (threadIdx.x == 0) P.chunk_sum[blockIdx.x] = sd[0];
+  __syncthreads();
+}
+
+// Phase T: the sum of Eq. 5 from the chunk sums, then P_accept and the
+// integer threshold of this block's region chunk.
+__device__ __forceinline__ void phase_thresholds(const KParams& P, int nch, double* sd) {
+  if ((int)blockIdx.x >= nch) return;
+  for (int i = threadIdx.x; i < nch; i += blockDim.x) sd[i] = P.chunk_sum[i];
+  smem_pairwise(sd, nch);
+  const double sum = sd[0];
+  __syncthreads();
+  const int ch = P.R_pad / nch;
+  const int r0 = blockIdx.x * ch;
+  for (int i = threadIdx.x; i < ch; i += blockDim.x) {
+    const int r = r0 + i;
+    if (r >= P.R) break;
+    uint64_t thr = 1ull << 32;  // P_accept = 1 outside R_avail
+    if (P.avail[r]) {
+      double p;
+      if (sum > 0.0) {
+        p = __dadd_rn(__ddiv_rn(P.score[r], sum), P.eps);
+        if (p > 1.0) p = 1.0;
+      } else {
+        p = P.eps < 1.0 ? P.eps : 1.0;
+      }
+      if (p < 1.0) thr = (uint64_t)floor(__dmul_rn(p, 4294967296.0));
+    }
+    P.thr[r] = thr;
+  }
+}
+
+// Phase P: append this block's accepted samples in key order.
+template <bool LOG>
+__device__ __forceinline__ void phase_append(const KParams& P, int S, int lam, int t_old,
+                                             LoopShared& sh, int* total_out) {
+  constexpr int DMAX = 12, NMAX = 4;
+  int k0, k1;
+  chunk_of(S, &k0, &k1);
+  unsigned long long off, total;
+  block_prefix(P.blk_a, sh, &off, &total);
+  *total_out = (int)total;
+  const int D = P.sys == KP_SYS_QUAD ? 12 : 6;
+  const int N = P.sys == KP_SYS_QUAD ? 4 : 3;
+  int base = t_old + (int)off;
+  for (int kb = k0; kb < k1; kb += blockDim.x) {
+    const int key = kb + threadIdx.x;
+    const bool in = key < k1;
+    uint32_t f = in ? P.flags[key] : 0u;
+    const bool acc = (f & KP_F_ACCEPTED) != 0;
+    int cnt;
+    const int rank = block_rank(acc, sh.scan, &cnt);
+    if (acc) {
+      const int id = base + rank;
+      float pos[3];
+      for (int i = 0; i < DMAX; ++i) {
+        if (i >= D) break;
+        const float xi = P.cst[(size_t)i * P.t_e + key];
+        P.st[(size_t)i * P.t_e + id] = xi;
+        if (i < 3) pos[i] = xi;
+      }
+      for (int i = 0; i < NMAX; ++i) {
+        if (i >= N) break;
+        P.ctrl[(size_t)i * P.t_e + id] = P.cctrl[(size_t)i * P.t_e + key];
+      }
+      P.steps[id] = P.ck[key];
+      P.parent[id] = P.ve[key / lam];
+      P.region[id] = P.cr[key];
+      P.node_sub[id] = P.cs[key];
+      P.in_ve[id] = 1;
+      P.visited[P.cs[key]] = 1;
+      const float dx = pos[0] - P.goal_c[0], dy = pos[1] - P.goal_c[1], dz = pos[2] - P.goal_c[2];
+      if (dx * dx + dy * dy + dz * dz <= P.goal_r2) {
+        f |= KP_F_GOAL;
+        atomicMin(&P.ctl->goal_node, id);
+      }
+    }
+    if (LOG && in && key < P.log.capacity) P.log.flags[key] = (uint8_t)f;
+    base += cnt;
+  }
+}
+
+// Phase N: Algorithm 4 node sets, one draw per old node (counter: it, v, 0,
+// purpose 2) against the threshold of its region; new nodes are in V_E.
+__device__ __forceinline__ void phase_nodesets(const KParams& P, uint32_t it, int t_old,
+                                               int t_new, LoopShared& sh) {
+  int v0, v1;
+  chunk_of(t_new, &v0, &v1);
+  unsigned long long c = 0;
+  for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+    int e = 1;
+    if (v < t_old) {
+      const uint4 w = philox4x32_10(make_uint4(it, (uint32_t)v, 0u, 2u), P.seed_lo, P.seed_hi);
+      e = (uint64_t)w.x < P.thr[P.region[v]] ? 1 : 0;
+      P.in_ve[v] = (uint8_t)e;
+    }
+    c += e;
+  }
+  unsigned long long tot, dummy;
+  block_sum2(c, 0, sh.red, &tot, &dummy);
+  if (threadIdx.x == 0) P.blk_b[blockIdx.x] = (uint32_t)tot;
+}
+
+template <int SYS, bool LOG>
+__global__ void __launch_bounds__(KP_BLOCK) kp_loop_kernel(KParams P, int max_iters,
+                                                           uint64_t max_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ LoopShared sh;
+  float4* sbox = reinterpret_cast<float4*>(smem);
+  double* sd = reinterpret_cast<double*>(smem + (size_t)P.n_boxes_pad * 32);
+  KCtl* ctl = P.ctl;
+  const uint32_t G = gridDim.x;
+  const uint64_t t_start = global_ns();
+
+  if (ctl->state != KP_DEV_RUNNING) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_run = 0;
+    return;
+  }
+  if (!stage_boxes(P, sbox, sh)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->it_valid = 0;
+    ctl->stop = 0;
+    ctl->n_run = 0;
+  }
+  int n_tree = ctl->n_nodes;
+  uint32_t it = (uint32_t)ctl->iteration;
+  const int nch = P.nch;
+
+  // V_E list from the stored node sets
+  count_ve(P, n_tree, sh);
+  if (!grid_sync(ctl, G, P.wait_ns, 10)) return;
+  int n_ve = write_ve(P, n_tree, sh);
+  if (!grid_sync(ctl, G, P.wait_ns, 11)) return;
+  int lam = eq6_lambda(P.t_e, n_tree, n_ve, P.lambda_max);
+  if (n_ve > 0 && lam == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctl->state = KP_DEV_FULL;
+      ctl->n_ve = n_ve;
+    }
+    return;
+  }
+
+  int run = 0;
+  for (;;) {
+    const int S = n_ve > 0 ? n_ve * lam : 0;
+    phase_expand<SYS, LOG>(P, sbox, it, lam, S, sh);
+    if (!grid_sync(ctl, G, P.wait_ns, 20)) return;
+    phase_accept(P, S, sh);
+    phase_scores(P, nch, sd);
+    if (!grid_sync(ctl, G, P.wait_ns, 21)) return;
+    int n_acc;
+    phase_append<LOG>(P, S, lam, n_tree, sh, &n_acc);
+    phase_thresholds(P, nch, sd);
+    if (!grid_sync(ctl, G, P.wait_ns, 22)) return;
+    const int t_old = n_tree;
+    n_tree = t_old + n_acc;
+    phase_nodesets(P, it, t_old, n_tree, sh);
+    if (!grid_sync(ctl, G, P.wait_ns, 23)) return;
+    const int ve_prev = n_ve, lam_prev = lam;
+    n_ve = write_ve(P, n_tree, sh);
+    lam = eq6_lambda(P.t_e, n_tree, n_ve, P.lambda_max);
+    ++run;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const int goal = *((volatile int*)&ctl->goal_node);
+      const bool solved = goal != KP_NO_GOAL;
+      const bool full = n_ve > 0 && lam == 0;
+      if (run <= P.stats_cap && P.stats) {
+        KStats s;
+        s.iteration = (int)it;
+        s.n_ve = ve_prev;
+        s.lambda = lam_prev;
+        s.n_samples = S;
+        s.n_valid = (int)*((volatile uint32_t*)&ctl->it_valid);
+        s.n_accepted = n_acc;
+        s.n_nodes = n_tree;
+        s.goal_node = solved ? goal : -1;
+        P.stats[run - 1] = s;
+      }
+      ctl->it_valid = 0;
+      ctl->tot_samples += (unsigned long long)S;
+      const bool out_of_time = max_ns > 0 && global_ns() - t_start >= max_ns;
+      ctl->state = solved ? KP_DEV_SOLVED : (full ? KP_DEV_FULL : KP_DEV_RUNNING);
+      ctl->stop = (solved || full || run >= max_iters || out_of_time) ? 1 : 0;
+    }
+    ++it;
+    if (!grid_sync(ctl, G, P.wait_ns, 24)) return;
+    if (*((volatile int*)&ctl->stop)) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->n_nodes = n_tree;
+    ctl->n_ve = n_ve;
+    ctl->iteration = (int)it;
+    ctl->n_run = run;
+  }
+}
+
+// Algorithm 1, lines 1-3 on the device (after the host cleared the tables):
+// block 0 thread 0 checks and bins x_init and writes the root; every thread
+// sets P_accept = 1 (threshold 2^32) for its regions.
+template <int SYS>
+__global__ void kp_reset_kernel(KParams P, RootState root) {
+  using Sys = System<SYS>;
+  constexpr int D = Sys::D;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.R; r += gridDim.x * blockDim.x)
+    P.thr[r] = 1ull << 32;
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  KCtl* ctl = P.ctl;
+  float x[D];
+  for (int i = 0; i < D; ++i) x[i] = root.x[i];
+  const float4* gb = reinterpret_cast<const float4*>(P.boxes);
+  bool ok = in_state_box<D>(x, P) &&
+            !hull_hits_boxes(gb, P.n_boxes_pad, x[0], x[1], x[2], x[0], x[1], x[2]);
+  ctl->n_run = 0;
+  ctl->stop = 0;
+  ctl->it_valid = 0;
+  ctl->err = 0;
+  ctl->err_where = 0;
+  ctl->bar_count = 0;
+  ctl->iteration = 0;
+  ctl->n_edges = 0;
+  ctl->tot_samples = 0;
+  ctl->tot_steps = 0;
+  ctl->tot_hull = 0;
+  if (!ok) {
+    ctl->state = KP_DEV_BAD_ROOT;
+    ctl->n_nodes = 0;
+    ctl->n_ve = 0;
+    ctl->goal_node = KP_NO_GOAL;
+    return;
+  }
+  int r, s;
+  bin_state<SYS>(x, P, &r, &s);
+  for (int i = 0; i < D; ++i) P.st[(size_t)i * P.t_e] = x[i];
+  for (int i = 0; i < Sys::N; ++i) P.ctrl[(size_t)i * P.t_e] = 0.0f;
+  P.parent[0] = -1;
+  P.steps[0] = 0;
+  P.region[0] = r;
+  P.node_sub[0] = s;
+  P.in_ve[0] = 1;
+  P.visited[s] = 1;
+  P.cov[r] = 1;
+  P.avail[r] = 1;
+  ctl->n_nodes = 1;
+  ctl->n_ve = 1;
+  const float dx = x[0] - P.goal_c[0], dy = x[1] - P.goal_c[1], dz = x[2] - P.goal_c[2];
+  const bool in_goal = dx * dx + dy * dy + dz * dz <= P.goal_r2;
+  ctl->goal_node = in_goal ? 0 : KP_NO_GOAL;
+  ctl->state = in_goal ? KP_DEV_SOLVED : KP_DEV_RUNNING;
+}
+
+}  // namespace kp

@@ -1,0 +1,5 @@
+// kp_sys_dubins.cu -- kernels and launchers of one system (see kp_launch.cuh).
+#include "kp_layout.h"
+#define KP_SYS kp::KP_SYS_DUBINS
+#define KP_SYS_NAME dubins
+#include "kp_launch.cuh"

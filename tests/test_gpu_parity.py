@@ -1,0 +1,267 @@
+"""CUDA planner vs the FP64 oracle, element by element, through the C ABI.
+
+Every input is a seeded synthetic workload (or a tree state the oracle grew
+from one); nothing the device computes feeds the oracle."""
+import numpy as np
+import pytest
+
+from oracle import kpo
+from oracle.kpo import Oracle
+from paper_2409_06807_gb300 import workloads as W
+from parity_util import compare_pass, compare_trees, state_scale
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2409_06807_gb300.build import build_planner
+    build_planner()
+    from paper_2409_06807_gb300 import planner
+    return planner
+
+
+def lockstep(P, w, n_iters, log_cap=None):
+    """Both implementations from the same root; compare every pass until
+    the first ambiguous decision split (after which the trees may differ).
+    Returns (passes compared exactly, passes run)."""
+    g = P.Planner(w)
+    o = Oracle(w)
+    assert g.reset() == P.OK and o.reset() == kpo.RUNNING
+    g.enable_log(log_cap or w.t_e)
+    exact = 0
+    for i in range(n_iters):
+        status, ost, orec = o.iterate(records=True)
+        gstats = g.expand_step(1)
+        if status == kpo.FULL:
+            assert gstats == [] and g.info()["state"] == 2
+            break
+        assert len(gstats) == 1
+        grec = g.read_log(ost["n_samples"])
+        flips = compare_pass(w, ost, orec, gstats[0], grec)
+        if flips:
+            return exact, i + 1
+        compare_trees(w, g.export_tree(), o.export())
+        exact += 1
+        if status != kpo.RUNNING:
+            assert g.info()["state"] == 1
+            break
+    return exact, i + 1
+
+
+@pytest.mark.parametrize("system", [W.DI, W.DUBINS, W.QUAD])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lockstep_tiny(P, system, seed):
+    w = W.tiny(system, seed=seed, t_e=2000, lambda_max=8)
+    exact, ran = lockstep(P, w, 12)
+    assert exact >= min(ran, 3)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_lockstep_c1(P, seed):
+    """Double integrator, 16 boxes, 8^3 x 4^3 decomposition, lambda 32,
+    t_e 65,536: passes of 32 .. ~60,000 samples (many tiles, ragged)."""
+    w = W.c1(seed)
+    exact, ran = lockstep(P, w, 12)
+    assert exact >= 2
+
+
+def frontier(P, w, grow, n_pass=1):
+    """The oracle grows a tree for 'grow' passes; its state (rounded to
+    float32) is loaded into the device planner and into a fresh oracle, and
+    both run n_pass passes."""
+    src = Oracle(w)
+    src.reset()
+    for _ in range(grow):
+        src.iterate()
+    t = src.export()
+    t["state"] = t["state"].astype(np.float32)
+    t["ctrl"] = t["ctrl"].astype(np.float32)
+    o = Oracle(w)
+    o.import_(t)
+    g = P.Planner(w)
+    g.import_tree(t)
+    start = g.export_tree()
+    for key in ("parent", "region", "sub", "in_ve", "n_valid", "n_invalid", "thr", "visited"):
+        assert np.array_equal(start[key], t[key]), key
+    assert np.array_equal(start["cov"], t["cov"]) and np.array_equal(start["avail"], t["avail"])
+    g.enable_log(w.t_e)
+    flips_total = 0
+    for _ in range(n_pass):
+        status, ost, orec = o.iterate(records=True)
+        gs = g.expand_step(1)
+        assert len(gs) == 1
+        flips = compare_pass(w, ost, orec, gs[0], g.read_log(ost["n_samples"]))
+        flips_total += flips
+        if flips:
+            break
+        compare_trees(w, g.export_tree(), o.export())
+        if status != kpo.RUNNING:
+            break
+    return flips_total, ost
+
+
+def test_frontier_c2_dubins(P):
+    """Dubins airplane, 200-trunk forest, 16^3 x 4^3, lambda 64, t_e 2^20:
+    one pass over the oracle's 3-pass tree (~10^5 samples)."""
+    flips, ost = frontier(P, W.c2(0), grow=2)
+    assert ost["n_samples"] > 10000
+    assert flips <= 2
+
+
+def test_frontier_c3_quadrotor(P):
+    """Quadrotor, 1,200-box building, 16^3 x 4 speed bins x 4^3, lambda
+    128, t_e 2^22: one pass over the oracle's 1-pass tree (~1.6e4 samples)."""
+    flips, ost = frontier(P, W.c3(0), grow=1)
+    assert ost["n_samples"] > 10000
+    assert flips <= 2
+
+
+def test_frontier_empty_v_e(P):
+    """A pass with V_E empty draws no sample but still re-selects nodes."""
+    w = W.c1(0)
+    src = Oracle(w)
+    src.reset()
+    src.run(3)
+    t = src.export()
+    t["in_ve"][:] = 0
+    o = Oracle(w)
+    o.import_(t)
+    g = P.Planner(w)
+    g.import_tree(t)
+    status, ost, _ = o.iterate()
+    gs = g.expand_step(1)
+    assert ost["n_samples"] == 0 and gs[0]["n_samples"] == 0
+    compare_trees(w, g.export_tree(), o.export())
+
+
+def _revalidate(w, traj, x_init, tol=1e-4):
+    """Re-propagate every edge in FP64 from the returned parent state:
+    child state within tol, dense check within tol, goal reached."""
+    o = Oracle(w)
+    scale = state_scale(w)
+    prev = np.asarray(x_init, np.float64)
+    for e in range(len(traj["steps"])):
+        u = traj["ctrls"][e].astype(np.float64)
+        depth, x_end = o.dense_check(prev, u, int(traj["steps"][e]), 100)
+        assert depth <= tol, f"edge {e} penetrates by {depth}"
+        err = np.abs(x_end - traj["states"][e]) / scale
+        assert err.max() <= tol, f"edge {e} re-propagation error {err.max()}"
+        prev = traj["states"][e].astype(np.float64)
+    end = traj["states"][-1][:3].astype(np.float64)
+    assert np.linalg.norm(end - w.goal_c) <= float(w.goal_r) * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_plan_c1_revalidated(P, seed):
+    w = W.c1(seed)
+    g = P.Planner(w)
+    st, traj = g.plan(max_iters=200)
+    assert st == P.OK and len(traj["steps"]) > 0
+    _revalidate(w, traj, w.x_init)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_plan_c2_full_size(P, seed):
+    """Full-size Dubins forest query, the configuration the benchmark times:
+    the returned trajectory is re-validated edge by edge by the oracle, and
+    tree-wide invariants hold."""
+    w = W.c2(seed)
+    g = P.Planner(w)
+    st, traj = g.plan(max_iters=200)
+    assert st == P.OK
+    _revalidate(w, traj, w.x_init)
+    _tree_invariants(w, g.export_tree(), sample_edges=300)
+
+
+def _tree_invariants(w, t, sample_edges=0):
+    n = t["n_nodes"]
+    assert 1 <= n <= w.t_e
+    assert t["parent"][0] == -1 and np.all(t["parent"][1:n] < np.arange(1, n))
+    assert np.all(t["parent"][1:n] >= 0)
+    per = w.n_sub_per
+    assert np.array_equal(t["cov"], t["visited"].reshape(-1, per).sum(1))
+    av = np.zeros_like(t["avail"])
+    av[t["region"][:n]] = 1
+    assert np.array_equal(t["avail"], av)
+    assert np.all(t["visited"][t["sub"][:n]] == 1)
+    assert np.all(t["sub"][:n] // per == t["region"][:n])
+    thr = t["thr"].astype(np.float64) / 2 ** 32
+    assert np.all(thr[t["avail"] == 0] == 1.0)
+    assert np.all(thr[t["avail"] == 1] >= w.eps - 2 ** -32)
+    if sample_edges:
+        o = Oracle(w)
+        rng = np.random.default_rng(0)
+        scale = state_scale(w)
+        for v in rng.integers(1, n, size=min(sample_edges, n - 1)):
+            p = t["parent"][v]
+            traj = kpo.propagate(w, t["state"][p].astype(np.float64),
+                                 t["ctrl"][v].astype(np.float64), int(t["steps"][v]))
+            err = np.abs(traj[-1] - t["state"][v]) / scale
+            assert err.max() <= 1e-4
+            r, s, m = o.bin(traj[-1])
+            if m > 1e-4:
+                assert r == t["region"][v] and s == t["sub"][v]
+
+
+def test_tree_full_stops(P):
+    w = W.tiny(W.DI, seed=1, t_e=40, goal_r=np.float32(0.0))
+    g = P.Planner(w)
+    st, _ = g.plan(max_iters=100)
+    assert st == P.NO_SOLUTION
+    info = g.info()
+    assert info["state"] == 2 and info["n_nodes"] <= 40
+    o = Oracle(w)
+    o.reset()
+    status, _ = o.run(100)
+    assert status == kpo.FULL
+
+
+def test_root_cases(P):
+    w = W.tiny(W.DI)
+    g = P.Planner(w)
+    st, traj = g.plan(max_iters=5, x_init=w.x_init,
+                      goal=P.goal_struct(w.with_(goal_c=w.x_init[:3].copy())))
+    assert st == P.OK and len(traj["steps"]) == 0
+    bad = w.x_init.copy()
+    bad[3] = 5.0
+    with pytest.raises(P.KpError) as e:
+        g.reset(x_init=bad)
+    assert e.value.status == P.ERR_ARG
+    assert g.reset() == P.OK  # the context is still usable
+
+
+def test_no_obstacles_and_obstacle_swap(P):
+    w = W.c1(0)
+    g = P.Planner(w.with_(boxes=np.zeros((0, 6), np.float32)), box_capacity=16)
+    st, traj = g.plan(max_iters=100)
+    assert st == P.OK
+    g.set_obstacles(w.boxes)
+    g.w = w
+    st, traj = g.plan(max_iters=100)
+    assert st == P.OK
+    _revalidate(w, traj, w.x_init)
+
+
+def test_budget_iterations(P):
+    w = W.c2(0)
+    g = P.Planner(w)
+    st, _ = g.plan(max_iters=2)
+    assert st == P.NO_SOLUTION and g.info()["iteration"] == 2
+
+
+def test_bounded_wait_reports_timeout(P):
+    """A device wait on a flag nothing sets ends after the wait limit with
+    KP_ERR_TIMEOUT; the context is then poisoned, other contexts are not."""
+    w = W.tiny(W.DI)
+    g = P.Planner(w)
+    g.set_wait_limit(2_000_000)  # 2 ms
+    assert g.selftest_wait_timeout() == P.ERR_TIMEOUT
+    with pytest.raises(P.KpError) as e:
+        g.reset()
+    assert e.value.status == P.ERR_STATE
+    h = P.Planner(w)
+    assert h.reset() == P.OK
