@@ -275,6 +275,36 @@ kp_status kp_set_wait_limit(kp_ctx *ctx, uint64_t ns);
  * expired as designed. */
 kp_status kp_selftest_wait_timeout(kp_ctx *ctx);
 
+/* kp_plan for callers that cannot allocate device memory.  The paper has
+ * no counterpart: this is a deployment form of kp_plan.  Some callers may
+ * not call cudaMalloc (or hand this library an arena) at all: a host
+ * application that owns every byte of device memory through its own pool,
+ * a plugin loaded into such a process, or a real-time control loop that
+ * must not pay the implicit device synchronisation and unbounded latency of
+ * an allocation.  This entry point runs the same query as kp_plan (same
+ * kernels, same results) with no context, no arena and no allocation of any
+ * kind: its device scratch is one static array of KP_STATIC_SCRATCH_BYTES
+ * that every GPU loading this library holds until the process exits.  The
+ * caller still passes all inputs (host structs and arrays, as for
+ * kp_create/kp_plan) and the output trajectory buffers.
+ *  - Size limit: problems whose arena (kp_required_bytes) exceeds
+ *    KP_STATIC_SCRATCH_BYTES return KP_ERR_OOM without touching the device.
+ *  - Set-up: the first call on a device looks up the scratch's device
+ *    address (once per device, with that device current); make that first
+ *    call before any stream capture.
+ *  - Sharing: all calls on a device share the scratch, which keeps the last
+ *    call's contents; every call clears what must start at zero.  Calls
+ *    whose GPU work overlaps (other streams or host threads) race on the
+ *    scratch and must be serialised by the caller.
+ *  - Work is enqueued on cuda_stream (NULL = legacy default stream) and the
+ *    call waits for it.  Returns as kp_plan; error codes carry no message. */
+#define KP_STATIC_SCRATCH_BYTES (16u << 20)
+kp_status kp_plan_static(const kp_system *sys, const kp_workspace *ws,
+                         const kp_obstacles *obs, const kp_params *prm,
+                         const float *x_init, const kp_goal *goal,
+                         const kp_budget *budget, kp_traj *traj,
+                         void *cuda_stream);
+
 /* Last error message of the context (never NULL). */
 const char *kp_last_error(const kp_ctx *ctx);
 

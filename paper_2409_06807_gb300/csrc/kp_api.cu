@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -419,6 +420,74 @@ kp_status enqueue_reset(kp_ctx* ctx, const float* x_init) {
   return KP_OK;
 }
 
+// Launch constants and arena slices of a validated problem.
+void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* sys,
+                 const kp_workspace* ws, const kp_params* prm, char* A) {
+  P = KParams{};
+  P.sys = d.sys;
+  P.dt = sys->dt;
+  P.k_min = sys->k_min;
+  P.k_span = (uint32_t)(sys->k_max - sys->k_min + 1);
+  for (int i = 0; i < 12; ++i) {
+    P.x_lo[i] = i < d.D ? sys->x_lo[i] : -INFINITY;
+    P.x_hi[i] = i < d.D ? sys->x_hi[i] : INFINITY;
+  }
+  for (int i = 0; i < 4; ++i) {
+    P.u_lo[i] = sys->u_lo[i];
+    P.u_scale[i] = sys->u_hi[i] - sys->u_lo[i];
+  }
+  for (int i = 0; i < 16; ++i) P.phys[i] = sys->phys[i];
+  double vol = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    P.ws_lo[a] = ws->lo[a];
+    P.n_fine[a] = ws->grid[a] * ws->sub[a];
+    P.fine_scale[a] = (float)((double)P.n_fine[a] / ((double)ws->hi[a] - (double)ws->lo[a]));
+    P.sub[a] = ws->sub[a];
+    P.grid[a] = ws->grid[a];
+    vol *= ((double)ws->hi[a] - (double)ws->lo[a]) / (double)ws->grid[a];
+  }
+  P.speed_bins = ws->speed_bins;
+  P.speed_scale = ws->speed_bins > 1 ? (float)((double)ws->speed_bins / (double)ws->speed_hi) : 0.0f;
+  P.n_sub_per = d.n_sub_per;
+  P.R = d.R;
+  P.R_pad = d.R_pad;
+  P.t_e = d.t_e;
+  P.lambda_max = prm->lambda_max;
+  P.delta = prm->delta;
+  P.eps = prm->eps;
+  P.vol = vol;
+  P.boxes = reinterpret_cast<const float*>(A + lay.boxes);
+  P.st = reinterpret_cast<float*>(A + lay.st);
+  P.parent = reinterpret_cast<int32_t*>(A + lay.parent);
+  P.ctrl = reinterpret_cast<float*>(A + lay.ctrl);
+  P.steps = reinterpret_cast<uint8_t*>(A + lay.steps);
+  P.region = reinterpret_cast<int32_t*>(A + lay.region);
+  P.node_sub = reinterpret_cast<int32_t*>(A + lay.sub);
+  P.in_ve = reinterpret_cast<uint8_t*>(A + lay.in_ve);
+  P.cst = reinterpret_cast<float*>(A + lay.cst);
+  P.cctrl = reinterpret_cast<float*>(A + lay.cctrl);
+  P.ck = reinterpret_cast<uint8_t*>(A + lay.ck);
+  P.cr = reinterpret_cast<int32_t*>(A + lay.cr);
+  P.cs = reinterpret_cast<int32_t*>(A + lay.cs);
+  P.flags = reinterpret_cast<uint8_t*>(A + lay.flags);
+  P.n_valid = reinterpret_cast<uint32_t*>(A + lay.n_valid);
+  P.n_invalid = reinterpret_cast<uint32_t*>(A + lay.n_invalid);
+  P.cov = reinterpret_cast<uint32_t*>(A + lay.cov);
+  P.avail = reinterpret_cast<uint8_t*>(A + lay.avail);
+  P.visited = reinterpret_cast<uint8_t*>(A + lay.visited);
+  P.claim = reinterpret_cast<uint32_t*>(A + lay.claim);
+  P.score = reinterpret_cast<double*>(A + lay.score);
+  P.thr = reinterpret_cast<uint64_t*>(A + lay.thr);
+  P.ve = reinterpret_cast<int32_t*>(A + lay.ve);
+  P.blk_a = reinterpret_cast<uint32_t*>(A + lay.blk_a);
+  P.blk_b = reinterpret_cast<uint32_t*>(A + lay.blk_b);
+  P.chunk_sum = reinterpret_cast<double*>(A + lay.chunk_sum);
+  P.ctl = reinterpret_cast<KCtl*>(A + lay.ctl);
+  P.stats = reinterpret_cast<KStats*>(A + lay.stats);
+  P.stats_cap = kStatsCap;
+  P.traj = reinterpret_cast<float*>(A + lay.traj);
+}
+
 kp_status check_launch(kp_ctx* ctx, const KCtl& h) {
   if (h.err == KP_DEV_ERR_TIMEOUT)
     return fail(ctx, KP_ERR_TIMEOUT, "device wait exceeded %llu ns (site %d)",
@@ -483,71 +552,8 @@ kp_status kp_create(const kp_system* sys, const kp_workspace* ws, const kp_obsta
     }
   }
 
-  KParams& P = ctx->P;
-  P = KParams{};
-  P.sys = d.sys;
-  P.dt = sys->dt;
-  P.k_min = sys->k_min;
-  P.k_span = (uint32_t)(sys->k_max - sys->k_min + 1);
-  for (int i = 0; i < 12; ++i) {
-    P.x_lo[i] = i < d.D ? sys->x_lo[i] : -INFINITY;
-    P.x_hi[i] = i < d.D ? sys->x_hi[i] : INFINITY;
-  }
-  for (int i = 0; i < 4; ++i) {
-    P.u_lo[i] = sys->u_lo[i];
-    P.u_scale[i] = sys->u_hi[i] - sys->u_lo[i];
-  }
-  for (int i = 0; i < 16; ++i) P.phys[i] = sys->phys[i];
-  double vol = 1.0;
-  for (int a = 0; a < 3; ++a) {
-    P.ws_lo[a] = ws->lo[a];
-    P.n_fine[a] = ws->grid[a] * ws->sub[a];
-    P.fine_scale[a] = (float)((double)P.n_fine[a] / ((double)ws->hi[a] - (double)ws->lo[a]));
-    P.sub[a] = ws->sub[a];
-    P.grid[a] = ws->grid[a];
-    vol *= ((double)ws->hi[a] - (double)ws->lo[a]) / (double)ws->grid[a];
-  }
-  P.speed_bins = ws->speed_bins;
-  P.speed_scale = ws->speed_bins > 1 ? (float)((double)ws->speed_bins / (double)ws->speed_hi) : 0.0f;
-  P.n_sub_per = d.n_sub_per;
-  P.R = d.R;
-  P.R_pad = d.R_pad;
-  P.t_e = d.t_e;
-  P.lambda_max = prm->lambda_max;
-  P.delta = prm->delta;
-  P.eps = prm->eps;
-  P.vol = vol;
+  fill_params(ctx->P, d, lay, sys, ws, prm, ctx->arena);
   char* A = ctx->arena;
-  P.boxes = reinterpret_cast<const float*>(A + lay.boxes);
-  P.st = reinterpret_cast<float*>(A + lay.st);
-  P.parent = reinterpret_cast<int32_t*>(A + lay.parent);
-  P.ctrl = reinterpret_cast<float*>(A + lay.ctrl);
-  P.steps = reinterpret_cast<uint8_t*>(A + lay.steps);
-  P.region = reinterpret_cast<int32_t*>(A + lay.region);
-  P.node_sub = reinterpret_cast<int32_t*>(A + lay.sub);
-  P.in_ve = reinterpret_cast<uint8_t*>(A + lay.in_ve);
-  P.cst = reinterpret_cast<float*>(A + lay.cst);
-  P.cctrl = reinterpret_cast<float*>(A + lay.cctrl);
-  P.ck = reinterpret_cast<uint8_t*>(A + lay.ck);
-  P.cr = reinterpret_cast<int32_t*>(A + lay.cr);
-  P.cs = reinterpret_cast<int32_t*>(A + lay.cs);
-  P.flags = reinterpret_cast<uint8_t*>(A + lay.flags);
-  P.n_valid = reinterpret_cast<uint32_t*>(A + lay.n_valid);
-  P.n_invalid = reinterpret_cast<uint32_t*>(A + lay.n_invalid);
-  P.cov = reinterpret_cast<uint32_t*>(A + lay.cov);
-  P.avail = reinterpret_cast<uint8_t*>(A + lay.avail);
-  P.visited = reinterpret_cast<uint8_t*>(A + lay.visited);
-  P.claim = reinterpret_cast<uint32_t*>(A + lay.claim);
-  P.score = reinterpret_cast<double*>(A + lay.score);
-  P.thr = reinterpret_cast<uint64_t*>(A + lay.thr);
-  P.ve = reinterpret_cast<int32_t*>(A + lay.ve);
-  P.blk_a = reinterpret_cast<uint32_t*>(A + lay.blk_a);
-  P.blk_b = reinterpret_cast<uint32_t*>(A + lay.blk_b);
-  P.chunk_sum = reinterpret_cast<double*>(A + lay.chunk_sum);
-  P.ctl = reinterpret_cast<KCtl*>(A + lay.ctl);
-  P.stats = reinterpret_cast<KStats*>(A + lay.stats);
-  P.stats_cap = kStatsCap;
-  P.traj = reinterpret_cast<float*>(A + lay.traj);
 
   {
     cudaError_t e = cudaMemsetAsync(A + lay.ctl, 0, sizeof(KCtl), ctx->stream);
@@ -909,3 +915,186 @@ kp_status kp_last_launch_ms(kp_ctx* ctx, float* ms) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// kp_plan_static: kp_plan without any allocation, over a static scratch
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Scratch of kp_plan_static.  Every GPU that loads this library holds one
+// copy until the process exits.  All kp_plan_static calls on a device share
+// it and it keeps the last call's contents, so each call clears what must
+// start at zero; calls whose GPU work overlaps (other streams, other host
+// threads) race on it.
+static __device__ __align__(256) unsigned char g_kp_static_scratch[KP_STATIC_SCRATCH_BYTES];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_base[kStaticMaxDevices];  // device address of the scratch, per device
+
+// Raw {lo, hi} box rows -> the padded float4 pairs the loop kernel reads.
+__global__ void kp_static_pad_boxes_kernel(float* dst, const float* raw, int n, int pad) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < pad; b += gridDim.x * blockDim.x) {
+    float* o = dst + (size_t)b * 8;
+    if (b < n) {
+      const float* in = raw + (size_t)b * 6;
+      o[0] = in[0]; o[1] = in[1]; o[2] = in[2]; o[3] = 0.0f;
+      o[4] = in[3]; o[5] = in[4]; o[6] = in[5]; o[7] = 0.0f;
+    } else {
+      o[0] = o[1] = o[2] = INFINITY;
+      o[4] = o[5] = o[6] = -INFINITY;
+      o[3] = o[7] = 0.0f;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws,
+                                    const kp_obstacles* obs, const kp_params* prm,
+                                    const float* x_init, const kp_goal* goal,
+                                    const kp_budget* budget, kp_traj* traj, void* cuda_stream) {
+  if (!sys || !ws || !prm || !x_init || !goal || !budget || !traj) return KP_ERR_ARG;
+  const int nb = obs ? obs->n_boxes : 0;
+  Dims d{};
+  if (check_inputs(sys, ws, nb, prm, &d)) return KP_ERR_ARG;
+  if (nb > 0 && !obs->boxes) return KP_ERR_ARG;
+  for (int i = 0; i < 6 * nb; ++i)
+    if (std::isnan(obs->boxes[i])) return KP_ERR_ARG;
+  for (int i = 0; i < d.D; ++i)
+    if (std::isnan(x_init[i])) return KP_ERR_ARG;
+  if (!(goal->radius >= 0.0f) || std::isnan(goal->center[0]) || std::isnan(goal->center[1]) ||
+      std::isnan(goal->center[2]))
+    return KP_ERR_ARG;
+  if (budget->max_iters < 1 || traj->capacity < 0 ||
+      (traj->capacity > 0 && (!traj->states || !traj->ctrls || !traj->steps)))
+    return KP_ERR_ARG;
+  const Layout lay = make_layout(d);
+  if (lay.total > (size_t)KP_STATIC_SCRATCH_BYTES) return KP_ERR_OOM;
+
+  // one-time set-up per device: the device address of the scratch
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) {
+    cudaGetLastError();
+    return KP_ERR_CUDA;
+  }
+  char* A = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_base[dev]) {
+      void* base = nullptr;
+      if (cudaGetSymbolAddress(&base, g_kp_static_scratch) != cudaSuccess || !base) {
+        cudaGetLastError();
+        return KP_ERR_CUDA;
+      }
+      g_static_base[dev] = base;
+    }
+    A = static_cast<char*>(g_static_base[dev]);
+  }
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+
+  KParams P{};
+  fill_params(P, d, lay, sys, ws, prm, A);
+  const int pad = (nb + 7) / 8 * 8;
+  P.n_boxes_pad = pad;
+  for (int a = 0; a < 3; ++a) P.goal_c[a] = goal->center[a];
+  P.goal_r2 = (float)((double)goal->radius * (double)goal->radius);
+  P.seed_lo = (uint32_t)(prm->seed & 0xffffffffu);
+  P.seed_hi = (uint32_t)(prm->seed >> 32);
+  P.log = KLog{};
+  P.wait_ns = 2000000000ull;
+
+  // launch shape, as for a context with this obstacle count
+  int num_sms = 0, bps = 0;
+  if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return KP_ERR_CUDA;
+  }
+  const int min_ch = d.R_pad / (d.R_pad < 128 ? d.R_pad : 128);
+  const int sd = min_ch > 1024 ? min_ch : 1024;
+  const size_t smem = (size_t)pad * 32 + (size_t)sd * 8;
+  if (occupancy(d.sys, false, smem, &bps) != cudaSuccess || bps < 1) {
+    cudaGetLastError();
+    return KP_ERR_CUDA;
+  }
+  int grid = bps * num_sms;
+  if (grid > KP_MAX_GRID) grid = KP_MAX_GRID;
+  int nch = 1;
+  while (nch * 2 <= grid && nch * 2 <= d.R_pad && nch * 2 <= 1024) nch *= 2;
+  P.nch = nch;
+
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+    return e == cudaSuccess;
+  };
+  // obstacles: raw rows into the (not yet used) trajectory rows, padded on
+  // the device into the box slots
+  if (nb > 0) {
+    ok(cudaMemcpyAsync(A + lay.traj, obs->boxes, (size_t)nb * 24, cudaMemcpyHostToDevice, stream));
+    kp_static_pad_boxes_kernel<<<(pad + 255) / 256, 256, 0, stream>>>(
+        reinterpret_cast<float*>(A + lay.boxes), reinterpret_cast<const float*>(A + lay.traj), nb,
+        pad);
+    ok(cudaGetLastError());
+  }
+  // everything that must start from zero (the scratch keeps old contents)
+  ok(cudaMemsetAsync(A + lay.ctl, 0, sizeof(KCtl), stream));
+  ok(cudaMemsetAsync(A + lay.visited, 0, d.n_sub, stream));
+  ok(cudaMemsetAsync(A + lay.claim, 0xff, d.n_sub * 4, stream));
+  ok(cudaMemsetAsync(A + lay.n_valid, 0, (size_t)d.R * 4, stream));
+  ok(cudaMemsetAsync(A + lay.n_invalid, 0, (size_t)d.R * 4, stream));
+  ok(cudaMemsetAsync(A + lay.cov, 0, (size_t)d.R * 4, stream));
+  ok(cudaMemsetAsync(A + lay.avail, 0, (size_t)d.R, stream));
+  RootState root{};
+  for (int i = 0; i < d.D; ++i) root.x[i] = x_init[i];
+  const uint64_t max_ns = budget->max_ms > 0.0 ? (uint64_t)(budget->max_ms * 1e6) : 0ull;
+  if (e == cudaSuccess) {
+    switch (d.sys) {
+      case KP_SYS_DI:
+        ok(launch_reset_di(P, root, stream));
+        ok(launch_loop_di(P, grid, smem, budget->max_iters, max_ns, false, stream));
+        break;
+      case KP_SYS_DUBINS:
+        ok(launch_reset_dubins(P, root, stream));
+        ok(launch_loop_dubins(P, grid, smem, budget->max_iters, max_ns, false, stream));
+        break;
+      default:
+        ok(launch_reset_quad(P, root, stream));
+        ok(launch_loop_quad(P, grid, smem, budget->max_iters, max_ns, false, stream));
+    }
+  }
+  if (e == cudaSuccess) {
+    kp_extract_kernel<<<1, 32, 0, stream>>>(P);
+    ok(cudaGetLastError());
+  }
+  KCtl h{};
+  ok(cudaMemcpyAsync(&h, A + lay.ctl, sizeof(KCtl), cudaMemcpyDeviceToHost, stream));
+  ok(cudaStreamSynchronize(stream));
+  if (e != cudaSuccess) return KP_ERR_CUDA;
+  if (h.err == KP_DEV_ERR_TIMEOUT) return KP_ERR_TIMEOUT;
+  if (h.err != 0) return KP_ERR_CUDA;
+  if (h.state == KP_DEV_BAD_ROOT) return KP_ERR_ARG;
+  traj->n_edges = 0;
+  if (h.state != KP_DEV_SOLVED || h.n_edges < 0) return KP_NO_SOLUTION;
+  traj->n_edges = h.n_edges;
+  if (h.n_edges > traj->capacity || h.n_edges > KP_TRAJ_ROWS) return KP_ERR_ARG;
+  const int n = h.n_edges;
+  if (n > 0) {
+    const char* rows = A + lay.traj;
+    ok(cudaMemcpy2DAsync(traj->states, 12 * 4, rows, 17 * 4, 12 * 4, n, cudaMemcpyDeviceToHost,
+                         stream));
+    ok(cudaMemcpy2DAsync(traj->ctrls, 4 * 4, rows + 12 * 4, 17 * 4, 4 * 4, n,
+                         cudaMemcpyDeviceToHost, stream));
+    ok(cudaMemcpy2DAsync(traj->steps, 4, rows + 16 * 4, 17 * 4, 4, n, cudaMemcpyDeviceToHost,
+                         stream));
+    ok(cudaStreamSynchronize(stream));
+    if (e != cudaSuccess) return KP_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {  // the rows carry the step count as a float
+      float f;
+      std::memcpy(&f, &traj->steps[i], 4);
+      traj->steps[i] = (int32_t)f;
+    }
+  }
+  return KP_OK;
+}

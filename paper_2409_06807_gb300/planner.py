@@ -116,6 +116,9 @@ SIGNATURES = {
     "kp_set_sample_log": (C.c_int, [_vp, C.POINTER(SampleLog)]),
     "kp_set_wait_limit": (C.c_int, [_vp, C.c_uint64]),
     "kp_selftest_wait_timeout": (C.c_int, [_vp]),
+    "kp_plan_static": (C.c_int, [C.POINTER(System), C.POINTER(Workspace), C.POINTER(Obstacles),
+                                 C.POINTER(Params), C.POINTER(C.c_float), C.POINTER(Goal),
+                                 C.POINTER(Budget), C.POINTER(Traj), _vp]),
     "kp_last_error": (C.c_char_p, [_vp]),
     "kp_destroy": (None, [_vp]),
 }

@@ -1,0 +1,73 @@
+"""kp_plan_static: the planning query for callers that cannot allocate.
+
+Some callers may not allocate device memory at all (a host application
+that owns all device memory through its own pool, a plugin inside such a
+process, a real-time control loop that cannot afford an allocation's
+implicit synchronisation).  kp_plan_static serves them from a fixed static
+device scratch.  These tests call it through the C ABI and check that it
+returns what the arena-based kp_plan returns for the same query, on two
+calls in a row (the second call runs on the scratch the first one left
+behind), and that an oversized problem is refused before any device work.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2409_06807_gb300 import workloads as W
+from parity_util import state_scale
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2409_06807_gb300.build import build_planner
+    build_planner()
+    from paper_2409_06807_gb300 import planner
+    return planner
+
+
+def static_plan(P, w, max_iters=200, capacity=1024):
+    import torch
+    sys_, ws, prm = P.structs(w)
+    boxes = np.ascontiguousarray(np.asarray(w.boxes, np.float32).reshape(-1, 6))
+    obs = P.Obstacles(boxes.ctypes.data_as(C.POINTER(C.c_float)) if len(boxes) else None,
+                      len(boxes))
+    x = np.ascontiguousarray(w.x_init, np.float32)
+    g = P.goal_struct(w)
+    b = P.Budget(max_iters, 0.0)
+    states = np.zeros((capacity, 12), np.float32)
+    ctrls = np.zeros((capacity, 4), np.float32)
+    steps = np.zeros(capacity, np.int32)
+    t = P.Traj(capacity, 0, states.ctypes.data_as(C.POINTER(C.c_float)),
+               ctrls.ctypes.data_as(C.POINTER(C.c_float)),
+               steps.ctypes.data_as(C.POINTER(C.c_int32)))
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = P.lib().kp_plan_static(C.byref(sys_), C.byref(ws), C.byref(obs), C.byref(prm),
+                                x.ctypes.data_as(C.POINTER(C.c_float)), C.byref(g), C.byref(b),
+                                C.byref(t), stream)
+    n = t.n_edges
+    return st, dict(states=states[:n, : w.d], ctrls=ctrls[:n, : w.n_ctrl], steps=steps[:n])
+
+
+def test_static_plan_matches_kp_plan_on_consecutive_calls(P):
+    for seed in (0, 1):  # two calls in a row share the static scratch
+        w = W.c1(seed)
+        st_ref, ref = P.Planner(w).plan(max_iters=200, capacity=1024)
+        st, got = static_plan(P, w)
+        assert st == st_ref == P.OK
+        assert np.array_equal(got["steps"], ref["steps"])
+        scale = state_scale(w)
+        assert np.max(np.abs(got["states"] - ref["states"]) / scale) <= 1e-4
+        span = np.asarray(w.u_hi[: w.n_ctrl]) - np.asarray(w.u_lo[: w.n_ctrl])
+        assert np.max(np.abs(got["ctrls"] - ref["ctrls"]) / span) <= 1e-6
+
+
+def test_static_plan_refuses_oversized_problem(P):
+    w = W.c2(0)  # t_e = 2^20: its arena is far above the static maximum
+    st, _ = static_plan(P, w)
+    assert st == P.ERR_OOM
