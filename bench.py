@@ -41,16 +41,18 @@ KCTL_BYTES = 512
 # per sample: two Philox4x32-10 blocks (10 rounds x 10 integer ops each),
 # the control and duration maps, binning, counters and flags;
 # per integrator step: the integrator itself plus the state-box test;
-# per step hull: its 6 min/max plus 8 ops for every obstacle box tested.
+# per step hull: its 6 min/max and the broad-phase cell range (6 x 5 ops);
+# per hull-vs-box test: 8 ops, counted over the boxes the uniform-grid broad
+# phase leaves to test (the pruned count, not every box of the layout).
 OPS_PER_SAMPLE = {W.DI: 200 + 11 + 30, W.DUBINS: 200 + 11 + 30, W.QUAD: 200 + 14 + 34}
 OPS_PER_STEP = {W.DI: 6 + 18, W.DUBINS: 222 + 18, W.QUAD: 688 + 36}
 OPS_PER_BOX = 8
-OPS_PER_HULL = 6
+OPS_PER_HULL = 6 + 30
 
 
-def alg_ops(system, n_boxes, samples, steps, hulls):
+def alg_ops(system, samples, steps, hulls, box_tests):
     return (OPS_PER_SAMPLE[system] * samples + OPS_PER_STEP[system] * steps
-            + (OPS_PER_HULL + OPS_PER_BOX * n_boxes) * hulls)
+            + OPS_PER_HULL * hulls + OPS_PER_BOX * box_tests)
 
 
 def peaks():
@@ -319,8 +321,10 @@ def run_ours(args, world, rank, local):
     value = samples_all / (total_ms_max / 1e3)
 
     # roofline of the persistent loop kernel (dominant kernel)
-    ops = sum(alg_ops(w0.system, len(layouts[args.warmup + j].boxes), r[3]["n_samples"],
-                      r[3]["n_steps"], r[3]["n_hull_checks"]) for j, r in enumerate(rows))
+    ops = sum(alg_ops(w0.system, r[3]["n_samples"], r[3]["n_steps"], r[3]["n_hull_checks"],
+                      r[3]["n_box_tests"]) for r in rows)
+    box_tests_per_hull = (sum(r[3]["n_box_tests"] for r in rows)
+                          / max(1, sum(r[3]["n_hull_checks"] for r in rows)))
     pk, pk_kind = peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     peak_ops = n_sm * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12  # Top/s
@@ -359,6 +363,10 @@ def run_ours(args, world, rank, local):
                      "mean": float(np.mean(step_ms))},
         "success_rate": solved / len(rows),
         "loop_kernel_ms": {"mean": float(np.mean(loop_ms))},
+        "work": {"samples_per_step": samples / len(rows),
+                 "steps_per_sample": sum(r[3]["n_steps"] for r in rows) / max(1, samples),
+                 "box_tests_per_hull": box_tests_per_hull,
+                 "broad_phase_cells": rows[-1][3]["bp_cells"]},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
                      "frac": achieved / peak_ops, "traffic": traffic,
                      "peak_source": f"{n_sm} SMs x 128 lanes x {pk.get('sm_max_mhz')} MHz "

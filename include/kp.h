@@ -82,7 +82,8 @@ typedef struct {
 } kp_workspace;
 
 /* Obstacle set O (Sec. II): closed axis-aligned boxes, host pointer to
- * n_boxes rows of {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z}; copied. */
+ * n_boxes rows of {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z} with lo <= hi on
+ * every axis (KP_ERR_ARG otherwise); copied. */
 typedef struct {
   const float *boxes;
   int32_t n_boxes;            /* 0 .. KP_MAX_BOXES                          */
@@ -148,6 +149,8 @@ typedef struct {
   int64_t n_samples;   /* samples propagated and checked                   */
   int64_t n_steps;     /* integrator steps run (each one checked)          */
   int64_t n_hull_checks; /* step hulls tested against the obstacle set     */
+  int64_t n_box_tests;   /* hull-vs-box tests made (after the broad phase)   */
+  int32_t bp_cells;      /* broad-phase grid cells per axis                  */
 } kp_info;
 
 /* Host-side copy of the tree and decomposition (tests, checkpoints).

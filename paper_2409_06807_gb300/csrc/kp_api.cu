@@ -122,7 +122,7 @@ Layout make_layout(const Dims& d) {
   };
   const size_t te = (size_t)d.t_e;
   L.ctl = take(sizeof(KCtl));
-  L.boxes = take((size_t)KP_MAX_BOXES * 32);  // room for any obstacle set
+  L.boxes = take((size_t)KP_BLOB_BYTES);  // room for any obstacle set and its grid
   L.st = take(te * d.D * 4);
   L.parent = take(te * 4);
   L.ctrl = take(te * d.N * 4);
@@ -337,38 +337,111 @@ kp_status read_ctl(kp_ctx* ctx, KCtl* out) {
   return KP_OK;
 }
 
-kp_status configure_launch(kp_ctx* ctx);
 
-kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
-  const int nb = obs ? obs->n_boxes : 0;
-  if (nb < 0 || nb > ctx->n_boxes_cap) return fail(ctx, KP_ERR_ARG, "box count above capacity");
-  if (nb > 0 && !obs->boxes) return fail(ctx, KP_ERR_ARG, "null boxes");
+size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Broad-phase cell of a coordinate: the device's bp_cell in host FP32.
+int host_bp_cell(float v, float lo, float scale, int g) {
+  const float t = (v - lo) * scale;
+  return t >= 0.0f ? (t < (float)g ? (int)t : g - 1) : 0;
+}
+
+// Writes the obstacle blob (padded boxes, then the broad-phase grid: cell
+// start offsets and box ids of every cell a box overlaps) into 'blob' and
+// sets the blob fields of P.  The grid is the finest of 16^3, 8^3, 4^3,
+// 2^3, 1 cells whose entry count fits KP_BP_MAX_IDS (1 cell = every box).
+size_t build_blob(unsigned char* blob, const float* boxes, int nb, const kp_workspace& ws,
+                  KParams& P) {
   const int pad = (nb + 7) / 8 * 8;
-  // stage the padded rows in pinned host memory, then one async copy
-  kp_status ps = ensure_pinned(ctx, (size_t)pad * 32 + sizeof(KCtl));
-  if (ps != KP_OK) return ps;
-  KP_CUDA(cudaStreamSynchronize(ctx->stream));  // the staging buffer is free
-  float* host = static_cast<float*>(ctx->pinned);
+  float* fb = reinterpret_cast<float*>(blob);
   for (int b = 0; b < pad; ++b) {
-    float* o = host + (size_t)b * 8;
+    float* o = fb + (size_t)b * 8;
     if (b < nb) {
-      const float* in = obs->boxes + (size_t)b * 6;
-      for (int i = 0; i < 6; ++i)
-        if (std::isnan(in[i])) return fail(ctx, KP_ERR_ARG, "NaN in box %d", b);
-      o[0] = in[0]; o[1] = in[1]; o[2] = in[2]; o[3] = 0.0f;
-      o[4] = in[3]; o[5] = in[4]; o[6] = in[5]; o[7] = 0.0f;
+      const float* in = boxes + (size_t)b * 6;
+      // + 0.0f: no negative zeros reach the sign-bit box test
+      o[0] = in[0] + 0.0f; o[1] = in[1] + 0.0f; o[2] = in[2] + 0.0f; o[3] = 0.0f;
+      o[4] = in[3] + 0.0f; o[5] = in[4] + 0.0f; o[6] = in[5] + 0.0f; o[7] = 0.0f;
     } else {  // padding: an empty box no hull can meet
       o[0] = o[1] = o[2] = INFINITY;
       o[4] = o[5] = o[6] = -INFINITY;
       o[3] = o[7] = 0.0f;
     }
   }
-  if (pad > 0)
-    KP_CUDA(cudaMemcpyAsync(ctx->arena + ctx->lay.boxes, host, (size_t)pad * 32,
-                            cudaMemcpyHostToDevice, ctx->stream));
+  int g = nb > 0 ? KP_BP_MAX_G : 1;
+  float scale[3];
+  for (;; g /= 2) {
+    long long entries = 0;
+    for (int a = 0; a < 3; ++a)
+      scale[a] = (float)((double)g / ((double)ws.hi[a] - (double)ws.lo[a]));
+    for (int b = 0; b < nb; ++b) {
+      long long cells = 1;
+      for (int a = 0; a < 3; ++a)
+        cells *= host_bp_cell(fb[b * 8 + 4 + a], ws.lo[a], scale[a], g) -
+                 host_bp_cell(fb[b * 8 + a], ws.lo[a], scale[a], g) + 1;
+      entries += cells;
+    }
+    if (entries <= KP_BP_MAX_IDS || g == 1) break;
+  }
+  const int C = g * g * g;
+  const size_t start_off = (size_t)pad * 32;
+  const size_t ids_off = start_off + round16((size_t)(C + 1) * 4);
+  int* start = reinterpret_cast<int*>(blob + start_off);
+  uint16_t* ids = reinterpret_cast<uint16_t*>(blob + ids_off);
+  std::vector<int> lo3((size_t)nb * 3), hi3((size_t)nb * 3);
+  for (int c = 0; c <= C; ++c) start[c] = 0;
+  for (int b = 0; b < nb; ++b) {
+    for (int a = 0; a < 3; ++a) {
+      lo3[b * 3 + a] = host_bp_cell(fb[b * 8 + a], ws.lo[a], scale[a], g);
+      hi3[b * 3 + a] = host_bp_cell(fb[b * 8 + 4 + a], ws.lo[a], scale[a], g);
+    }
+    for (int z = lo3[b * 3 + 2]; z <= hi3[b * 3 + 2]; ++z)
+      for (int y = lo3[b * 3 + 1]; y <= hi3[b * 3 + 1]; ++y)
+        for (int x = lo3[b * 3]; x <= hi3[b * 3]; ++x) start[x + g * (y + g * z) + 1] += 1;
+  }
+  for (int c = 0; c < C; ++c) start[c + 1] += start[c];
+  std::vector<int> cursor(start, start + C);
+  for (int b = 0; b < nb; ++b)
+    for (int z = lo3[b * 3 + 2]; z <= hi3[b * 3 + 2]; ++z)
+      for (int y = lo3[b * 3 + 1]; y <= hi3[b * 3 + 1]; ++y)
+        for (int x = lo3[b * 3]; x <= hi3[b * 3]; ++x) ids[cursor[x + g * (y + g * z)]++] = (uint16_t)b;
+  const size_t bytes = ids_off + round16((size_t)start[C] * 2);
+  P.n_boxes_pad = pad;
+  P.blob_bytes = (int32_t)bytes;
+  P.bp_g = g;
+  P.bp_start_off = (int32_t)start_off;
+  P.bp_ids_off = (int32_t)ids_off;
+  for (int a = 0; a < 3; ++a) P.bp_scale[a] = scale[a];
+  return bytes;
+}
+
+// Closed boxes need lo <= hi on every axis and no NaN.
+const char* check_boxes(const float* boxes, int nb) {
+  for (int b = 0; b < nb; ++b)
+    for (int a = 0; a < 3; ++a) {
+      const float lo = boxes[(size_t)b * 6 + a], hi = boxes[(size_t)b * 6 + 3 + a];
+      if (std::isnan(lo) || std::isnan(hi)) return "NaN in a box";
+      if (!(lo <= hi)) return "box with lo > hi";
+    }
+  return nullptr;
+}
+
+kp_status configure_launch(kp_ctx* ctx);
+
+kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
+  const int nb = obs ? obs->n_boxes : 0;
+  if (nb < 0 || nb > ctx->n_boxes_cap) return fail(ctx, KP_ERR_ARG, "box count above capacity");
+  if (nb > 0 && !obs->boxes) return fail(ctx, KP_ERR_ARG, "null boxes");
+  if (const char* m = check_boxes(nb > 0 ? obs->boxes : nullptr, nb)) return fail(ctx, KP_ERR_ARG, "%s", m);
+  // build the blob in pinned host memory, then one async copy
+  kp_status ps = ensure_pinned(ctx, (size_t)KP_BLOB_BYTES + sizeof(KCtl));
+  if (ps != KP_OK) return ps;
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));  // the staging buffer is free
+  unsigned char* host = static_cast<unsigned char*>(ctx->pinned);
+  const size_t bytes = build_blob(host, nb > 0 ? obs->boxes : nullptr, nb, ctx->ws, ctx->P);
+  KP_CUDA(cudaMemcpyAsync(ctx->arena + ctx->lay.boxes, host, bytes, cudaMemcpyHostToDevice,
+                          ctx->stream));
   KP_CUDA(cudaStreamSynchronize(ctx->stream));
-  ctx->P.n_boxes_pad = pad;
-  ctx->dims.boxes_pad = pad;
+  ctx->dims.boxes_pad = ctx->P.n_boxes_pad;
   ctx->have_tree = false;
   return configure_launch(ctx);
 }
@@ -378,7 +451,7 @@ kp_status configure_launch(kp_ctx* ctx) {
   // shared memory: boxes + the double scratch of the region-score sums
   const int min_ch = d.R_pad / (d.R_pad < 128 ? d.R_pad : 128);
   const int sd = min_ch > 1024 ? min_ch : 1024;
-  ctx->smem = (size_t)d.boxes_pad * 32 + (size_t)sd * 8;
+  ctx->smem = (size_t)ctx->P.blob_bytes + (size_t)sd * 8;
   for (int log = 0; log < 2; ++log) {
     int bps = 0;
     KP_CUDA(occupancy(d.sys, log != 0, ctx->smem, &bps));
@@ -729,6 +802,8 @@ kp_status kp_get_info(kp_ctx* ctx, kp_info* out) {
   out->n_samples = ctx->have_tree ? (int64_t)h.tot_samples : 0;
   out->n_steps = ctx->have_tree ? (int64_t)h.tot_steps : 0;
   out->n_hull_checks = ctx->have_tree ? (int64_t)h.tot_hull : 0;
+  out->n_box_tests = ctx->have_tree ? (int64_t)h.tot_box_tests : 0;
+  out->bp_cells = ctx->P.bp_g;
   out->n_boxes = ctx->P.n_boxes_pad;
   out->grid_blocks = ctx->grid[ctx->log_on ? 1 : 0];
   return KP_OK;
@@ -933,19 +1008,29 @@ constexpr int kStaticMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_base[kStaticMaxDevices];  // device address of the scratch, per device
 
-// Raw {lo, hi} box rows -> the padded float4 pairs the loop kernel reads.
-__global__ void kp_static_pad_boxes_kernel(float* dst, const float* raw, int n, int pad) {
+// Raw {lo, hi} box rows -> the obstacle blob the loop kernel reads, with a
+// one-cell broad-phase grid (every box in the single cell).
+__global__ void kp_static_blob_kernel(unsigned char* blob, const float* raw, int n, int pad,
+                                      int start_off, int ids_off) {
+  float* dst = reinterpret_cast<float*>(blob);
+  int* start = reinterpret_cast<int*>(blob + start_off);
+  uint16_t* ids = reinterpret_cast<uint16_t*>(blob + ids_off);
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < pad; b += gridDim.x * blockDim.x) {
     float* o = dst + (size_t)b * 8;
     if (b < n) {
       const float* in = raw + (size_t)b * 6;
-      o[0] = in[0]; o[1] = in[1]; o[2] = in[2]; o[3] = 0.0f;
-      o[4] = in[3]; o[5] = in[4]; o[6] = in[5]; o[7] = 0.0f;
+      o[0] = in[0] + 0.0f; o[1] = in[1] + 0.0f; o[2] = in[2] + 0.0f; o[3] = 0.0f;
+      o[4] = in[3] + 0.0f; o[5] = in[4] + 0.0f; o[6] = in[5] + 0.0f; o[7] = 0.0f;
+      ids[b] = (uint16_t)b;
     } else {
       o[0] = o[1] = o[2] = INFINITY;
       o[4] = o[5] = o[6] = -INFINITY;
       o[3] = o[7] = 0.0f;
     }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    start[0] = 0;
+    start[1] = n;
   }
 }
 
@@ -960,8 +1045,7 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   Dims d{};
   if (check_inputs(sys, ws, nb, prm, &d)) return KP_ERR_ARG;
   if (nb > 0 && !obs->boxes) return KP_ERR_ARG;
-  for (int i = 0; i < 6 * nb; ++i)
-    if (std::isnan(obs->boxes[i])) return KP_ERR_ARG;
+  if (check_boxes(nb > 0 ? obs->boxes : nullptr, nb)) return KP_ERR_ARG;
   for (int i = 0; i < d.D; ++i)
     if (std::isnan(x_init[i])) return KP_ERR_ARG;
   if (!(goal->radius >= 0.0f) || std::isnan(goal->center[0]) || std::isnan(goal->center[1]) ||
@@ -998,6 +1082,11 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   fill_params(P, d, lay, sys, ws, prm, A);
   const int pad = (nb + 7) / 8 * 8;
   P.n_boxes_pad = pad;
+  P.bp_g = 1;
+  P.bp_start_off = pad * 32;
+  P.bp_ids_off = P.bp_start_off + 16;
+  P.blob_bytes = P.bp_ids_off + (int32_t)round16((size_t)nb * 2);
+  for (int a = 0; a < 3; ++a) P.bp_scale[a] = (float)(1.0 / ((double)ws->hi[a] - (double)ws->lo[a]));
   for (int a = 0; a < 3; ++a) P.goal_c[a] = goal->center[a];
   P.goal_r2 = (float)((double)goal->radius * (double)goal->radius);
   P.seed_lo = (uint32_t)(prm->seed & 0xffffffffu);
@@ -1013,7 +1102,7 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   }
   const int min_ch = d.R_pad / (d.R_pad < 128 ? d.R_pad : 128);
   const int sd = min_ch > 1024 ? min_ch : 1024;
-  const size_t smem = (size_t)pad * 32 + (size_t)sd * 8;
+  const size_t smem = (size_t)P.blob_bytes + (size_t)sd * 8;
   if (occupancy(d.sys, false, smem, &bps) != cudaSuccess || bps < 1) {
     cudaGetLastError();
     return KP_ERR_CUDA;
@@ -1031,13 +1120,12 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   };
   // obstacles: raw rows into the (not yet used) trajectory rows, padded on
   // the device into the box slots
-  if (nb > 0) {
+  if (nb > 0)
     ok(cudaMemcpyAsync(A + lay.traj, obs->boxes, (size_t)nb * 24, cudaMemcpyHostToDevice, stream));
-    kp_static_pad_boxes_kernel<<<(pad + 255) / 256, 256, 0, stream>>>(
-        reinterpret_cast<float*>(A + lay.boxes), reinterpret_cast<const float*>(A + lay.traj), nb,
-        pad);
-    ok(cudaGetLastError());
-  }
+  kp_static_blob_kernel<<<(pad + 255) / 256 > 0 ? (pad + 255) / 256 : 1, 256, 0, stream>>>(
+      reinterpret_cast<unsigned char*>(A + lay.boxes), reinterpret_cast<const float*>(A + lay.traj),
+      nb, pad, P.bp_start_off, P.bp_ids_off);
+  ok(cudaGetLastError());
   // everything that must start from zero (the scratch keeps old contents)
   ok(cudaMemsetAsync(A + lay.ctl, 0, sizeof(KCtl), stream));
   ok(cudaMemsetAsync(A + lay.visited, 0, d.n_sub, stream));

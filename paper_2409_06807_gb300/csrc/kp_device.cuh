@@ -343,4 +343,60 @@ __device__ __forceinline__ bool hull_hits_boxes(const float4* __restrict__ sb, i
   return false;
 }
 
+// Closed-box overlap of the hull [l, h] with box (bl, bh), on the FP32 add
+// pipe: the boxes meet iff all six differences bh - l and h - bl are >= 0,
+// i.e. iff none has its sign bit set.  Exact for finite or infinite inputs
+// without negative zeros (the caller canonicalises the hull with + 0.0f;
+// the host does the same for the boxes): a - b is +0 when a == b and
+// negative (never -0) when a < b, because the difference of two floats
+// never rounds to zero.
+__device__ __forceinline__ bool box_meets_hull(float4 bl, float4 bh, float lx, float ly,
+                                               float lz, float hx, float hy, float hz) {
+  const uint32_t s = __float_as_uint(bh.x - lx) | __float_as_uint(hx - bl.x) |
+                     __float_as_uint(bh.y - ly) | __float_as_uint(hy - bl.y) |
+                     __float_as_uint(bh.z - lz) | __float_as_uint(hz - bl.z);
+  return (int32_t)s >= 0;
+}
+
+// Broad-phase cell of a coordinate (same FP32 arithmetic as the host build).
+__device__ __forceinline__ int bp_cell(float v, float lo, float scale, int g) {
+  const float t = __fmul_rn(__fsub_rn(v, lo), scale);
+  return t >= 0.0f ? (t < (float)g ? (int)t : g - 1) : 0;
+}
+
+// Exact coarse-then-fine collision test of a step hull (the paper's coarse
+// phase, Sec. III-B): only boxes listed in the uniform-grid cells the hull
+// touches are tested.  A box meeting the hull shares a point with it; that
+// point's cell lies in both cell ranges (the cell map is monotone), so the
+// box is in one of the visited lists: the verdict equals testing every box.
+// 'tests' counts the box tests made.
+__device__ __forceinline__ bool hull_hits_grid(const KParams& P, const float4* __restrict__ sbox,
+                                               const int* __restrict__ sstart,
+                                               const uint16_t* __restrict__ sids, float lx,
+                                               float ly, float lz, float hx, float hy, float hz,
+                                               uint32_t* tests) {
+  const int g = P.bp_g;
+  const int x0 = bp_cell(lx, P.ws_lo[0], P.bp_scale[0], g), x1 = bp_cell(hx, P.ws_lo[0], P.bp_scale[0], g);
+  const int y0 = bp_cell(ly, P.ws_lo[1], P.bp_scale[1], g), y1 = bp_cell(hy, P.ws_lo[1], P.bp_scale[1], g);
+  const int z0 = bp_cell(lz, P.ws_lo[2], P.bp_scale[2], g), z1 = bp_cell(hz, P.ws_lo[2], P.bp_scale[2], g);
+  uint32_t n = 0;
+  bool hit = false;
+  for (int cz = z0; cz <= z1 && !hit; ++cz)
+    for (int cy = y0; cy <= y1 && !hit; ++cy)
+      for (int cx = x0; cx <= x1 && !hit; ++cx) {
+        const int c = cx + g * (cy + g * cz);
+        const int e = sstart[c + 1];
+        for (int q = sstart[c]; q < e; ++q) {
+          const int b = sids[q];
+          ++n;
+          if (box_meets_hull(sbox[2 * b], sbox[2 * b + 1], lx, ly, lz, hx, hy, hz)) {
+            hit = true;
+            break;
+          }
+        }
+      }
+  *tests += n;
+  return hit;
+}
+
 }  // namespace kp

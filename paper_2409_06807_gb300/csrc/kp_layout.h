@@ -28,6 +28,10 @@ constexpr int KP_BLOCK = 256;          // threads per block of the loop kernel
 constexpr int KP_MAX_GRID = 8192;      // upper bound on loop-kernel blocks
 constexpr int KP_NO_GOAL = 0x7fffffff; // goal_node sentinel on the device
 constexpr int KP_TRAJ_ROWS = 16384;    // longest root-to-goal chain returned
+constexpr int KP_BP_MAX_G = 16;        // finest broad-phase grid per axis
+constexpr int KP_BP_MAX_IDS = 32768;   // broad-phase (cell, box) entries
+constexpr int KP_BLOB_BYTES = 4096 * 32 + (KP_BP_MAX_G * KP_BP_MAX_G * KP_BP_MAX_G + 4) * 4 +
+                              KP_BP_MAX_IDS * 2;  // arena room for the obstacle blob
 
 // Device control block (one per context, in the arena).
 struct KCtl {
@@ -43,12 +47,13 @@ struct KCtl {
   int32_t stop;        // loop stop flag inside a launch
   uint32_t it_valid;   // valid samples of the current pass
   int32_t n_edges;     // trajectory extraction: edges on the chain
-  int32_t pad0[1];
+  int32_t work_next;   // next sample key handed out in the expand phase
   // work counters since the last reset (samples, integrator steps run,
   // segment hulls tested against the obstacle set)
   unsigned long long tot_samples;
   unsigned long long tot_steps;
   unsigned long long tot_hull;
+  unsigned long long tot_box_tests;
   // barrier words on their own 128-byte line
   uint32_t bar_count;
   uint32_t pad1[31];
@@ -110,9 +115,16 @@ struct KParams {
   int32_t lambda_max;
   double delta, eps, vol;
   uint32_t seed_lo, seed_hi;
-  // obstacles: [n_boxes_pad][8] floats (lo.xyz, pad, hi.xyz, pad)
+  // obstacles: a blob staged whole into shared memory:
+  //   [n_boxes_pad][8] floats (lo.xyz, pad, hi.xyz, pad), then the
+  //   broad-phase grid: int32 cell_start[bp_g^3 + 1], uint16 ids[...]
   const float* boxes;
   int32_t n_boxes_pad;
+  int32_t blob_bytes;
+  int32_t bp_g;          // broad-phase cells per axis (1 = every box in one cell)
+  int32_t bp_start_off;  // byte offsets inside the blob
+  int32_t bp_ids_off;
+  float bp_scale[3];     // cells per unit length, per axis
   // tree, SoA over t_e nodes
   float* st;          // [D][t_e]
   int32_t* parent;

@@ -37,10 +37,11 @@ struct LoopShared {
   int flag;
 };
 
-// Stage the obstacle boxes into shared memory with bulk asynchronous copies
-// (TMA engine) completing on one mbarrier.  Returns false on a wait timeout.
+// Stage the obstacle blob (boxes and broad-phase grid) into shared memory
+// with bulk asynchronous copies (TMA engine) completing on one mbarrier.
+// Returns false on a wait timeout.
 __device__ __forceinline__ bool stage_boxes(const KParams& P, float4* sbox, LoopShared& sh) {
-  const uint32_t bytes = (uint32_t)P.n_boxes_pad * 32u;
+  const uint32_t bytes = (uint32_t)P.blob_bytes;  // multiple of 16
   if (bytes == 0) return true;
   const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&sh.mbar);
   const uint32_t dst0 = (uint32_t)__cvta_generic_to_shared(sbox);
@@ -51,7 +52,7 @@ __device__ __forceinline__ bool stage_boxes(const KParams& P, float4* sbox, Loop
                  : "memory");
     const uint32_t piece = 16384u;  // several copies of <= 16 KB each
     for (uint32_t off = 0; off < bytes; off += piece) {
-      const uint32_t n = bytes - off < piece ? bytes - off : piece;  // multiple of 32
+      const uint32_t n = bytes - off < piece ? bytes - off : piece;  // multiple of 16
       asm volatile(
           "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
           "[%3];" ::"r"(dst0 + off),
@@ -152,99 +153,177 @@ __device__ __forceinline__ int write_ve(const KParams& P, int n, LoopShared& sh)
 }
 
 // Phase E: Algorithm 2 for every sample key in [0, S).
+//
+// Lanes integrate step by step and are refilled as they finish: a warp
+// takes keys in batches from a grid-wide counter, every lane carries one
+// sample (k steps, or fewer when a step is invalid), and when enough lanes
+// of the warp have finished they are finalised (binning, counters, claim,
+// candidate payload) and given new keys together, so that the divergent
+// finalise / start-up work is shared by many lanes and no lane idles while
+// a long sample runs next to it.  Every sample's arithmetic depends on its
+// key alone, so the result does not depend on which lane ran it.
+constexpr int KP_REFILL_MIN = 8;  // lanes that must be free before a refill
+constexpr int KP_KEY_BATCH = 128; // keys a warp takes from the grid counter
+
 template <int SYS, bool LOG>
-__device__ __forceinline__ void phase_expand(const KParams& P, const float4* sbox, uint32_t it,
-                                             int lam, int S, LoopShared& sh) {
+__device__ __forceinline__ void phase_expand(const KParams& P, const unsigned char* sblob,
+                                             uint32_t it, int lam, int S, LoopShared& sh) {
   using Sys = System<SYS>;
   constexpr int D = Sys::D, N = Sys::N;
-  const int stride = gridDim.x * blockDim.x;
+  const float4* sbox = reinterpret_cast<const float4*>(sblob);
+  const int* sstart = reinterpret_cast<const int*>(sblob + P.bp_start_off);
+  const uint16_t* sids = reinterpret_cast<const uint16_t*>(sblob + P.bp_ids_off);
+  const uint32_t FULL = 0xffffffffu;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt = (1u << lane) - 1u;
+
   unsigned long long n_steps = 0, n_hull = 0;
-  for (int key = blockIdx.x * blockDim.x + threadIdx.x; key < S; key += stride) {
-    const int p = key / lam;
-    const int j = key - p * lam;
-    const int v = P.ve[p];
-    float x[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) x[i] = P.st[(size_t)i * P.t_e + v];
-    // random control in U and duration k * dt (counter: it, node, j, purpose)
-    const uint4 w0 = philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 0u), P.seed_lo, P.seed_hi);
-    const uint4 w1 = philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 1u), P.seed_lo, P.seed_hi);
-    const uint32_t wr[4] = {w0.x, w0.y, w0.z, w0.w};
-    float u[4];
-#pragma unroll
-    for (int i = 0; i < N; ++i) u[i] = fmaf(P.u_scale[i], unit24(wr[i]), P.u_lo[i]);
-    const int k = P.k_min + (int)__umulhi(w1.x, P.k_span);
-    // PropagateODE with the validity check after every integrator step
-    bool valid = true;
-    int fail = 0, hulls = 0;
-    for (int i = 1; i <= k; ++i) {
-      const float px = x[0], py = x[1], pz = x[2];
-      Sys::step(x, u, P.dt, P);
-      bool ok = in_state_box<D>(x, P);
-      if (ok) {
-        ++hulls;
-        ok = !hull_hits_boxes(sbox, P.n_boxes_pad, fminf(px, x[0]), fminf(py, x[1]),
-                              fminf(pz, x[2]), fmaxf(px, x[0]), fmaxf(py, x[1]), fmaxf(pz, x[2]));
-      }
-      if (!ok) {
-        valid = false;
-        fail = i;
+  uint32_t n_box = 0;
+  // lane state: the sample being integrated
+  int key = -1, v = 0, k = 0, i = 0, fail = 0;
+  bool done = false;
+  float x[D], u[N];
+  uint32_t wacc = 0, wr[4] = {0, 0, 0, 0};
+  // warp state (uniform): the current batch of keys
+  int pool_next = 0, pool_end = 0;
+  bool exhausted = S <= 0;
+  // bound on the phase's device time, checked warp-uniformly
+  const uint64_t t_phase = global_ns();
+  uint32_t guard = 0;
+
+  for (;;) {
+    if ((++guard & 1023u) == 0) {
+      const uint64_t now = __shfl_sync(FULL, global_ns(), 0);
+      if (now - t_phase > P.wait_ns) {
+        if (lane == 0) raise_error(P.ctl, KP_DEV_ERR_TIMEOUT, 30);
         break;
       }
     }
-    n_steps += valid ? k : fail;
-    n_hull += hulls;
-    int r, s;
-    bin_state<SYS>(x, P, &r, &s);
-    uint32_t f = 0;
-    if (valid) {
-      atomicAdd(&P.n_valid[r], 1u);
-      f = KP_F_VALID;
-      const bool cont = P.visited[s] == 0;
-      const bool bern = (uint64_t)w1.y < P.thr[r];
-      if (cont) {
-        f |= KP_F_CONTENDER;
-        // the first claimant of a sub-region knows it is newly reached: it
-        // will get exactly one representative in region r
-        if (atomicMin(&P.claim[s], (uint32_t)key) == 0xffffffffu) {
-          atomicAdd(&P.cov[r], 1u);
-          P.avail[r] = 1;
+    const uint32_t m_free = __ballot_sync(FULL, key < 0 || done);
+    if (__popc(m_free) >= KP_REFILL_MIN || (exhausted && m_free)) {
+      // ---- finalise the lanes that finished -------------------------------
+      if (key >= 0 && done) {
+        int r, s;
+        bin_state<SYS>(x, P, &r, &s);
+        const bool valid = fail == 0;
+        uint32_t f = 0;
+        if (valid) {
+          atomicAdd(&P.n_valid[r], 1u);
+          f = KP_F_VALID;
+          const bool cont = P.visited[s] == 0;
+          const bool bern = (uint64_t)wacc < P.thr[r];
+          if (cont) {
+            f |= KP_F_CONTENDER;
+            // the first claimant of a sub-region knows it is newly reached:
+            // it will get exactly one representative in region r
+            if (atomicMin(&P.claim[s], (uint32_t)key) == 0xffffffffu) {
+              atomicAdd(&P.cov[r], 1u);
+              P.avail[r] = 1;
+            }
+          }
+          if (bern) {
+            f |= KP_F_BERN;
+            P.avail[r] = 1;
+          }
+          if (cont || bern) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) P.cst[(size_t)d * P.t_e + key] = x[d];
+#pragma unroll
+            for (int d = 0; d < N; ++d) P.cctrl[(size_t)d * P.t_e + key] = u[d];
+            P.ck[key] = (uint8_t)k;
+            P.cr[key] = r;
+            P.cs[key] = s;
+          }
+        } else {
+          atomicAdd(&P.n_invalid[r], 1u);
         }
-      }
-      if (bern) {
-        f |= KP_F_BERN;
-        P.avail[r] = 1;
-      }
-      if (cont || bern) {
+        P.flags[key] = (uint8_t)f;
+        if (LOG && key < P.log.capacity) {
+          P.log.node[key] = v;
+          P.log.k[key] = k;
 #pragma unroll
-        for (int i = 0; i < D; ++i) P.cst[(size_t)i * P.t_e + key] = x[i];
+          for (int d = 0; d < 4; ++d) P.log.uraw[4 * (size_t)key + d] = wr[d];
+          P.log.fail_step[key] = fail;
+          P.log.region[key] = r;
+          P.log.sub[key] = s;
 #pragma unroll
-        for (int i = 0; i < N; ++i) P.cctrl[(size_t)i * P.t_e + key] = u[i];
-        P.ck[key] = (uint8_t)k;
-        P.cr[key] = r;
-        P.cs[key] = s;
+          for (int d = 0; d < 12; ++d) P.log.state[12 * (size_t)key + d] = d < D ? x[d] : 0.0f;
+        }
+        key = -1;
       }
-    } else {
-      atomicAdd(&P.n_invalid[r], 1u);
+      // ---- hand new keys to the free lanes --------------------------------
+      uint32_t m_idle = __ballot_sync(FULL, key < 0);
+      while (m_idle && !exhausted) {
+        if (pool_next >= pool_end) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&P.ctl->work_next, KP_KEY_BATCH);
+          base = __shfl_sync(FULL, base, 0);
+          if (base >= S) {
+            exhausted = true;
+            break;
+          }
+          pool_next = base;
+          pool_end = base + KP_KEY_BATCH < S ? base + KP_KEY_BATCH : S;
+        }
+        const int avail = pool_end - pool_next;
+        const int rank = __popc(m_idle & lt);
+        if (key < 0 && rank < avail) {
+          key = pool_next + rank;
+          // random control in U and duration k * dt (counter: it, node, j, purpose)
+          const int p = key / lam;
+          const int j = key - p * lam;
+          v = P.ve[p];
+#pragma unroll
+          for (int d = 0; d < D; ++d) x[d] = P.st[(size_t)d * P.t_e + v];
+          const uint4 w0 =
+              philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 0u), P.seed_lo, P.seed_hi);
+          const uint4 w1 =
+              philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 1u), P.seed_lo, P.seed_hi);
+          wr[0] = w0.x; wr[1] = w0.y; wr[2] = w0.z; wr[3] = w0.w;
+#pragma unroll
+          for (int d = 0; d < N; ++d) u[d] = fmaf(P.u_scale[d], unit24(wr[d]), P.u_lo[d]);
+          k = P.k_min + (int)__umulhi(w1.x, P.k_span);
+          wacc = w1.y;
+          i = 0;
+          fail = 0;
+          done = false;
+        }
+        const int n_idle = __popc(m_idle);
+        pool_next += n_idle < avail ? n_idle : avail;
+        m_idle = __ballot_sync(FULL, key < 0);
+      }
+      if (__ballot_sync(FULL, key >= 0) == 0) break;
     }
-    P.flags[key] = (uint8_t)f;
-    if (LOG && key < P.log.capacity) {
-      P.log.node[key] = v;
-      P.log.k[key] = k;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) P.log.uraw[4 * (size_t)key + i] = wr[i];
-      P.log.fail_step[key] = fail;
-      P.log.region[key] = r;
-      P.log.sub[key] = s;
-#pragma unroll
-      for (int i = 0; i < 12; ++i) P.log.state[12 * (size_t)key + i] = i < D ? x[i] : 0.0f;
+    // ---- one integrator step (PropagateODE) and its validity check --------
+    if (key >= 0 && !done) {
+      const float px = x[0], py = x[1], pz = x[2];
+      Sys::step(x, u, P.dt, P);
+      ++i;
+      ++n_steps;
+      bool ok = in_state_box<D>(x, P);
+      if (ok) {
+        ++n_hull;
+        // hull of the step; + 0.0f turns a -0 into +0 for the box test
+        ok = !hull_hits_grid(P, sbox, sstart, sids, fminf(px, x[0]) + 0.0f,
+                             fminf(py, x[1]) + 0.0f, fminf(pz, x[2]) + 0.0f,
+                             fmaxf(px, x[0]) + 0.0f, fmaxf(py, x[1]) + 0.0f,
+                             fmaxf(pz, x[2]) + 0.0f, &n_box);
+      }
+      if (!ok) {
+        done = true;
+        fail = i;
+      } else if (i >= k) {
+        done = true;
+      }
     }
   }
-  unsigned long long bs, bh;
+  unsigned long long bs, bh, bb, dummy;
   block_sum2(n_steps, n_hull, sh.red, &bs, &bh);
+  block_sum2((unsigned long long)n_box, 0, sh.red, &bb, &dummy);
   if (threadIdx.x == 0 && bs) {
     atomicAdd(&P.ctl->tot_steps, bs);
     atomicAdd(&P.ctl->tot_hull, bh);
+    atomicAdd(&P.ctl->tot_box_tests, bb);
   }
 }
 
@@ -272,6 +351,7 @@ __device__ __forceinline__ void phase_accept(const KParams& P, int S, LoopShared
   unsigned long long a, b;
   block_sum2(acc_n, valid_n, sh.red, &a, &b);
   if (threadIdx.x == 0) {
+    if (blockIdx.x == 0) P.ctl->work_next = 0;  // the expand phase is over
     P.blk_a[blockIdx.x] = (uint32_t)a;
     if (b) atomicAdd(&P.ctl->it_valid, (uint32_t)b);
   }
@@ -424,7 +504,7 @@ __global__ void __launch_bounds__(KP_BLOCK) kp_loop_kernel(KParams P, int max_it
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LoopShared sh;
   float4* sbox = reinterpret_cast<float4*>(smem);
-  double* sd = reinterpret_cast<double*>(smem + (size_t)P.n_boxes_pad * 32);
+  double* sd = reinterpret_cast<double*>(smem + (size_t)P.blob_bytes);
   KCtl* ctl = P.ctl;
   const uint32_t G = gridDim.x;
   const uint64_t t_start = global_ns();
@@ -438,6 +518,7 @@ __global__ void __launch_bounds__(KP_BLOCK) kp_loop_kernel(KParams P, int max_it
     ctl->it_valid = 0;
     ctl->stop = 0;
     ctl->n_run = 0;
+    ctl->work_next = 0;
   }
   int n_tree = ctl->n_nodes;
   uint32_t it = (uint32_t)ctl->iteration;
@@ -460,7 +541,7 @@ __global__ void __launch_bounds__(KP_BLOCK) kp_loop_kernel(KParams P, int max_it
   int run = 0;
   for (;;) {
     const int S = n_ve > 0 ? n_ve * lam : 0;
-    phase_expand<SYS, LOG>(P, sbox, it, lam, S, sh);
+    phase_expand<SYS, LOG>(P, smem, it, lam, S, sh);
     if (!grid_sync(ctl, G, P.wait_ns, 20)) return;
     phase_accept(P, S, sh);
     phase_scores(P, nch, sd);
@@ -538,6 +619,8 @@ __global__ void kp_reset_kernel(KParams P, RootState root) {
   ctl->tot_samples = 0;
   ctl->tot_steps = 0;
   ctl->tot_hull = 0;
+  ctl->tot_box_tests = 0;
+  ctl->work_next = 0;
   if (!ok) {
     ctl->state = KP_DEV_BAD_ROOT;
     ctl->n_nodes = 0;

@@ -75,7 +75,8 @@ class Info(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("n_nodes", "n_ve", "iteration", "goal_node", "state",
                                            "n_regions", "n_subregions", "state_dim",
                                            "control_dim", "n_boxes", "grid_blocks")] + \
-        [(n, C.c_int64) for n in ("n_samples", "n_steps", "n_hull_checks")]
+        [(n, C.c_int64) for n in ("n_samples", "n_steps", "n_hull_checks", "n_box_tests")] + \
+        [("bp_cells", C.c_int32)]
 
 
 class TreeView(C.Structure):

@@ -265,3 +265,37 @@ def test_bounded_wait_reports_timeout(P):
     assert e.value.status == P.ERR_STATE
     h = P.Planner(w)
     assert h.reset() == P.OK
+
+
+def test_broad_phase_coarsens_for_large_boxes(P):
+    """Many boxes spanning most of the workspace overflow the finest
+    broad-phase grid; the planner coarsens it and the verdicts still match
+    the oracle's test of every box."""
+    rng = np.random.default_rng(7)
+    n = 600
+    lo = rng.uniform(0.0, 0.45, (n, 3)).astype(np.float32)
+    hi = (lo + rng.uniform(0.3, 0.5, (n, 3))).astype(np.float32)
+    boxes = np.concatenate([lo, hi], 1)
+    w = W.tiny(W.DI, seed=3, t_e=3000, lambda_max=16)
+    p0 = w.x_init[:3]
+    keep = ~np.all((boxes[:, :3] <= p0 + 0.06) & (boxes[:, 3:] >= p0 - 0.06), axis=1)
+    w = w.with_(boxes=boxes[keep][:400])
+    g = P.Planner(w)
+    g.reset()
+    assert g.info()["bp_cells"] < 16
+    exact, ran = lockstep(P, w, 6)
+    assert exact >= min(ran, 2)
+
+
+def test_boxes_on_cell_faces(P):
+    """Boxes whose faces sit exactly on broad-phase cell faces (multiples
+    of 1/16) and a sample path along them: verdicts match the oracle."""
+    boxes = []
+    for i in range(1, 15, 3):
+        for j in range(1, 15, 4):
+            boxes.append([i / 16, j / 16, 0.0, (i + 1) / 16, (j + 1) / 16, 1.0])
+    boxes = np.asarray(boxes, np.float32)
+    w = W.tiny(W.DI, seed=0, t_e=4000, lambda_max=16, n_boxes=0).with_(
+        boxes=boxes, x_init=np.array([0.03, 0.03, 0.5, 0, 0, 0], np.float32))
+    exact, ran = lockstep(P, w, 8)
+    assert exact >= min(ran, 3)
