@@ -136,6 +136,13 @@ typedef struct {
   int32_t n_accepted;  /* |V_U| appended to the tree                       */
   int32_t n_nodes;     /* |T| after the pass                               */
   int32_t goal_node;   /* smallest new goal node id, -1 if none            */
+  int32_t phase_ns[12]; /* device time of the pass's phases (ns) as seen by
+                           one block, each phase's work then its barrier
+                           wait: [0] Propagate, [1] wait, [2] accept flags,
+                           [3] Score (Eq. 3-4), [4] wait, [5] append to T,
+                           [6] P_accept (Eq. 5), [7] wait, [8] node-set
+                           draws, [9] wait, [10] V_E list and Eq. 6,
+                           [11] the previous pass's final wait */
 } kp_iter_stats;
 
 /* Context status snapshot.  The work counters cover every pass since the

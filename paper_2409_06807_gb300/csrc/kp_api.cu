@@ -170,6 +170,9 @@ const char* check_inputs(const kp_system* sys, const kp_workspace* ws, int32_t n
     if (!finite_or_inf(sys->x_lo[i]) || !finite_or_inf(sys->x_hi[i]) ||
         !(sys->x_lo[i] <= sys->x_hi[i]))
       return "bad state bounds";
+  if (sys->id == KP_QUADROTOR_12D)
+    for (int i : {0, 4, 5, 6})
+      if (!(sys->phys[i] > 0.0f) || !std::isfinite(sys->phys[i])) return "quadrotor mass and inertia must be positive";
   for (int i = 0; i < d->N; ++i)
     if (!std::isfinite(sys->u_lo[i]) || !std::isfinite(sys->u_hi[i]) ||
         !(sys->u_lo[i] <= sys->u_hi[i]))
@@ -510,6 +513,11 @@ void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* 
     P.u_scale[i] = sys->u_hi[i] - sys->u_lo[i];
   }
   for (int i = 0; i < 16; ++i) P.phys[i] = sys->phys[i];
+  if (d.sys == KP_SYS_QUAD)
+    for (int i = 0; i < 4; ++i) {
+      const float q = sys->phys[i == 0 ? 0 : 3 + i];  // m, Ixx, Iyy, Izz
+      P.recip[i] = q != 0.0f ? 1.0f / q : 0.0f;
+    }
   double vol = 1.0;
   for (int a = 0; a < 3; ++a) {
     P.ws_lo[a] = ws->lo[a];

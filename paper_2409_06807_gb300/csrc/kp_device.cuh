@@ -108,6 +108,35 @@ __device__ __forceinline__ int block_rank(bool flag, ScanSmem& sm, int* total) {
   return r;
 }
 
+// Exclusive prefix sum of one int per thread in thread order; total in
+// *total.  Must be called by every thread of the block.
+__device__ __forceinline__ int block_exclusive_scan(int v, ScanSmem& sm, int* total) {
+  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if ((int)lane >= o) x += y;
+  }
+  if (lane == 31) sm.warp[w] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) {
+      const int c = sm.warp[i];
+      sm.warp[i] = acc;
+      acc += c;
+    }
+    sm.warp[32] = acc;
+  }
+  __syncthreads();
+  const int r = sm.warp[w] + x - v;
+  *total = sm.warp[32];
+  __syncthreads();
+  return r;
+}
+
 // Block sum of two per-thread values.
 __device__ __forceinline__ void block_sum2(unsigned long long a, unsigned long long b,
                                            unsigned long long* s /*[64]*/,
@@ -163,6 +192,21 @@ __device__ __forceinline__ float unit24(uint32_t w) {
 }
 
 // ---------------------------------------------------------------------------
+// sine and cosine for the integrators
+// ---------------------------------------------------------------------------
+
+// Cody & Waite (1980) argument reduction: r = x - k 2pi with k = rint(x /
+// 2pi), 2pi split into C1 = fl32(2pi) and C2 = 2pi - C1 so that k C1 is
+// exact for |k| < 2^11 (|x| below ~1.2e4 rad); then the hardware sin/cos
+// approximations on r in [-pi, pi] (absolute error below 1e-6).
+__device__ __forceinline__ void sincos_reduced(float x, float* s, float* c) {
+  const float k = rintf(x * 0.159154943091895336f);
+  float r = fmaf(-k, 6.28318548202514648f, x);
+  r = fmaf(-k, -1.74845560007448838e-07f, r);
+  __sincosf(r, s, c);
+}
+
+// ---------------------------------------------------------------------------
 // systems (Sec. II, Eq. 1-2), FP32 in registers
 // ---------------------------------------------------------------------------
 
@@ -194,8 +238,8 @@ struct System<KP_SYS_DUBINS> {
   static constexpr int D = 6, N = 3;
   __device__ __forceinline__ static void f(const float* x, const float* u, float* dx) {
     float sp, cp, st, ct;
-    sincosf(x[3], &sp, &cp);
-    sincosf(x[4], &st, &ct);
+    sincos_reduced(x[3], &sp, &cp);
+    sincos_reduced(x[4], &st, &ct);
     dx[0] = x[5] * cp * ct;
     dx[1] = x[5] * sp * ct;
     dx[2] = x[5] * st;
@@ -230,22 +274,24 @@ struct System<KP_SYS_QUAD> {
   static constexpr int D = 12, N = 4;
   __device__ __forceinline__ static void f(const float* x, const float* u, const KParams& P,
                                            float* dx) {
-    const float m = P.phys[0], g = P.phys[1], l = P.phys[2], c = P.phys[3];
+    // phys: m g l c Ixx Iyy Izz; recip: 1/m 1/Ixx 1/Iyy 1/Izz
+    const float g = P.phys[1], l = P.phys[2], c = P.phys[3];
     const float Ix = P.phys[4], Iy = P.phys[5], Iz = P.phys[6];
     float sphi, cphi, sth, cth, sps, cps;
-    sincosf(x[3], &sphi, &cphi);
-    sincosf(x[4], &sth, &cth);
-    sincosf(x[5], &sps, &cps);
-    const float tth = sth / cth;
+    sincos_reduced(x[3], &sphi, &cphi);
+    sincos_reduced(x[4], &sth, &cth);
+    sincos_reduced(x[5], &sps, &cps);
+    const float sec = 1.0f / cth;
+    const float tth = sth * sec;
     const float p = x[9], q = x[10], r = x[11];
     dx[0] = x[6];
     dx[1] = x[7];
     dx[2] = x[8];
     dx[3] = p + sphi * tth * q + cphi * tth * r;
     dx[4] = cphi * q - sphi * r;
-    dx[5] = (sphi * q + cphi * r) / cth;
+    dx[5] = (sphi * q + cphi * r) * sec;
     const float thrust = u[0] + u[1] + u[2] + u[3];
-    const float a = thrust / m;
+    const float a = thrust * P.recip[0];
     dx[6] = a * (cphi * sth * cps + sphi * sps);
     dx[7] = a * (cphi * sth * sps - sphi * cps);
     dx[8] = a * (cphi * cth) - g;
@@ -253,9 +299,9 @@ struct System<KP_SYS_QUAD> {
     const float ty = l * (u[2] - u[0]);
     const float tz = c * (u[0] - u[1] + u[2] - u[3]);
     const float Lx = Ix * p, Ly = Iy * q, Lz = Iz * r;
-    dx[9] = (tx - (q * Lz - r * Ly)) / Ix;
-    dx[10] = (ty - (r * Lx - p * Lz)) / Iy;
-    dx[11] = (tz - (p * Ly - q * Lx)) / Iz;
+    dx[9] = (tx - (q * Lz - r * Ly)) * P.recip[1];
+    dx[10] = (ty - (r * Lx - p * Lz)) * P.recip[2];
+    dx[11] = (tz - (p * Ly - q * Lx)) * P.recip[3];
   }
   __device__ __forceinline__ static void step(float* x, const float* u, float h,
                                               const KParams& P) {

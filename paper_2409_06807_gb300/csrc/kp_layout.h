@@ -78,6 +78,11 @@ struct KLog {
 
 struct KStats {
   int32_t iteration, n_ve, lambda, n_samples, n_valid, n_accepted, n_nodes, goal_node;
+  // device time of the pass as seen by block 0 (ns): work then barrier wait
+  // of each phase: [0,1] Propagate, [2] accept flags, [3] Score, [4] wait,
+  // [5] append, [6] thresholds, [7] wait, [8] node sets, [9] wait,
+  // [10] V_E list and Eq. 6, [11] wait
+  int32_t phase_ns[12];
 };
 
 // x_init of a reset, passed by value.
@@ -95,6 +100,7 @@ struct KParams {
   float x_lo[12], x_hi[12];
   float u_lo[4], u_scale[4];  // u = u_lo + u_scale * r
   float phys[16];
+  float recip[4];       // quadrotor 1/m, 1/Ixx, 1/Iyy, 1/Izz
   // decomposition (Sec. III)
   float ws_lo[3];
   float fine_scale[3];  // fine cells per unit length

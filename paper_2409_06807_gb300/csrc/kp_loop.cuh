@@ -110,6 +110,14 @@ __device__ __forceinline__ void chunk_of(int n, int* c0, int* c1) {
   *c1 = (int)(a + per < n ? a + per : n);
 }
 
+// Contiguous run [r0, r1) of this thread inside the block's chunk [c0, c1).
+__device__ __forceinline__ void thread_run(int c0, int c1, int* r0, int* r1) {
+  const int per = (c1 - c0 + (int)blockDim.x - 1) / (int)blockDim.x;
+  const long long a = (long long)c0 + (long long)threadIdx.x * per;
+  *r0 = (int)(a < c1 ? a : c1);
+  *r1 = (int)(a + per < c1 ? a + per : c1);
+}
+
 // Sum of blk[0..G) and of blk[0..blockIdx.x).
 __device__ __forceinline__ void block_prefix(const uint32_t* blk, LoopShared& sh,
                                              unsigned long long* before,
@@ -124,31 +132,30 @@ __device__ __forceinline__ void block_prefix(const uint32_t* blk, LoopShared& sh
 }
 
 // Phase N': count V_E members of this block's node chunk (no draws).
-__device__ __forceinline__ void count_ve(const KParams& P, int n, LoopShared& sh) {
-  int v0, v1;
+// Returns this thread's offset inside the block.
+__device__ __forceinline__ int count_ve(const KParams& P, int n, LoopShared& sh) {
+  int v0, v1, r0, r1;
   chunk_of(n, &v0, &v1);
-  unsigned long long c = 0;
-  for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) c += P.in_ve[v] ? 1 : 0;
-  unsigned long long tot, dummy;
-  block_sum2(c, 0, sh.red, &tot, &dummy);
+  thread_run(v0, v1, &r0, &r1);
+  int c = 0;
+  for (int v = r0; v < r1; ++v) c += P.in_ve[v] ? 1 : 0;
+  int tot;
+  const int off = block_exclusive_scan(c, sh.scan, &tot);
   if (threadIdx.x == 0) P.blk_b[blockIdx.x] = (uint32_t)tot;
+  return off;
 }
 
-// Phase L: write the V_E list (ascending node id); returns |V_E|.
-__device__ __forceinline__ int write_ve(const KParams& P, int n, LoopShared& sh) {
-  int v0, v1;
+// Phase L: write the V_E list (ascending node id) from the per-block counts
+// and this thread's offset; returns |V_E|.
+__device__ __forceinline__ int write_ve(const KParams& P, int n, LoopShared& sh, int thread_off) {
+  int v0, v1, r0, r1;
   chunk_of(n, &v0, &v1);
+  thread_run(v0, v1, &r0, &r1);
   unsigned long long off, total;
   block_prefix(P.blk_b, sh, &off, &total);
-  int base = (int)off;
-  for (int vb = v0; vb < v1; vb += blockDim.x) {
-    const int v = vb + threadIdx.x;
-    const bool e = v < v1 && P.in_ve[v];
-    int cnt;
-    const int rank = block_rank(e, sh.scan, &cnt);
-    if (e) P.ve[base + rank] = v;
-    base += cnt;
-  }
+  int pos = (int)off + thread_off;
+  for (int v = r0; v < r1; ++v)
+    if (P.in_ve[v]) P.ve[pos++] = v;
   return (int)total;
 }
 
@@ -255,15 +262,19 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const unsigned ch
       uint32_t m_idle = __ballot_sync(FULL, key < 0);
       while (m_idle && !exhausted) {
         if (pool_next >= pool_end) {
+          // batches shrink towards the end of the pass so that warps run
+          // out of work together
+          int want = (S - pool_end) / (2 * (int)(gridDim.x * (blockDim.x >> 5)));
+          want = want < 32 ? 32 : (want > KP_KEY_BATCH ? KP_KEY_BATCH : want);
           int base = 0;
-          if (lane == 0) base = atomicAdd(&P.ctl->work_next, KP_KEY_BATCH);
+          if (lane == 0) base = atomicAdd(&P.ctl->work_next, want);
           base = __shfl_sync(FULL, base, 0);
           if (base >= S) {
             exhausted = true;
             break;
           }
           pool_next = base;
-          pool_end = base + KP_KEY_BATCH < S ? base + KP_KEY_BATCH : S;
+          pool_end = base + want < S ? base + want : S;
         }
         const int avail = pool_end - pool_next;
         const int rank = __popc(m_idle & lt);
@@ -327,13 +338,17 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const unsigned ch
   }
 }
 
-// Phase A: accept flags of this block's key chunk; returns the block count
-// of accepted samples (all threads) and adds the valid count to the pass.
-__device__ __forceinline__ void phase_accept(const KParams& P, int S, LoopShared& sh) {
-  int k0, k1;
+// Phase A: accept flags of this block's key chunk, each thread over a
+// contiguous run of keys.  Publishes the block's accepted count and adds
+// the valid count to the pass; returns this thread's offset among the
+// block's accepted samples (kept in a register across the grid barrier).
+__device__ __forceinline__ int phase_accept(const KParams& P, int S, LoopShared& sh) {
+  int k0, k1, r0, r1;
   chunk_of(S, &k0, &k1);
-  unsigned long long acc_n = 0, valid_n = 0;
-  for (int key = k0 + threadIdx.x; key < k1; key += blockDim.x) {
+  thread_run(k0, k1, &r0, &r1);
+  int acc_n = 0;
+  unsigned long long valid_n = 0;
+  for (int key = r0; key < r1; ++key) {
     uint32_t f = P.flags[key];
     if (f & KP_F_VALID) {
       ++valid_n;
@@ -348,13 +363,16 @@ __device__ __forceinline__ void phase_accept(const KParams& P, int S, LoopShared
       P.flags[key] = (uint8_t)f;
     }
   }
-  unsigned long long a, b;
-  block_sum2(acc_n, valid_n, sh.red, &a, &b);
+  int block_acc;
+  const int off = block_exclusive_scan(acc_n, sh.scan, &block_acc);
+  unsigned long long b, dummy;
+  block_sum2(valid_n, 0, sh.red, &b, &dummy);
   if (threadIdx.x == 0) {
     if (blockIdx.x == 0) P.ctl->work_next = 0;  // the expand phase is over
-    P.blk_a[blockIdx.x] = (uint32_t)a;
+    P.blk_a[blockIdx.x] = (uint32_t)block_acc;
     if (b) atomicAdd(&P.ctl->it_valid, (uint32_t)b);
   }
+  return off;
 }
 
 // Pairwise sum of buf[0..n), n a power of two (bottom-up tree, which is the
@@ -427,64 +445,59 @@ __device__ __forceinline__ void phase_thresholds(const KParams& P, int nch, doub
   }
 }
 
-// Phase P: append this block's accepted samples in key order.
-template <bool LOG>
+// Phase P: append this block's accepted samples in key order; each thread
+// writes the accepted samples of its own run from its offset.
+template <int SYS, bool LOG>
 __device__ __forceinline__ void phase_append(const KParams& P, int S, int lam, int t_old,
-                                             LoopShared& sh, int* total_out) {
-  constexpr int DMAX = 12, NMAX = 4;
-  int k0, k1;
+                                             LoopShared& sh, int thread_off, int* total_out) {
+  constexpr int D = System<SYS>::D, N = System<SYS>::N;
+  int k0, k1, r0, r1;
   chunk_of(S, &k0, &k1);
+  thread_run(k0, k1, &r0, &r1);
   unsigned long long off, total;
   block_prefix(P.blk_a, sh, &off, &total);
   *total_out = (int)total;
-  const int D = P.sys == KP_SYS_QUAD ? 12 : 6;
-  const int N = P.sys == KP_SYS_QUAD ? 4 : 3;
-  int base = t_old + (int)off;
-  for (int kb = k0; kb < k1; kb += blockDim.x) {
-    const int key = kb + threadIdx.x;
-    const bool in = key < k1;
-    uint32_t f = in ? P.flags[key] : 0u;
-    const bool acc = (f & KP_F_ACCEPTED) != 0;
-    int cnt;
-    const int rank = block_rank(acc, sh.scan, &cnt);
-    if (acc) {
-      const int id = base + rank;
+  int id = t_old + (int)off + thread_off;
+  for (int key = r0; key < r1; ++key) {
+    uint32_t f = P.flags[key];
+    if (f & KP_F_ACCEPTED) {
       float pos[3];
-      for (int i = 0; i < DMAX; ++i) {
-        if (i >= D) break;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
         const float xi = P.cst[(size_t)i * P.t_e + key];
         P.st[(size_t)i * P.t_e + id] = xi;
         if (i < 3) pos[i] = xi;
       }
-      for (int i = 0; i < NMAX; ++i) {
-        if (i >= N) break;
-        P.ctrl[(size_t)i * P.t_e + id] = P.cctrl[(size_t)i * P.t_e + key];
-      }
+#pragma unroll
+      for (int i = 0; i < N; ++i) P.ctrl[(size_t)i * P.t_e + id] = P.cctrl[(size_t)i * P.t_e + key];
+      const int s = P.cs[key];
       P.steps[id] = P.ck[key];
       P.parent[id] = P.ve[key / lam];
       P.region[id] = P.cr[key];
-      P.node_sub[id] = P.cs[key];
+      P.node_sub[id] = s;
       P.in_ve[id] = 1;
-      P.visited[P.cs[key]] = 1;
+      P.visited[s] = 1;
       const float dx = pos[0] - P.goal_c[0], dy = pos[1] - P.goal_c[1], dz = pos[2] - P.goal_c[2];
       if (dx * dx + dy * dy + dz * dz <= P.goal_r2) {
         f |= KP_F_GOAL;
         atomicMin(&P.ctl->goal_node, id);
       }
+      ++id;
     }
-    if (LOG && in && key < P.log.capacity) P.log.flags[key] = (uint8_t)f;
-    base += cnt;
+    if (LOG && key < P.log.capacity) P.log.flags[key] = (uint8_t)f;
   }
 }
 
 // Phase N: Algorithm 4 node sets, one draw per old node (counter: it, v, 0,
 // purpose 2) against the threshold of its region; new nodes are in V_E.
-__device__ __forceinline__ void phase_nodesets(const KParams& P, uint32_t it, int t_old,
-                                               int t_new, LoopShared& sh) {
-  int v0, v1;
+// Returns this thread's offset among the block's V_E members.
+__device__ __forceinline__ int phase_nodesets(const KParams& P, uint32_t it, int t_old,
+                                              int t_new, LoopShared& sh) {
+  int v0, v1, r0, r1;
   chunk_of(t_new, &v0, &v1);
-  unsigned long long c = 0;
-  for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+  thread_run(v0, v1, &r0, &r1);
+  int c = 0;
+  for (int v = r0; v < r1; ++v) {
     int e = 1;
     if (v < t_old) {
       const uint4 w = philox4x32_10(make_uint4(it, (uint32_t)v, 0u, 2u), P.seed_lo, P.seed_hi);
@@ -493,13 +506,17 @@ __device__ __forceinline__ void phase_nodesets(const KParams& P, uint32_t it, in
     }
     c += e;
   }
-  unsigned long long tot, dummy;
-  block_sum2(c, 0, sh.red, &tot, &dummy);
+  int tot;
+  const int off = block_exclusive_scan(c, sh.scan, &tot);
   if (threadIdx.x == 0) P.blk_b[blockIdx.x] = (uint32_t)tot;
+  return off;
 }
 
+#ifndef KP_MIN_BLOCKS
+#define KP_MIN_BLOCKS 1
+#endif
 template <int SYS, bool LOG>
-__global__ void __launch_bounds__(KP_BLOCK) kp_loop_kernel(KParams P, int max_iters,
+__global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParams P, int max_iters,
                                                            uint64_t max_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LoopShared sh;
@@ -525,9 +542,9 @@ __global__ void __launch_bounds__(KP_BLOCK) kp_loop_kernel(KParams P, int max_it
   const int nch = P.nch;
 
   // V_E list from the stored node sets
-  count_ve(P, n_tree, sh);
+  int ve_off = count_ve(P, n_tree, sh);
   if (!grid_sync(ctl, G, P.wait_ns, 10)) return;
-  int n_ve = write_ve(P, n_tree, sh);
+  int n_ve = write_ve(P, n_tree, sh, ve_off);
   if (!grid_sync(ctl, G, P.wait_ns, 11)) return;
   int lam = eq6_lambda(P.t_e, n_tree, n_ve, P.lambda_max);
   if (n_ve > 0 && lam == 0) {
@@ -539,23 +556,45 @@ __global__ void __launch_bounds__(KP_BLOCK) kp_loop_kernel(KParams P, int max_it
   }
 
   int run = 0;
+  // block 0 stamps the device clock between phases and barriers
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  uint64_t t_mark = timer ? global_ns() : 0;
+  int32_t phase_ns[12];
+  int32_t prev_wait = 0;
+  auto stamp = [&](int ph) {
+    if (timer) {
+      const uint64_t now = global_ns();
+      phase_ns[ph] = (int32_t)(now - t_mark);
+      t_mark = now;
+    }
+  };
   for (;;) {
     const int S = n_ve > 0 ? n_ve * lam : 0;
     phase_expand<SYS, LOG>(P, smem, it, lam, S, sh);
+    stamp(0);
     if (!grid_sync(ctl, G, P.wait_ns, 20)) return;
-    phase_accept(P, S, sh);
+    stamp(1);
+    const int acc_off = phase_accept(P, S, sh);
+    stamp(2);
     phase_scores(P, nch, sd);
+    stamp(3);
     if (!grid_sync(ctl, G, P.wait_ns, 21)) return;
+    stamp(4);
     int n_acc;
-    phase_append<LOG>(P, S, lam, n_tree, sh, &n_acc);
+    phase_append<SYS, LOG>(P, S, lam, n_tree, sh, acc_off, &n_acc);
+    stamp(5);
     phase_thresholds(P, nch, sd);
+    stamp(6);
     if (!grid_sync(ctl, G, P.wait_ns, 22)) return;
+    stamp(7);
     const int t_old = n_tree;
     n_tree = t_old + n_acc;
-    phase_nodesets(P, it, t_old, n_tree, sh);
+    ve_off = phase_nodesets(P, it, t_old, n_tree, sh);
+    stamp(8);
     if (!grid_sync(ctl, G, P.wait_ns, 23)) return;
+    stamp(9);
     const int ve_prev = n_ve, lam_prev = lam;
-    n_ve = write_ve(P, n_tree, sh);
+    n_ve = write_ve(P, n_tree, sh, ve_off);
     lam = eq6_lambda(P.t_e, n_tree, n_ve, P.lambda_max);
     ++run;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -572,6 +611,9 @@ __global__ void __launch_bounds__(KP_BLOCK) kp_loop_kernel(KParams P, int max_it
         s.n_accepted = n_acc;
         s.n_nodes = n_tree;
         s.goal_node = solved ? goal : -1;
+        phase_ns[10] = (int32_t)(global_ns() - t_mark);
+        phase_ns[11] = prev_wait;
+        for (int q = 0; q < 12; ++q) s.phase_ns[q] = phase_ns[q];
         P.stats[run - 1] = s;
       }
       ctl->it_valid = 0;
@@ -581,7 +623,12 @@ __global__ void __launch_bounds__(KP_BLOCK) kp_loop_kernel(KParams P, int max_it
       ctl->stop = (solved || full || run >= max_iters || out_of_time) ? 1 : 0;
     }
     ++it;
+    const uint64_t t_l = timer ? global_ns() : 0;
     if (!grid_sync(ctl, G, P.wait_ns, 24)) return;
+    if (timer) {
+      t_mark = global_ns();
+      prev_wait = (int32_t)(t_mark - t_l);  // reported with the next pass
+    }
     if (*((volatile int*)&ctl->stop)) break;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {

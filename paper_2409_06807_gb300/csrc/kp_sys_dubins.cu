@@ -1,5 +1,7 @@
 // kp_sys_dubins.cu -- kernels and launchers of one system (see kp_launch.cuh).
 #include "kp_layout.h"
 #define KP_SYS kp::KP_SYS_DUBINS
+// resident blocks per SM the register budget is fitted to (measured best)
+#define KP_MIN_BLOCKS 4
 #define KP_SYS_NAME dubins
 #include "kp_launch.cuh"

@@ -68,7 +68,8 @@ STAT_FIELDS = ("iteration", "n_ve", "lambda", "n_samples", "n_valid", "n_accepte
 
 
 class IterStats(C.Structure):
-    _fields_ = [(n if n != "lambda" else "lambda_", C.c_int32) for n in STAT_FIELDS]
+    _fields_ = [(n if n != "lambda" else "lambda_", C.c_int32) for n in STAT_FIELDS] + \
+        [("phase_ns", C.c_int32 * 12)]
 
 
 class Info(C.Structure):
@@ -255,8 +256,12 @@ class Planner:
         n_run = C.c_int32()
         self._check(lib().kp_expand_step(self._ctx, n_iters, out, C.byref(n_run)),
                     "kp_expand_step")
-        return [dict(zip(STAT_FIELDS, (getattr(s, f) for f, _ in IterStats._fields_)))
-                for s in out[: n_run.value]]
+        res = []
+        for s in out[: n_run.value]:
+            d = {f: getattr(s, f if f != "lambda" else "lambda_") for f in STAT_FIELDS}
+            d["phase_ns"] = list(s.phase_ns)
+            res.append(d)
+        return res
 
     def plan(self, max_iters=1000, max_ms=0.0, capacity=4096, x_init=None, goal=None):
         w = self.w
