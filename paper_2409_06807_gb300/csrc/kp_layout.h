@@ -48,6 +48,9 @@ struct KCtl {
   uint32_t it_valid;   // valid samples of the current pass
   int32_t n_edges;     // trajectory extraction: edges on the chain
   int32_t work_next;   // next sample key handed out in the expand phase
+  uint32_t s_done;     // region chunks whose Score partial sum is written
+  int32_t pad_sd;
+  double score_sum;    // sum of Eq. 5 over R_avail, this pass
   // work counters since the last reset (samples, integrator steps run,
   // segment hulls tested against the obstacle set)
   unsigned long long tot_samples;
@@ -79,9 +82,9 @@ struct KLog {
 struct KStats {
   int32_t iteration, n_ve, lambda, n_samples, n_valid, n_accepted, n_nodes, goal_node;
   // device time of the pass as seen by block 0 (ns): work then barrier wait
-  // of each phase: [0,1] Propagate, [2] accept flags, [3] Score, [4] wait,
-  // [5] append, [6] thresholds, [7] wait, [8] node sets, [9] wait,
-  // [10] V_E list and Eq. 6, [11] wait
+  // of each phase: [0,1] Propagate, [2] accept + Score, [3] 0, [4] wait,
+  // [5] append + P_accept, [6] 0, [7] wait, [8] node sets, [9] wait,
+  // [10] V_E list and Eq. 6, [11] previous pass's final wait
   int32_t phase_ns[12];
 };
 

@@ -118,6 +118,39 @@ __device__ __forceinline__ void thread_run(int c0, int c1, int* r0, int* r1) {
   *r1 = (int)(a + per < c1 ? a + per : c1);
 }
 
+// The accept and append phases run on warps 1.. of each block while warp 0
+// does the region estimates (FP64, long latency) alongside them.
+__device__ __forceinline__ void scan_run(int c0, int c1, int* r0, int* r1) {
+  const int nt = (int)blockDim.x - 32;
+  const int t = (int)threadIdx.x - 32;
+  if (t < 0) {
+    *r0 = *r1 = c0;
+    return;
+  }
+  const int per = (c1 - c0 + nt - 1) / nt;
+  const long long a = (long long)c0 + (long long)t * per;
+  *r0 = (int)(a < c1 ? a : c1);
+  *r1 = (int)(a + per < c1 ? a + per : c1);
+}
+
+// Sum of blk[0..G) and of blk[0..blockIdx.x), by one warp (no block sync).
+__device__ __forceinline__ void warp_prefix(const uint32_t* blk, unsigned long long* before,
+                                            unsigned long long* total) {
+  unsigned long long pre = 0, tot = 0;
+  for (int i = (int)(threadIdx.x & 31u); i < (int)gridDim.x; i += 32) {
+    const unsigned long long c = __ldcg(blk + i);
+    tot += c;
+    if (i < (int)blockIdx.x) pre += c;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    pre += __shfl_xor_sync(0xffffffffu, pre, o);
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  }
+  *before = pre;
+  *total = tot;
+}
+
 // Sum of blk[0..G) and of blk[0..blockIdx.x).
 __device__ __forceinline__ void block_prefix(const uint32_t* blk, LoopShared& sh,
                                              unsigned long long* before,
@@ -264,8 +297,11 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const unsigned ch
         if (pool_next >= pool_end) {
           // batches shrink towards the end of the pass so that warps run
           // out of work together
+          // (at the very end a warp takes only what its idle lanes can
+          // start now, so no warp is left with a second round of samples)
+          const int n_idle_now = __popc(m_idle);
           int want = (S - pool_end) / (2 * (int)(gridDim.x * (blockDim.x >> 5)));
-          want = want < 32 ? 32 : (want > KP_KEY_BATCH ? KP_KEY_BATCH : want);
+          want = want < n_idle_now ? n_idle_now : (want > KP_KEY_BATCH ? KP_KEY_BATCH : want);
           int base = 0;
           if (lane == 0) base = atomicAdd(&P.ctl->work_next, want);
           base = __shfl_sync(FULL, base, 0);
@@ -338,14 +374,19 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const unsigned ch
   }
 }
 
-// Phase A: accept flags of this block's key chunk, each thread over a
-// contiguous run of keys.  Publishes the block's accepted count and adds
-// the valid count to the pass; returns this thread's offset among the
-// block's accepted samples (kept in a register across the grid barrier).
-__device__ __forceinline__ int phase_accept(const KParams& P, int S, LoopShared& sh) {
+// Phase A (warps 1..): accept flags of this block's key chunk, each thread
+// over a contiguous run of keys; phase S (warp 0) runs alongside.
+// Publishes the block's accepted count and adds the valid count to the
+// pass; returns this thread's offset among the block's accepted samples
+// (kept in a register across the grid barrier).
+__device__ __forceinline__ void phase_scores(const KParams& P, int nch, double* sd);
+
+__device__ __forceinline__ int phase_accept(const KParams& P, int S, int nch, double* sd,
+                                            LoopShared& sh) {
+  if (threadIdx.x < 32) phase_scores(P, nch, sd);
   int k0, k1, r0, r1;
   chunk_of(S, &k0, &k1);
-  thread_run(k0, k1, &r0, &r1);
+  scan_run(k0, k1, &r0, &r1);
   int acc_n = 0;
   unsigned long long valid_n = 0;
   for (int key = r0; key < r1; ++key) {
@@ -375,27 +416,31 @@ __device__ __forceinline__ int phase_accept(const KParams& P, int S, LoopShared&
   return off;
 }
 
-// Pairwise sum of buf[0..n), n a power of two (bottom-up tree, which is the
-// same tree as recursive halving).  All threads; result in buf[0].
-__device__ __forceinline__ void smem_pairwise(double* buf, int n) {
+// Pairwise sum of buf[0..n), n a power of two, by one warp (bottom-up
+// tree, the same tree as recursive halving); result in buf[0].
+__device__ __forceinline__ void warp_pairwise(double* buf, int n) {
+  const int lane = (int)(threadIdx.x & 31u);
   for (int stride = 1; stride < n; stride <<= 1) {
-    __syncthreads();
-    for (int i = threadIdx.x * 2 * stride; i < n; i += blockDim.x * 2 * stride)
+    __syncwarp();
+    for (int i = lane * 2 * stride; i < n; i += 64 * stride)
       buf[i] = __dadd_rn(buf[i], buf[i + stride]);
   }
-  __syncthreads();
+  __syncwarp();
 }
 
-// Phase S: Eq. 3-4 for this block's region chunk and its pairwise partial
-// sum.  Every operation is an explicitly rounded IEEE double operation in
-// the order FreeVol = ((delta + nv) vol) / ((delta + nv) + ni),
+// Phase S (warp 0): Eq. 3-4 for this block's region chunk and its pairwise
+// partial sum; the last chunk to finish reduces the partial sums into the
+// sum of Eq. 5 (same pairwise tree whichever block it is).  Every operation
+// is an explicitly rounded IEEE double operation in the order
+// FreeVol = ((delta + nv) vol) / ((delta + nv) + ni),
 // f4 = (FreeVol FreeVol)(FreeVol FreeVol),
 // Score = f4 / ((1 + Cov)(1 + (nv + ni)(nv + ni))).
 __device__ __forceinline__ void phase_scores(const KParams& P, int nch, double* sd) {
   if ((int)blockIdx.x >= nch) return;
+  const int lane = (int)(threadIdx.x & 31u);
   const int ch = P.R_pad / nch;
   const int r0 = blockIdx.x * ch;
-  for (int i = threadIdx.x; i < ch; i += blockDim.x) {
+  for (int i = lane; i < ch; i += 32) {
     const int r = r0 + i;
     double sc = 0.0;
     if (r < P.R && P.avail[r]) {
@@ -412,22 +457,34 @@ __device__ __forceinline__ void phase_scores(const KParams& P, int nch, double* 
     if (r < P.R) P.score[r] = sc;
     sd[i] = sc;
   }
-  smem_pairwise(sd, ch);
-  if (threadIdx.x == 0) P.chunk_sum[blockIdx.x] = sd[0];
-  __syncthreads();
+  warp_pairwise(sd, ch);
+  int last = 0;
+  if (lane == 0) {
+    P.chunk_sum[blockIdx.x] = sd[0];
+    __threadfence();
+    last = atomicAdd(&P.ctl->s_done, 1u) == (uint32_t)(nch - 1);
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) {
+    __threadfence();
+    for (int i = lane; i < nch; i += 32) sd[i] = __ldcg(P.chunk_sum + i);
+    warp_pairwise(sd, nch);
+    if (lane == 0) {
+      P.ctl->score_sum = sd[0];
+      P.ctl->s_done = 0;  // for the next pass
+    }
+  }
+  __syncwarp();
 }
 
-// Phase T: the sum of Eq. 5 from the chunk sums, then P_accept and the
-// integer threshold of this block's region chunk.
-__device__ __forceinline__ void phase_thresholds(const KParams& P, int nch, double* sd) {
+// Phase T (warp 0): P_accept and the integer threshold of this block's
+// region chunk (Eq. 5), from the sum the last chunk published.
+__device__ __forceinline__ void phase_thresholds(const KParams& P, int nch) {
   if ((int)blockIdx.x >= nch) return;
-  for (int i = threadIdx.x; i < nch; i += blockDim.x) sd[i] = P.chunk_sum[i];
-  smem_pairwise(sd, nch);
-  const double sum = sd[0];
-  __syncthreads();
+  const double sum = __ldcg(&P.ctl->score_sum);
   const int ch = P.R_pad / nch;
   const int r0 = blockIdx.x * ch;
-  for (int i = threadIdx.x; i < ch; i += blockDim.x) {
+  for (int i = (int)(threadIdx.x & 31u); i < ch; i += 32) {
     const int r = r0 + i;
     if (r >= P.R) break;
     uint64_t thr = 1ull << 32;  // P_accept = 1 outside R_avail
@@ -445,18 +502,23 @@ __device__ __forceinline__ void phase_thresholds(const KParams& P, int nch, doub
   }
 }
 
-// Phase P: append this block's accepted samples in key order; each thread
-// writes the accepted samples of its own run from its offset.
+// Phase P (warps 1..): append this block's accepted samples in key order;
+// each thread writes the accepted samples of its own run from its offset.
+// Phase T (warp 0) runs alongside.  No block-wide synchronisation.
 template <int SYS, bool LOG>
 __device__ __forceinline__ void phase_append(const KParams& P, int S, int lam, int t_old,
-                                             LoopShared& sh, int thread_off, int* total_out) {
+                                             int nch, int thread_off, int* total_out) {
   constexpr int D = System<SYS>::D, N = System<SYS>::N;
+  unsigned long long off, total;
+  warp_prefix(P.blk_a, &off, &total);
+  *total_out = (int)total;
+  if (threadIdx.x < 32) {
+    phase_thresholds(P, nch);
+    return;
+  }
   int k0, k1, r0, r1;
   chunk_of(S, &k0, &k1);
-  thread_run(k0, k1, &r0, &r1);
-  unsigned long long off, total;
-  block_prefix(P.blk_a, sh, &off, &total);
-  *total_out = (int)total;
+  scan_run(k0, k1, &r0, &r1);
   int id = t_old + (int)off + thread_off;
   for (int key = r0; key < r1; ++key) {
     uint32_t f = P.flags[key];
@@ -536,6 +598,7 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParam
     ctl->stop = 0;
     ctl->n_run = 0;
     ctl->work_next = 0;
+    ctl->s_done = 0;
   }
   int n_tree = ctl->n_nodes;
   uint32_t it = (uint32_t)ctl->iteration;
@@ -574,16 +637,14 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParam
     stamp(0);
     if (!grid_sync(ctl, G, P.wait_ns, 20)) return;
     stamp(1);
-    const int acc_off = phase_accept(P, S, sh);
+    const int acc_off = phase_accept(P, S, nch, sd, sh);
     stamp(2);
-    phase_scores(P, nch, sd);
     stamp(3);
     if (!grid_sync(ctl, G, P.wait_ns, 21)) return;
     stamp(4);
     int n_acc;
-    phase_append<SYS, LOG>(P, S, lam, n_tree, sh, acc_off, &n_acc);
+    phase_append<SYS, LOG>(P, S, lam, n_tree, nch, acc_off, &n_acc);
     stamp(5);
-    phase_thresholds(P, nch, sd);
     stamp(6);
     if (!grid_sync(ctl, G, P.wait_ns, 22)) return;
     stamp(7);
@@ -668,6 +729,7 @@ __global__ void kp_reset_kernel(KParams P, RootState root) {
   ctl->tot_hull = 0;
   ctl->tot_box_tests = 0;
   ctl->work_next = 0;
+  ctl->s_done = 0;
   if (!ok) {
     ctl->state = KP_DEV_BAD_ROOT;
     ctl->n_nodes = 0;
