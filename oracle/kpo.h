@@ -125,6 +125,38 @@ void kpo_estimates(const kpo *o, double *score, double *p_accept,
  * chain length, 0 when there is no goal node. */
 int32_t kpo_path(const kpo *o, int32_t *nodes, int32_t cap);
 
+/* ---- learned proposal (an addition to the paper's uniform draw) ----
+ * Node features (32 values, the last 8 zero) of node v under the current
+ * region tables:
+ *   [0..5]  state, each bounded entry mapped to [-1, 1]; an unbounded
+ *           entry wrapped to [-pi, pi) and divided by pi
+ *   [6..8]  goal centre minus position
+ *   [9]     Cov / n'          [10] FreeVol / vol = (delta+nv)/(delta+nv+ni)
+ *   [11]    log(1 + nv)       [12] log(1 + ni)
+ *   [13]    P_accept = thr / 2^32
+ *   [14..19] P_accept of the -x, +x, -y, +y, -z, +z neighbour regions in
+ *           the position grid (0 outside the grid)
+ * Targets: (u_i - lo_i) / (hi_i - lo_i) * 2 - 1 for the 3 controls and
+ * (k - k_min) / (k_max - k_min) * 2 - 1 for the duration.
+ * Learned draw of a sample (selector word < mix * 2^32): normals z_0..z_3
+ * by Box-Muller from Philox purpose 3 words, q = clamp(mean + exp(log_std)
+ * z, -1, 1), u_i = lo_i + (hi_i - lo_i)(q_i + 1)/2, k = k_min +
+ * floor((k_max - k_min)(q_3 + 1)/2 + 1/2).  Only 6D systems. */
+int32_t kpo_mlp_num_params(void);
+void kpo_mlp_forward(const double *p, const double *x, int32_t M, double *out);
+double kpo_mlp_loss_grad(const double *p, const double *x, const double *t,
+                         int32_t M, double *grad);
+void kpo_adam(double *p, const double *g, double *m, double *v, int32_t n,
+              double lr, double beta1, double beta2, double eps, int32_t t);
+void kpo_features(const kpo *o, int32_t v, double *feat);
+/* Enables the learned draw with the given parameter vector (NULL: off). */
+int32_t kpo_set_mlp(kpo *o, const float *params, double mix);
+/* Harvest: every representative of a newly reached sub-region appends its
+ * parent's features and its own target; returns pairs written so far. */
+int32_t kpo_set_harvest(kpo *o, double *feat, double *target, int32_t capacity);
+int32_t kpo_harvest_count(const kpo *o);
+void kpo_box_muller(const uint32_t w[4], double z[4]);
+
 /* ---- building blocks, exported for the oracle's own pin tests ---- */
 void kpo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
                        uint32_t out[4]);

@@ -105,6 +105,21 @@ def lib():
                                 C.POINTER(C.c_double)]
         L.kpo_lambda.restype = C.c_int32
         L.kpo_lambda.argtypes = [C.c_int32] * 4
+        L.kpo_mlp_num_params.restype = C.c_int32
+        L.kpo_mlp_num_params.argtypes = []
+        L.kpo_mlp_forward.argtypes = [_f64p, _f64p, C.c_int32, _f64p]
+        L.kpo_mlp_loss_grad.restype = C.c_double
+        L.kpo_mlp_loss_grad.argtypes = [_f64p, _f64p, _f64p, C.c_int32, C.c_void_p]
+        L.kpo_adam.argtypes = [_f64p, _f64p, _f64p, _f64p, C.c_int32, C.c_double, C.c_double,
+                               C.c_double, C.c_double, C.c_int32]
+        L.kpo_features.argtypes = [vp, C.c_int32, _f64p]
+        L.kpo_set_mlp.restype = C.c_int32
+        L.kpo_set_mlp.argtypes = [vp, C.c_void_p, C.c_double]
+        L.kpo_set_harvest.restype = C.c_int32
+        L.kpo_set_harvest.argtypes = [vp, C.c_void_p, C.c_void_p, C.c_int32]
+        L.kpo_harvest_count.restype = C.c_int32
+        L.kpo_harvest_count.argtypes = [vp]
+        L.kpo_box_muller.argtypes = [_u32p, _f64p]
         L.kpo_dense_check.restype = C.c_double
         L.kpo_dense_check.argtypes = [vp, _f64p, _f64p, C.c_int32, C.c_int32, _f64p]
         _lib = L
@@ -157,6 +172,52 @@ def eq345(n_valid, n_invalid, cov, avail, vol, delta, eps):
                     np.ascontiguousarray(avail, np.uint8), vol, delta, eps,
                     score, p, thr, C.byref(s))
     return score, p, thr, s.value
+
+
+MLP_IN, MLP_H, MLP_OUT = 32, 256, 8
+
+
+def mlp_num_params() -> int:
+    return lib().kpo_mlp_num_params()
+
+
+def mlp_forward(params, x) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, MLP_IN)
+    out = np.zeros((len(x), MLP_OUT))
+    lib().kpo_mlp_forward(np.ascontiguousarray(params, np.float64), x, len(x), out.reshape(-1))
+    return out
+
+
+def mlp_loss_grad(params, x, t, grad=True):
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, MLP_IN)
+    t = np.ascontiguousarray(t, np.float64).reshape(-1, 4)
+    g = np.zeros(mlp_num_params()) if grad else None
+    loss = lib().kpo_mlp_loss_grad(np.ascontiguousarray(params, np.float64), x.reshape(-1),
+                                   t.reshape(-1), len(x),
+                                   g.ctypes.data if grad else None)
+    return loss, g
+
+
+def adam(p, g, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
+    lib().kpo_adam(p, np.ascontiguousarray(g, np.float64), m, v, len(p), lr, beta1, beta2,
+                   eps, t)
+
+
+def box_muller(words) -> np.ndarray:
+    z = np.zeros(4)
+    lib().kpo_box_muller(np.ascontiguousarray(words, np.uint32), z)
+    return z
+
+
+def mlp_split(p):
+    """Views (W1, b1, W2, b2, W3, b3) of a flat parameter vector."""
+    sizes = [(MLP_H, MLP_IN), (MLP_H,), (MLP_H, MLP_H), (MLP_H,), (MLP_OUT, MLP_H), (MLP_OUT,)]
+    out, o = [], 0
+    for s in sizes:
+        n = int(np.prod(s))
+        out.append(p[o:o + n].reshape(s))
+        o += n
+    return out
 
 
 def lam(t_e, n_tree, n_ve, lambda_max) -> int:
@@ -325,6 +386,29 @@ class Oracle:
         lib().kpo_bin(self._h, np.asarray(x, np.float64), C.byref(r), C.byref(s),
                       C.byref(m))
         return r.value, s.value, m.value
+
+    def features(self, v) -> np.ndarray:
+        f = np.zeros(32)
+        lib().kpo_features(self._h, int(v), f)
+        return f
+
+    def set_mlp(self, params, mix=0.5):
+        if params is None:
+            self._mlp = None
+            lib().kpo_set_mlp(self._h, None, 0.0)
+            return
+        self._mlp = np.ascontiguousarray(params, np.float32)
+        if lib().kpo_set_mlp(self._h, self._mlp.ctypes.data, float(mix)) != 0:
+            raise ValueError("learned proposal needs a 6D system")
+
+    def set_harvest(self, capacity):
+        self._hv = (np.zeros((capacity, 32)), np.zeros((capacity, 4)))
+        lib().kpo_set_harvest(self._h, self._hv[0].ctypes.data, self._hv[1].ctypes.data,
+                              int(capacity))
+
+    def harvest(self):
+        n = lib().kpo_harvest_count(self._h)
+        return self._hv[0][:n].copy(), self._hv[1][:n].copy()
 
     def dense_check(self, x0, u, k, sub=100):
         x_end = np.zeros(self.d)

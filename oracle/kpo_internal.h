@@ -38,6 +38,12 @@ struct kpo {
   int iteration;
   int status;
   int goal_node;
+
+  /* learned proposal */
+  double *mlp;           /* parameter vector, NULL when off */
+  double mix;
+  double *hv_feat, *hv_target;
+  int hv_cap, hv_count;
 };
 
 #endif

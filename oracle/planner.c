@@ -100,7 +100,7 @@ void kpo_destroy(kpo *o) {
   free(o->boxes); free(o->x); free(o->parent); free(o->u); free(o->steps);
   free(o->region); free(o->sub); free(o->in_ve); free(o->n_valid);
   free(o->n_invalid); free(o->cov); free(o->avail); free(o->visited);
-  free(o->score); free(o->p_accept); free(o->thr);
+  free(o->score); free(o->p_accept); free(o->thr); free(o->mlp);
   free(o);
 }
 
@@ -209,6 +209,75 @@ static void draw(const kpo *o, uint32_t it, uint32_t node, uint32_t j,
 }
 
 /* ------------------------------------------------------------------ */
+/* learned proposal                                                     */
+/* ------------------------------------------------------------------ */
+
+#define PI_ 3.14159265358979323846
+
+void kpo_features(const kpo *o, int32_t v, double *f) {
+  const double *x = o->x + (size_t)v * o->d;
+  for (int i = 0; i < 32; ++i) f[i] = 0.0;
+  for (int i = 0; i < 6 && i < o->d; ++i) {
+    const double lo = o->cfg.x_lo[i], hi = o->cfg.x_hi[i];
+    if (isfinite(lo) && isfinite(hi) && hi > lo)
+      f[i] = 2.0 * (x[i] - lo) / (hi - lo) - 1.0;
+    else
+      f[i] = (x[i] - 2.0 * PI_ * floor((x[i] + PI_) / (2.0 * PI_))) / PI_;
+  }
+  for (int a = 0; a < 3; ++a) f[6 + a] = o->cfg.goal_c[a] - x[a];
+  const int r = o->region[v];
+  const double nv = (double)o->n_valid[r], ni = (double)o->n_invalid[r];
+  f[9] = (double)o->cov[r] / (double)o->n_sub_per;
+  f[10] = (o->cfg.delta + nv) / (o->cfg.delta + nv + ni);
+  f[11] = log1p(nv);
+  f[12] = log1p(ni);
+  f[13] = (double)o->thr[r] / TWO32;
+  /* face neighbours in the position grid, same speed bin */
+  const int gx = o->cfg.grid[0], gy = o->cfg.grid[1], gz = o->cfg.grid[2];
+  const int cx = r % gx, cy = (r / gx) % gy, cz = (r / (gx * gy)) % gz;
+  const int sb = r / (gx * gy * gz);
+  const int dx[6] = {-1, 1, 0, 0, 0, 0}, dy[6] = {0, 0, -1, 1, 0, 0}, dz[6] = {0, 0, 0, 0, -1, 1};
+  for (int k = 0; k < 6; ++k) {
+    const int nx = cx + dx[k], ny = cy + dy[k], nz = cz + dz[k];
+    if (nx < 0 || nx >= gx || ny < 0 || ny >= gy || nz < 0 || nz >= gz) continue;
+    const int rn = nx + gx * (ny + gy * (nz + gz * sb));
+    f[14 + k] = (double)o->thr[rn] / TWO32;
+  }
+}
+
+void kpo_box_muller(const uint32_t w[4], double z[4]) {
+  for (int pr = 0; pr < 2; ++pr) {
+    const double r1 = ((double)(w[2 * pr] >> 8) + 1.0) * (1.0 / 16777216.0); /* (0, 1] */
+    const double r2 = (double)(w[2 * pr + 1] >> 8) * (1.0 / 16777216.0);   /* [0, 1) */
+    const double rad = sqrt(-2.0 * log(r1));
+    z[2 * pr] = rad * cos(2.0 * PI_ * r2);
+    z[2 * pr + 1] = rad * sin(2.0 * PI_ * r2);
+  }
+}
+
+int32_t kpo_set_mlp(kpo *o, const float *params, double mix) {
+  free(o->mlp);
+  o->mlp = NULL;
+  if (!params) return 0;
+  if (o->d != 6) return KPO_ERR;
+  const int n = kpo_mlp_num_params();
+  o->mlp = (double *)malloc(sizeof(double) * (size_t)n);
+  for (int i = 0; i < n; ++i) o->mlp[i] = (double)params[i];
+  o->mix = mix;
+  return 0;
+}
+
+int32_t kpo_set_harvest(kpo *o, double *feat, double *target, int32_t capacity) {
+  o->hv_feat = feat;
+  o->hv_target = target;
+  o->hv_cap = capacity;
+  o->hv_count = 0;
+  return 0;
+}
+
+int32_t kpo_harvest_count(const kpo *o) { return o->hv_count; }
+
+/* ------------------------------------------------------------------ */
 /* Algorithm 1, lines 1-3                                               */
 /* ------------------------------------------------------------------ */
 
@@ -284,6 +353,18 @@ int32_t kpo_iterate(kpo *o, kpo_records *rec, kpo_iter_stats *st) {
   memcpy(visited0, o->visited, (size_t)o->n_sub);
   double *traj = (double *)malloc(sizeof(double) * (size_t)(o->cfg.k_max + 1) * d);
 
+  /* learned proposal: features and network outputs per expanded node */
+  double *feat = NULL, *net = NULL;
+  if (o->mlp || o->hv_feat) {
+    feat = (double *)malloc(sizeof(double) * 32 * (size_t)(nve > 0 ? nve : 1));
+    for (int p = 0; p < nve; ++p) kpo_features(o, ve[p], feat + 32 * (size_t)p);
+  }
+  if (o->mlp) {
+    net = (double *)malloc(sizeof(double) * 8 * (size_t)(nve > 0 ? nve : 1));
+    kpo_mlp_forward(o->mlp, feat, nve, net);
+  }
+  const uint64_t mix_thr = o->mlp ? (uint64_t)floor(o->mix * TWO32) : 0;
+
   /* ---------------- Algorithm 2: Propagate ---------------- */
   int n_valid_total = 0;
   for (int p = 0; p < nve; ++p) {
@@ -299,6 +380,23 @@ int32_t kpo_iterate(kpo *o, kpo_records *rec, kpo_iter_stats *st) {
         u[i] = o->cfg.u_lo[i] + (o->cfg.u_hi[i] - o->cfg.u_lo[i]) * unit24(w0[i]);
       uint64_t span = (uint64_t)(o->cfg.k_max - o->cfg.k_min + 1);
       int k = o->cfg.k_min + (int)(((uint64_t)w1[0] * span) >> 32);
+      if (net && (uint64_t)w1[2] < mix_thr) {
+        /* learned draw from the network's Gaussian */
+        uint32_t w3[4];
+        double z[4], q[4];
+        draw(o, it, (uint32_t)v, (uint32_t)j, 3, w3);
+        kpo_box_muller(w3, z);
+        const double *nn = net + 8 * (size_t)p;
+        for (int i = 0; i < 4; ++i) {
+          q[i] = nn[i] + exp(nn[4 + i]) * z[i];
+          q[i] = q[i] < -1.0 ? -1.0 : (q[i] > 1.0 ? 1.0 : q[i]);
+        }
+        for (int i = 0; i < N; ++i)
+          u[i] = o->cfg.u_lo[i] + (o->cfg.u_hi[i] - o->cfg.u_lo[i]) * (q[i] + 1.0) * 0.5;
+        k = o->cfg.k_min +
+            (int)floor((double)(o->cfg.k_max - o->cfg.k_min) * (q[3] + 1.0) * 0.5 + 0.5);
+        if (k > o->cfg.k_max) k = o->cfg.k_max;
+      }
       /* PropagateODE with the validity check after every step */
       memcpy(traj, o->x + (size_t)v * d, sizeof(double) * d);
       int valid = 1, fail = 0, last = 0;
@@ -389,6 +487,17 @@ int32_t kpo_iterate(kpo *o, kpo_records *rec, kpo_iter_stats *st) {
     o->sub[id] = ss[key];
     o->in_ve[id] = 1;
     o->visited[ss[key]] = 1;
+    if (o->hv_feat && (fl[key] & 8) && o->hv_count < o->hv_cap) {
+      const int h = o->hv_count++;
+      memcpy(o->hv_feat + 32 * (size_t)h, feat + 32 * (size_t)(key / lambda), sizeof(double) * 32);
+      for (int i = 0; i < 3; ++i)
+        o->hv_target[4 * (size_t)h + i] =
+            2.0 * (us[(size_t)key * N + i] - o->cfg.u_lo[i]) / (o->cfg.u_hi[i] - o->cfg.u_lo[i]) - 1.0;
+      o->hv_target[4 * (size_t)h + 3] =
+          o->cfg.k_max > o->cfg.k_min
+              ? 2.0 * (double)(ks[key] - o->cfg.k_min) / (double)(o->cfg.k_max - o->cfg.k_min) - 1.0
+              : 0.0;
+    }
     if (in_goal(o, o->x + (size_t)id * d, NULL)) {
       fl[key] |= 32;
       if (o->goal_node < 0) o->goal_node = id;
@@ -422,7 +531,7 @@ int32_t kpo_iterate(kpo *o, kpo_records *rec, kpo_iter_stats *st) {
   if (o->goal_node >= 0) o->status = KPO_SOLVED;
 
   free(ve); free(xs); free(us); free(ks); free(rs); free(ss); free(fl);
-  free(visited0); free(traj);
+  free(visited0); free(traj); free(feat); free(net);
   return o->status;
 }
 
