@@ -316,6 +316,59 @@ kp_status kp_plan_static(const kp_system *sys, const kp_workspace *ws,
                          const kp_budget *budget, kp_traj *traj,
                          void *cuda_stream);
 
+/* ---- learned control proposal -------------------------------------------
+ * Not in the paper: an addition on top of Algorithm 2's uniform control
+ * draw.  A network maps 24 node features (zero padded to KP_MLP_INPUTS) to
+ * a Gaussian over 4 normalised quantities (3 controls, the duration): two
+ * ReLU layers of 256 units, outputs mean = tanh(o[0..3]) and log_std =
+ * clamp(o[4..7], -4, 1).  BF16 weights and activations on the tensor
+ * cores, FP32 accumulation, FP32 master weights and Adam moments.
+ * Parameter vector (FP32, row-major): W1 [256][32], b1 [256], W2
+ * [256][256], b2 [256], W3 [8][256], b3 [8].  A network context lives in a
+ * caller-owned device arena (kp_mlp_required_bytes) and works on the
+ * stream given at creation. */
+#define KP_MLP_INPUTS 32
+#define KP_MLP_OUTPUTS 8
+typedef struct kp_mlp kp_mlp;
+int32_t kp_mlp_num_params(void);
+size_t kp_mlp_required_bytes(int32_t max_batch);
+/* Copies host_params (kp_mlp_num_params floats); Adam state starts at 0. */
+kp_status kp_mlp_create(void *dev_arena, size_t arena_bytes, int32_t max_batch,
+                        const float *host_params, void *cuda_stream,
+                        kp_mlp **out);
+kp_status kp_mlp_set_params(kp_mlp *mlp, const float *host_params);
+kp_status kp_mlp_get_params(kp_mlp *mlp, float *host_params);
+/* dev_x: device [M][32] FP32 inputs; dev_out: device [M][8] FP32 (mean[4],
+ * log_std[4]).  Enqueued only. */
+kp_status kp_mlp_forward(kp_mlp *mlp, const float *dev_x, int32_t M,
+                         float *dev_out);
+/* Gradient of the batch-mean Gaussian negative log-likelihood of the device
+ * targets dev_t [M][4] (normalised to [-1, 1]) w.r.t. every parameter, to
+ * host_grad (nullable), and the loss (nullable).  Synchronises. */
+kp_status kp_mlp_gradients(kp_mlp *mlp, const float *dev_x, const float *dev_t,
+                           int32_t M, float *host_grad, float *host_loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on that loss; host_loss
+ * (nullable) receives the loss before the step (synchronises). */
+kp_status kp_mlp_train_step(kp_mlp *mlp, const float *dev_x,
+                            const float *dev_t, int32_t M, float lr,
+                            float *host_loss);
+void kp_mlp_destroy(kp_mlp *mlp);
+/* Planner use of a network (6D systems): each pass evaluates the network on
+ * the features of every V_E node; a sample whose selector draw falls below
+ * 'mix' draws its controls and duration from the node's Gaussian (Box-
+ * Muller normals from its own Philox counter, clamped to the bounds), the
+ * others from the uniform draw.  Propagation and validity are unchanged.
+ * NULL detaches.  The network must outlive its use by the context. */
+kp_status kp_attach_mlp(kp_ctx *ctx, const kp_mlp *mlp, float mix);
+/* Harvest of training pairs (6D systems): every sample that becomes the
+ * representative of a newly reached sub-region appends its parent's
+ * features (dev_feat [capacity][32]) and its own normalised controls and
+ * duration (dev_target [capacity][4]); *dev_count counts the pairs offered
+ * (may exceed capacity; the caller zeroes it).  Device pointers; NULL
+ * disables. */
+kp_status kp_set_harvest(kp_ctx *ctx, float *dev_feat, float *dev_target,
+                         int32_t capacity, uint32_t *dev_count);
+
 /* Last error message of the context (never NULL). */
 const char *kp_last_error(const kp_ctx *ctx);
 

@@ -16,8 +16,12 @@
 
 #include "../../include/kp.h"
 #include "kp_device.cuh"
+#include "kp_mlp.cuh"
 
+struct kp_mlp;
 namespace kp {
+void mlp_device_weights(const kp_mlp* n, const void** W1, const float** b1, const void** W2,
+                        const float** b2, const void** W3, const float** b3);
 // launchers defined in kp_sys_*.cu
 #define KP_DECLARE_SYS(name)                                                                   \
   cudaError_t loop_occupancy_##name(bool log, size_t smem, int* blocks_per_sm);                \
@@ -107,7 +111,7 @@ struct Dims {
 struct Layout {
   size_t ctl, boxes, st, parent, ctrl, steps, region, sub, in_ve, cst, cctrl, ck, cr, cs, flags,
       n_valid, n_invalid, cov, avail, visited, claim, score, thr, ve, blk_a, blk_b, chunk_sum,
-      stats, traj, total;
+      stats, traj, feat, net_raw, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -150,6 +154,8 @@ Layout make_layout(const Dims& d) {
   L.chunk_sum = take((size_t)KP_MAX_GRID * 8);
   L.stats = take((size_t)kStatsCap * sizeof(KStats));
   L.traj = take((size_t)KP_TRAJ_ROWS * 17 * 4);
+  L.feat = take(te * 32 * 2);     // bf16 node features of the V_E positions
+  L.net_raw = take(te * 8 * 4);   // network outputs of the V_E positions
   L.total = off;
   return L;
 }
@@ -454,7 +460,9 @@ kp_status configure_launch(kp_ctx* ctx) {
   // shared memory: boxes + the double scratch of the region-score sums
   const int min_ch = d.R_pad / (d.R_pad < 128 ? d.R_pad : 128);
   const int sd = min_ch > 1024 ? min_ch : 1024;
-  ctx->smem = (size_t)ctx->P.blob_bytes + (size_t)sd * 8;
+  ctx->P.sd_bytes = sd * 8;
+  ctx->smem = (size_t)ctx->P.blob_bytes + (size_t)sd * 8 +
+              (ctx->P.features_on ? (size_t)MLP_TILE_SMEM : 0);
   for (int log = 0; log < 2; ++log) {
     int bps = 0;
     KP_CUDA(occupancy(d.sys, log != 0, ctx->smem, &bps));
@@ -567,6 +575,13 @@ void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* 
   P.stats = reinterpret_cast<KStats*>(A + lay.stats);
   P.stats_cap = kStatsCap;
   P.traj = reinterpret_cast<float*>(A + lay.traj);
+  P.feat = reinterpret_cast<uint16_t*>(A + lay.feat);
+  P.net_raw = reinterpret_cast<float*>(A + lay.net_raw);
+  for (int i = 0; i < 6; ++i) {
+    const float lo = i < d.D ? sys->x_lo[i] : 0.0f, hi = i < d.D ? sys->x_hi[i] : 0.0f;
+    P.feat_scale[i] =
+        std::isfinite(lo) && std::isfinite(hi) && hi > lo ? (float)(2.0 / ((double)hi - (double)lo)) : 0.0f;
+  }
 }
 
 kp_status check_launch(kp_ctx* ctx, const KCtl& h) {
@@ -973,6 +988,50 @@ kp_status kp_selftest_wait_timeout(kp_ctx* ctx) {
   return check_launch(ctx, h);
 }
 
+kp_status kp_attach_mlp(kp_ctx* ctx, const kp_mlp* mlp, float mix) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  KParams& P = ctx->P;
+  if (!mlp) {
+    P.mix_thr = 0;
+    P.mlp_W1 = P.mlp_W2 = P.mlp_W3 = nullptr;
+    P.mlp_b1 = P.mlp_b2 = P.mlp_b3 = nullptr;
+  } else {
+    if (ctx->dims.D != 6) return fail(ctx, KP_ERR_ARG, "the learned proposal needs a 6D system");
+    if (!(mix >= 0.0f && mix <= 1.0f)) return fail(ctx, KP_ERR_ARG, "mix must be in [0, 1]");
+    const void *W1, *W2, *W3;
+    mlp_device_weights(mlp, &W1, &P.mlp_b1, &W2, &P.mlp_b2, &W3, &P.mlp_b3);
+    P.mlp_W1 = static_cast<const uint16_t*>(W1);
+    P.mlp_W2 = static_cast<const uint16_t*>(W2);
+    P.mlp_W3 = static_cast<const uint16_t*>(W3);
+    const double thr = std::floor((double)mix * 4294967296.0);
+    P.mix_thr = thr >= 4294967295.0 ? 0xffffffffu : (uint32_t)thr;
+    if (P.mix_thr == 0) P.mlp_W1 = nullptr;
+  }
+  P.features_on = (P.mix_thr != 0 || P.hv_cap > 0) ? 1 : 0;
+  return configure_launch(ctx);
+}
+
+kp_status kp_set_harvest(kp_ctx* ctx, float* dev_feat, float* dev_target, int32_t capacity,
+                         uint32_t* dev_count) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  KParams& P = ctx->P;
+  if (!dev_feat || !dev_target || !dev_count || capacity <= 0) {
+    P.hv_feat = P.hv_target = nullptr;
+    P.hv_count = nullptr;
+    P.hv_cap = 0;
+  } else {
+    if (ctx->dims.D != 6) return fail(ctx, KP_ERR_ARG, "the harvest needs a 6D system");
+    P.hv_feat = dev_feat;
+    P.hv_target = dev_target;
+    P.hv_count = dev_count;
+    P.hv_cap = capacity;
+  }
+  P.features_on = (P.mix_thr != 0 || P.hv_cap > 0) ? 1 : 0;
+  return configure_launch(ctx);
+}
+
 const char* kp_last_error(const kp_ctx* ctx) {
   if (!ctx) return "null context";
   return ctx->err.c_str();
@@ -1110,6 +1169,7 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   }
   const int min_ch = d.R_pad / (d.R_pad < 128 ? d.R_pad : 128);
   const int sd = min_ch > 1024 ? min_ch : 1024;
+  P.sd_bytes = sd * 8;
   const size_t smem = (size_t)P.blob_bytes + (size_t)sd * 8;
   if (occupancy(d.sys, false, smem, &bps) != cudaSuccess || bps < 1) {
     cudaGetLastError();

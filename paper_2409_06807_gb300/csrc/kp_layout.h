@@ -130,6 +130,7 @@ struct KParams {
   const float* boxes;
   int32_t n_boxes_pad;
   int32_t blob_bytes;
+  int32_t sd_bytes;      // score scratch after the blob; the network tile follows
   int32_t bp_g;          // broad-phase cells per axis (1 = every box in one cell)
   int32_t bp_start_off;  // byte offsets inside the blob
   int32_t bp_ids_off;
@@ -169,6 +170,22 @@ struct KParams {
   float* traj;        // [KP_TRAJ_ROWS][17]: state 12, ctrl 4, steps
   KLog log;
   uint64_t wait_ns;
+  // learned proposal and training-pair harvest (6D systems)
+  const uint16_t* mlp_W1;  // bf16 [256][32]
+  const float* mlp_b1;
+  const uint16_t* mlp_W2;  // bf16 [256][256]
+  const float* mlp_b2;
+  const uint16_t* mlp_W3;  // bf16 [8][256]
+  const float* mlp_b3;
+  uint32_t mix_thr;        // learned draw iff selector word < mix_thr (0: off)
+  int32_t features_on;     // node features computed each pass
+  uint16_t* feat;          // bf16 [t_e][32]: features of the V_E positions
+  float* net_raw;          // [t_e][8]: network outputs of the V_E positions
+  float feat_scale[6];     // 2 / (hi - lo) of a bounded state entry, 0 if unbounded
+  float* hv_feat;          // harvest: [hv_cap][32]
+  float* hv_target;        // [hv_cap][4]
+  uint32_t* hv_count;
+  int32_t hv_cap;
 };
 
 }  // namespace kp

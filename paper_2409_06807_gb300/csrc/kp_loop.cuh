@@ -27,6 +27,7 @@
 #include <cstdint>
 
 #include "kp_device.cuh"
+#include "kp_mlp.cuh"
 
 namespace kp {
 
@@ -192,6 +193,106 @@ __device__ __forceinline__ int write_ve(const KParams& P, int n, LoopShared& sh,
   return (int)total;
 }
 
+// ---------------------------------------------------------------------------
+// learned proposal: node features and the network (6D systems)
+// ---------------------------------------------------------------------------
+
+// The 32 features of node v (the last 12 zero) under the current region
+// tables: bounded state entries mapped to [-1, 1], an unbounded one wrapped
+// to [-pi, pi) and divided by pi; goal minus position; Cov / n'; FreeVol /
+// vol; log(1 + n_valid); log(1 + n_invalid); P_accept of the node's region
+// and of its six face neighbours in the position grid (0 outside).
+__device__ __forceinline__ void node_features(const KParams& P, int v, float* f) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) f[i] = 0.0f;
+  float x[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) x[i] = P.st[(size_t)i * P.t_e + v];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    if (P.feat_scale[i] > 0.0f) {
+      f[i] = (x[i] - P.x_lo[i]) * P.feat_scale[i] - 1.0f;
+    } else {
+      const float y = x[i] - 6.28318530717958648f * floorf((x[i] + 3.14159265358979324f) *
+                                                           0.159154943091895336f);
+      f[i] = y * 0.318309886183790672f;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) f[6 + a] = P.goal_c[a] - x[a];
+  const int r = P.region[v];
+  const float nv = (float)P.n_valid[r], ni = (float)P.n_invalid[r], dl = (float)P.delta;
+  f[9] = (float)P.cov[r] / (float)P.n_sub_per;
+  f[10] = (dl + nv) / (dl + nv + ni);
+  f[11] = log1pf(nv);
+  f[12] = log1pf(ni);
+  const float inv32 = 2.3283064365386963e-10f;
+  f[13] = (float)P.thr[r] * inv32;
+  const int gx = P.grid[0], gy = P.grid[1], gz = P.grid[2];
+  const int cx = r % gx, cy = (r / gx) % gy, cz = (r / (gx * gy)) % gz, sb = r / (gx * gy * gz);
+  const int dx[6] = {-1, 1, 0, 0, 0, 0}, dy[6] = {0, 0, -1, 1, 0, 0}, dz[6] = {0, 0, 0, 0, -1, 1};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int nx = cx + dx[k], ny = cy + dy[k], nz = cz + dz[k];
+    if (nx < 0 || nx >= gx || ny < 0 || ny >= gy || nz < 0 || nz >= gz) continue;
+    f[14 + k] = (float)P.thr[nx + gx * (ny + gy * (nz + gz * sb))] * inv32;
+  }
+}
+
+// Phase F: features of every V_E position (kept for the harvest) and, with
+// a network attached, its outputs, in tiles of 32 positions per block.
+__device__ __forceinline__ void phase_features(const KParams& P, int n_ve, unsigned char* mtile) {
+  __nv_bfloat16* sX = reinterpret_cast<__nv_bfloat16*>(mtile);
+  __nv_bfloat16* sH = sX + MLP_TILE * MLP_XS;
+  MlpWeights w;
+  w.W1 = reinterpret_cast<const __nv_bfloat16*>(P.mlp_W1);
+  w.b1 = P.mlp_b1;
+  w.W2 = reinterpret_cast<const __nv_bfloat16*>(P.mlp_W2);
+  w.b2 = P.mlp_b2;
+  w.W3 = reinterpret_cast<const __nv_bfloat16*>(P.mlp_W3);
+  w.b3 = P.mlp_b3;
+  const int n_tiles = (n_ve + MLP_TILE - 1) / MLP_TILE;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int p0 = tile * MLP_TILE;
+    const int rows = n_ve - p0 < MLP_TILE ? n_ve - p0 : MLP_TILE;
+    if (threadIdx.x < MLP_TILE) {
+      float f[32];
+      if ((int)threadIdx.x < rows) {
+        node_features(P, P.ve[p0 + threadIdx.x], f);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) f[i] = 0.0f;
+      }
+#pragma unroll
+      for (int c = 0; c < 32; c += 2) {
+        const uint32_t v2 = pack_bf16(f[c], f[c + 1]);
+        *reinterpret_cast<uint32_t*>(sX + threadIdx.x * MLP_XS + c) = v2;
+        if ((int)threadIdx.x < rows)
+          *reinterpret_cast<uint32_t*>(P.feat + (size_t)(p0 + threadIdx.x) * 32 + c) = v2;
+      }
+    }
+    __syncthreads();
+    if (P.mix_thr) mlp_tile_forward(w, sX, sH, P.net_raw, p0, rows, nullptr, nullptr);
+    __syncthreads();
+  }
+}
+
+// Standard normals z[0..3] from four Philox words (Box-Muller, pairs of
+// words: radius from the first, angle from the second).
+__device__ __forceinline__ void box_muller4(uint4 w, float* z) {
+  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {
+    const float r1 = (float)((ws[2 * pr] >> 8) + 1u) * 5.9604644775390625e-08f;  // (0, 1]
+    const float r2 = (float)(ws[2 * pr + 1] >> 8) * 5.9604644775390625e-08f;     // [0, 1)
+    const float rad = sqrtf(-2.0f * logf(r1));
+    float s, c;
+    sincospif(2.0f * r2, &s, &c);
+    z[2 * pr] = rad * c;
+    z[2 * pr + 1] = rad * s;
+  }
+}
+
 // Phase E: Algorithm 2 for every sample key in [0, S).
 //
 // Lanes integrate step by step and are refilled as they finish: a warp
@@ -330,6 +431,20 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const unsigned ch
 #pragma unroll
           for (int d = 0; d < N; ++d) u[d] = fmaf(P.u_scale[d], unit24(wr[d]), P.u_lo[d]);
           k = P.k_min + (int)__umulhi(w1.x, P.k_span);
+          if (w1.z < P.mix_thr) {
+            // learned draw from the node's Gaussian (normals: purpose 3)
+            const uint4 w3 =
+                philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 3u), P.seed_lo, P.seed_hi);
+            float z[4], mean[MLP_NQ], ls[MLP_NQ], q[4];
+            box_muller4(w3, z);
+            mlp_heads(P.net_raw + (size_t)p * MLP_OUT, mean, ls);
+#pragma unroll
+            for (int d = 0; d < 4; ++d) q[d] = fminf(fmaxf(mean[d] + expf(ls[d]) * z[d], -1.0f), 1.0f);
+#pragma unroll
+            for (int d = 0; d < N; ++d) u[d] = P.u_lo[d] + P.u_scale[d] * ((q[d] + 1.0f) * 0.5f);
+            const int kk = P.k_min + (int)floorf((float)(P.k_span - 1) * ((q[3] + 1.0f) * 0.5f) + 0.5f);
+            k = kk < P.k_min + (int)P.k_span - 1 ? kk : P.k_min + (int)P.k_span - 1;
+          }
           wacc = w1.y;
           i = 0;
           fail = 0;
@@ -533,8 +648,23 @@ __device__ __forceinline__ void phase_append(const KParams& P, int S, int lam, i
 #pragma unroll
       for (int i = 0; i < N; ++i) P.ctrl[(size_t)i * P.t_e + id] = P.cctrl[(size_t)i * P.t_e + key];
       const int s = P.cs[key];
+      const int pos_ve = key / lam;
       P.steps[id] = P.ck[key];
-      P.parent[id] = P.ve[key / lam];
+      P.parent[id] = P.ve[pos_ve];
+      if (P.hv_cap > 0 && (f & KP_F_WINNER)) {
+        // training pair: the parent's features and this sample's draw
+        const uint32_t h = atomicAdd(P.hv_count, 1u);
+        if (h < (uint32_t)P.hv_cap) {
+          const __nv_bfloat16* fr = reinterpret_cast<const __nv_bfloat16*>(P.feat) + (size_t)pos_ve * 32;
+          for (int c = 0; c < 32; ++c) P.hv_feat[(size_t)h * 32 + c] = __bfloat162float(fr[c]);
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            P.hv_target[(size_t)h * 4 + d] =
+                2.0f * (P.cctrl[(size_t)d * P.t_e + key] - P.u_lo[d]) / P.u_scale[d] - 1.0f;
+          P.hv_target[(size_t)h * 4 + 3] =
+              P.k_span > 1 ? 2.0f * (float)(P.ck[key] - P.k_min) / (float)(P.k_span - 1) - 1.0f : 0.0f;
+        }
+      }
       P.region[id] = P.cr[key];
       P.node_sub[id] = s;
       P.in_ve[id] = 1;
@@ -631,7 +761,17 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParam
       t_mark = now;
     }
   };
+  unsigned char* mtile = smem + P.blob_bytes + P.sd_bytes;
   for (;;) {
+    if (P.features_on) {
+      phase_features(P, n_ve, mtile);
+      if (!grid_sync(ctl, G, P.wait_ns, 19)) return;
+    }
+    if (timer) {  // network time goes to slot 3
+      const uint64_t now = global_ns();
+      phase_ns[3] = (int32_t)(now - t_mark);
+      t_mark = now;
+    }
     const int S = n_ve > 0 ? n_ve * lam : 0;
     phase_expand<SYS, LOG>(P, smem, it, lam, S, sh);
     stamp(0);
@@ -639,13 +779,12 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParam
     stamp(1);
     const int acc_off = phase_accept(P, S, nch, sd, sh);
     stamp(2);
-    stamp(3);
     if (!grid_sync(ctl, G, P.wait_ns, 21)) return;
     stamp(4);
     int n_acc;
     phase_append<SYS, LOG>(P, S, lam, n_tree, nch, acc_off, &n_acc);
     stamp(5);
-    stamp(6);
+    if (timer) phase_ns[6] = 0;
     if (!grid_sync(ctl, G, P.wait_ns, 22)) return;
     stamp(7);
     const int t_old = n_tree;

@@ -121,6 +121,19 @@ SIGNATURES = {
     "kp_plan_static": (C.c_int, [C.POINTER(System), C.POINTER(Workspace), C.POINTER(Obstacles),
                                  C.POINTER(Params), C.POINTER(C.c_float), C.POINTER(Goal),
                                  C.POINTER(Budget), C.POINTER(Traj), _vp]),
+    "kp_mlp_num_params": (C.c_int32, []),
+    "kp_mlp_required_bytes": (C.c_size_t, [C.c_int32]),
+    "kp_mlp_create": (C.c_int, [_vp, C.c_size_t, C.c_int32, C.POINTER(C.c_float), _vp,
+                                C.POINTER(_vp)]),
+    "kp_mlp_set_params": (C.c_int, [_vp, C.POINTER(C.c_float)]),
+    "kp_mlp_get_params": (C.c_int, [_vp, C.POINTER(C.c_float)]),
+    "kp_mlp_forward": (C.c_int, [_vp, _vp, C.c_int32, _vp]),
+    "kp_mlp_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.POINTER(C.c_float),
+                                   C.POINTER(C.c_float)]),
+    "kp_mlp_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
+    "kp_mlp_destroy": (None, [_vp]),
+    "kp_attach_mlp": (C.c_int, [_vp, _vp, C.c_float]),
+    "kp_set_harvest": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp]),
     "kp_last_error": (C.c_char_p, [_vp]),
     "kp_destroy": (None, [_vp]),
 }
@@ -389,6 +402,37 @@ class Planner:
                 a = a.reshape(-1, 12)[:, : self.d]
             out[k] = a[:n]
         return out
+
+    # ------------------------------------------------------------------
+    def attach_mlp(self, mlp, mix=0.5):
+        """Learned proposal: mix fraction of samples drawn from the network."""
+        self._mlp = mlp
+        self._check(lib().kp_attach_mlp(self._ctx, mlp._ctx if mlp is not None else None,
+                                        float(mix)), "kp_attach_mlp")
+
+    def set_harvest(self, capacity):
+        """Collect (parent features, normalised draw) of every representative
+        of a newly reached sub-region into device buffers of 'capacity' rows."""
+        import torch
+        if capacity is None or capacity <= 0:
+            self._check(lib().kp_set_harvest(self._ctx, None, None, 0, None), "kp_set_harvest")
+            self._hv = None
+            return
+        dev = self.device
+        self._hv = (torch.zeros((capacity, 32), dtype=torch.float32, device=dev),
+                    torch.zeros((capacity, 4), dtype=torch.float32, device=dev),
+                    torch.zeros(1, dtype=torch.int32, device=dev), capacity)
+        self._check(lib().kp_set_harvest(self._ctx, self._hv[0].data_ptr(), self._hv[1].data_ptr(),
+                                         capacity, self._hv[2].data_ptr()), "kp_set_harvest")
+
+    def harvest(self):
+        """(features, targets) tensors of the pairs collected so far."""
+        self.stream.synchronize()
+        n = min(int(self._hv[2].item()), self._hv[3])
+        return self._hv[0][:n], self._hv[1][:n]
+
+    def harvest_reset(self):
+        self._hv[2].zero_()
 
     # ------------------------------------------------------------------
     def set_wait_limit(self, ns):

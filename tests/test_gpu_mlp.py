@@ -1,0 +1,182 @@
+"""The learned proposal's network kernels (BF16 tensor cores, FP32
+accumulation) against the FP64 oracle network, and its use by the planner."""
+import numpy as np
+import pytest
+
+from oracle import kpo
+from oracle.kpo import Oracle
+from paper_2409_06807_gb300 import workloads as W
+from parity_util import compare_pass, state_scale
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2409_06807_gb300.build import build_planner
+    build_planner()
+    from paper_2409_06807_gb300 import mlp, planner
+    return mlp, planner
+
+
+def _bf16(a):
+    """Round float32 values to bfloat16 (nearest even), as float64."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _oracle_params(p):
+    """The parameters the device computes with: BF16 weights, FP32 biases."""
+    q = p.astype(np.float64).copy()
+    W1, b1, W2, b2, W3, b3 = kpo.mlp_split(q)
+    for Wm in (W1, W2, W3):
+        Wm[...] = _bf16(Wm)
+    return q
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    x = np.zeros((n, 32), np.float32)
+    x[:, :20] = rng.normal(0, 1, (n, 20))
+    t = rng.uniform(-0.95, 0.95, (n, 4)).astype(np.float32)
+    return x, t
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 200])
+def test_forward_matches_oracle(M, n):
+    import torch
+    mlp, _ = M
+    p = mlp.init_params(3)
+    _, _, _, _, _, b3 = mlp.split(p)
+    b3[4:] = -1.0
+    net = mlp.Mlp(p, max_batch=256)
+    x, _ = _data(n, 4)
+    out = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = kpo.mlp_forward(_oracle_params(p), _bf16(x))
+    np.testing.assert_allclose(out[:, :4], ref[:, :4], atol=2e-2)
+    np.testing.assert_allclose(out[:, 4:], ref[:, 4:], atol=2e-2)
+
+
+def test_gradients_match_oracle(M):
+    """Every parameter block's gradient against the FP64 oracle's
+    backpropagation (relative L2 error, BF16 activations)."""
+    import torch
+    mlp, _ = M
+    p = mlp.init_params(5)
+    net = mlp.Mlp(p, max_batch=512)
+    x, t = _data(500, 6)
+    g, loss = net.gradients(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    ref_loss, ref = kpo.mlp_loss_grad(_oracle_params(p), _bf16(x), t.astype(np.float64))
+    assert abs(loss - ref_loss) <= 2e-2 * abs(ref_loss) + 1e-3
+    for blk_g, blk_r in zip(mlp.split(g), kpo.mlp_split(ref)):
+        err = np.linalg.norm(blk_g - blk_r) / max(np.linalg.norm(blk_r), 1e-12)
+        assert err < 3e-2, err
+
+
+def test_training_lowers_the_loss(M):
+    """Targets that depend on the features: Adam steps on the device lower
+    the negative log-likelihood well below its starting value."""
+    import torch
+    mlp, _ = M
+    rng = np.random.default_rng(9)
+    x = np.zeros((8192, 32), np.float32)
+    x[:, :20] = rng.normal(0, 1, (8192, 20))
+    t = np.tanh(x[:, :4] * 0.7 + 0.05 * rng.normal(0, 1, (8192, 4))).astype(np.float32)
+    net = mlp.Mlp(mlp.init_params(1), max_batch=1024)
+    X, T = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    first = net.gradients(X[:1024], T[:1024])[1]
+    hist = mlp.train(net, X, T, epochs=6, batch=1024, lr=2e-3)
+    last = net.gradients(X[:1024], T[:1024])[1]
+    assert last < first - 1.0, (first, hist, last)
+
+
+def test_harvest_matches_oracle(M):
+    """Lock-step plain passes with the harvest on: the device collects the
+    same pairs as the oracle (features within BF16 rounding, targets within
+    float32 rounding), compared as sorted sets."""
+    import torch
+    _, P = M
+    w = W.c1(2)
+    g = P.Planner(w)
+    o = Oracle(w)
+    g.reset()
+    o.reset()
+    g.set_harvest(100000)
+    o.set_harvest(100000)
+    g.enable_log(w.t_e)
+    for _ in range(3):
+        _, ost, orec = o.iterate(records=True)
+        gs = g.expand_step(1)[0]
+        assert compare_pass(w, ost, orec, gs, g.read_log(ost["n_samples"])) == 0
+    gf, gt = (a.cpu().numpy() for a in g.harvest())
+    of, ot = o.harvest()
+    assert len(gf) == len(of) > 0
+    kg = np.lexsort(np.round(gt, 4).T[::-1])
+    ko = np.lexsort(np.round(ot, 4).T[::-1])
+    np.testing.assert_allclose(gt[kg], ot[ko], atol=1e-5)
+    np.testing.assert_allclose(gf[kg], of[ko], atol=2e-2, rtol=1e-2)
+
+
+def test_learned_pass_matches_oracle(M):
+    """One pass from the root with a network attached: samples whose
+    selector picks the uniform draw match the oracle as in the plain
+    planner; learned samples draw controls within BF16 tolerance."""
+    import torch
+    mlp, P = M
+    w = W.c2(0, lambda_max=256)
+    p = mlp.init_params(2)
+    _, _, _, _, _, b3 = mlp.split(p)
+    b3[4:] = -1.5
+    net = mlp.Mlp(p, max_batch=64)
+    g = P.Planner(w)
+    g.attach_mlp(net, 0.5)
+    o = Oracle(w)
+    o.set_mlp(_oracle_params(p).astype(np.float32), 0.5)
+    g.reset()
+    o.reset()
+    g.enable_log(4096)
+    _, ost, orec = o.iterate(records=True)
+    gs = g.expand_step(1)[0]
+    grec = g.read_log(ost["n_samples"])
+    assert gs["n_samples"] == ost["n_samples"] == 256
+    key = [w.seed & 0xFFFFFFFF, w.seed >> 32]
+    sel = np.array([kpo.philox4x32_10([0, 0, j, 1], key)[2] for j in range(256)])
+    learned = sel < 2 ** 31
+    assert 0.35 < learned.mean() < 0.65
+    uni = ~learned
+    assert np.array_equal(grec["k"][uni], orec["k"][uni])
+    ok = (grec["flags"][uni] & 1) == (orec["flags"][uni] & 1)
+    amb = orec["m_valid"][uni] < 1e-4
+    assert np.all(ok | amb)
+    assert np.all(np.abs(grec["k"][learned] - orec["k"][learned]) <= 1)
+
+
+def test_learned_plan_revalidated(M):
+    """A trained network on the Dubins forest: every returned trajectory
+    is valid under the oracle's dense re-check."""
+    import torch
+    mlp, P = M
+    feats, targs = mlp.harvest(W.c2, list(range(3)), 60000)
+    net = mlp.Mlp(max_batch=4096)
+    mlp.train(net, feats, targs, epochs=2, batch=4096, lr=2e-3)
+    for seed in (50, 51):
+        w = W.c2(seed)
+        g = P.Planner(w)
+        g.attach_mlp(net, 0.5)
+        st, traj = g.plan(max_iters=200)
+        if st != P.OK:
+            continue
+        o = Oracle(w)
+        scale = state_scale(w)
+        prev = w.x_init.astype(np.float64)
+        for e in range(len(traj["steps"])):
+            depth, x_end = o.dense_check(prev, traj["ctrls"][e].astype(np.float64),
+                                         int(traj["steps"][e]), 100)
+            assert depth <= 1e-4
+            assert np.max(np.abs(x_end - traj["states"][e]) / scale) <= 1e-4
+            prev = traj["states"][e].astype(np.float64)
+        assert np.linalg.norm(prev[:3] - w.goal_c) <= float(w.goal_r) * (1 + 1e-6)
