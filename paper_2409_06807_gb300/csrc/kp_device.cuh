@@ -34,29 +34,39 @@ __device__ __forceinline__ void raise_error(KCtl* ctl, int code, int where) {
   if (atomicCAS(&ctl->err, 0, code) == 0) ctl->err_where = where;
 }
 
-// Grid-wide barrier for a cooperative launch.  Every wait is bounded by
+// A team of blocks that plans one query: block index within the team, team
+// size, and the team's barrier words.  The single-query launch is one team
+// of the whole grid; the server launch splits its grid into teams.
+struct Team {
+  int b, nb;
+  uint32_t* bar_count;
+  uint32_t* bar_gen;
+};
+
+// Barrier of a team of co-resident blocks (cooperative launch).  Every wait
+// is bounded by
 // 'limit_ns' of device time; on expiry the block records KP_ERR_TIMEOUT and
 // all blocks leave at their next barrier.  Returns false when the launch
 // must stop.  Sense is carried by a generation counter: a block reads the
 // generation, arrives, and the last arriver resets the count and publishes
 // the next generation with release semantics.
-__device__ __forceinline__ bool grid_sync(KCtl* ctl, uint32_t nblocks, uint64_t limit_ns,
-                                          int where) {
+__device__ __forceinline__ bool team_sync(const Team& T, KCtl* ctl, uint64_t limit_ns, int where) {
+  const uint32_t nblocks = (uint32_t)T.nb;
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    uint32_t gen = ld_acquire(&ctl->bar_gen);
+    uint32_t gen = ld_acquire(T.bar_gen);
     __threadfence();
-    uint32_t ticket = atomicAdd(&ctl->bar_count, 1u);
+    uint32_t ticket = atomicAdd(T.bar_count, 1u);
     if (ticket == nblocks - 1) {
-      ctl->bar_count = 0;
+      *T.bar_count = 0;
       __threadfence();
-      st_release(&ctl->bar_gen, gen + 1);
+      st_release(T.bar_gen, gen + 1);
     } else {
       const uint64_t t0 = global_ns();
       uint32_t spins = 0;
-      while (ld_acquire(&ctl->bar_gen) == gen) {
+      while (ld_acquire(T.bar_gen) == gen) {
         if ((++spins & 63u) == 0) {
           if (*((volatile int*)&ctl->err) != 0) { ok = 0; break; }
           if (global_ns() - t0 > limit_ns) {

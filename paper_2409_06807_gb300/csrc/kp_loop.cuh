@@ -104,9 +104,9 @@ __device__ __forceinline__ int eq6_lambda(int t_e, int n_tree, int n_ve, int lam
 }
 
 // Node chunk [v0, v1) of this block over n nodes.
-__device__ __forceinline__ void chunk_of(int n, int* c0, int* c1) {
-  const int per = (n + (int)gridDim.x - 1) / (int)gridDim.x;
-  const long long a = (long long)blockIdx.x * per;
+__device__ __forceinline__ void chunk_of(const Team& T, int n, int* c0, int* c1) {
+  const int per = (n + T.nb - 1) / T.nb;
+  const long long a = (long long)T.b * per;
   *c0 = (int)(a < n ? a : n);
   *c1 = (int)(a + per < n ? a + per : n);
 }
@@ -135,13 +135,14 @@ __device__ __forceinline__ void scan_run(int c0, int c1, int* r0, int* r1) {
 }
 
 // Sum of blk[0..G) and of blk[0..blockIdx.x), by one warp (no block sync).
-__device__ __forceinline__ void warp_prefix(const uint32_t* blk, unsigned long long* before,
+__device__ __forceinline__ void warp_prefix(const Team& T, const uint32_t* blk,
+                                            unsigned long long* before,
                                             unsigned long long* total) {
   unsigned long long pre = 0, tot = 0;
-  for (int i = (int)(threadIdx.x & 31u); i < (int)gridDim.x; i += 32) {
+  for (int i = (int)(threadIdx.x & 31u); i < T.nb; i += 32) {
     const unsigned long long c = __ldcg(blk + i);
     tot += c;
-    if (i < (int)blockIdx.x) pre += c;
+    if (i < T.b) pre += c;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -153,40 +154,41 @@ __device__ __forceinline__ void warp_prefix(const uint32_t* blk, unsigned long l
 }
 
 // Sum of blk[0..G) and of blk[0..blockIdx.x).
-__device__ __forceinline__ void block_prefix(const uint32_t* blk, LoopShared& sh,
+__device__ __forceinline__ void block_prefix(const Team& T, const uint32_t* blk, LoopShared& sh,
                                              unsigned long long* before,
                                              unsigned long long* total) {
   unsigned long long pre = 0, tot = 0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-    const unsigned long long c = blk[i];
+  for (int i = threadIdx.x; i < T.nb; i += blockDim.x) {
+    const unsigned long long c = __ldcg(blk + i);
     tot += c;
-    if (i < (int)blockIdx.x) pre += c;
+    if (i < T.b) pre += c;
   }
   block_sum2(pre, tot, sh.red, before, total);
 }
 
 // Phase N': count V_E members of this block's node chunk (no draws).
 // Returns this thread's offset inside the block.
-__device__ __forceinline__ int count_ve(const KParams& P, int n, LoopShared& sh) {
+__device__ __forceinline__ int count_ve(const KParams& P, const Team& T, int n, LoopShared& sh) {
   int v0, v1, r0, r1;
-  chunk_of(n, &v0, &v1);
+  chunk_of(T, n, &v0, &v1);
   thread_run(v0, v1, &r0, &r1);
   int c = 0;
   for (int v = r0; v < r1; ++v) c += P.in_ve[v] ? 1 : 0;
   int tot;
   const int off = block_exclusive_scan(c, sh.scan, &tot);
-  if (threadIdx.x == 0) P.blk_b[blockIdx.x] = (uint32_t)tot;
+  if (threadIdx.x == 0) P.blk_b[T.b] = (uint32_t)tot;
   return off;
 }
 
 // Phase L: write the V_E list (ascending node id) from the per-block counts
 // and this thread's offset; returns |V_E|.
-__device__ __forceinline__ int write_ve(const KParams& P, int n, LoopShared& sh, int thread_off) {
+__device__ __forceinline__ int write_ve(const KParams& P, const Team& T, int n, LoopShared& sh,
+                                        int thread_off) {
   int v0, v1, r0, r1;
-  chunk_of(n, &v0, &v1);
+  chunk_of(T, n, &v0, &v1);
   thread_run(v0, v1, &r0, &r1);
   unsigned long long off, total;
-  block_prefix(P.blk_b, sh, &off, &total);
+  block_prefix(T, P.blk_b, sh, &off, &total);
   int pos = (int)off + thread_off;
   for (int v = r0; v < r1; ++v)
     if (P.in_ve[v]) P.ve[pos++] = v;
@@ -241,7 +243,8 @@ __device__ __forceinline__ void node_features(const KParams& P, int v, float* f)
 
 // Phase F: features of every V_E position (kept for the harvest) and, with
 // a network attached, its outputs, in tiles of 32 positions per block.
-__device__ __forceinline__ void phase_features(const KParams& P, int n_ve, unsigned char* mtile) {
+__device__ __forceinline__ void phase_features(const KParams& P, const Team& T, int n_ve,
+                                               unsigned char* mtile) {
   __nv_bfloat16* sX = reinterpret_cast<__nv_bfloat16*>(mtile);
   __nv_bfloat16* sH = sX + MLP_TILE * MLP_XS;
   MlpWeights w;
@@ -252,7 +255,7 @@ __device__ __forceinline__ void phase_features(const KParams& P, int n_ve, unsig
   w.W3 = reinterpret_cast<const __nv_bfloat16*>(P.mlp_W3);
   w.b3 = P.mlp_b3;
   const int n_tiles = (n_ve + MLP_TILE - 1) / MLP_TILE;
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  for (int tile = T.b; tile < n_tiles; tile += T.nb) {
     const int p0 = tile * MLP_TILE;
     const int rows = n_ve - p0 < MLP_TILE ? n_ve - p0 : MLP_TILE;
     if (threadIdx.x < MLP_TILE) {
@@ -307,8 +310,9 @@ constexpr int KP_REFILL_MIN = 8;  // lanes that must be free before a refill
 constexpr int KP_KEY_BATCH = 128; // keys a warp takes from the grid counter
 
 template <int SYS, bool LOG>
-__device__ __forceinline__ void phase_expand(const KParams& P, const unsigned char* sblob,
-                                             uint32_t it, int lam, int S, LoopShared& sh) {
+__device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
+                                             const unsigned char* sblob, uint32_t it, int lam,
+                                             int S, LoopShared& sh) {
   using Sys = System<SYS>;
   constexpr int D = Sys::D, N = Sys::N;
   const float4* sbox = reinterpret_cast<const float4*>(sblob);
@@ -401,7 +405,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const unsigned ch
           // (at the very end a warp takes only what its idle lanes can
           // start now, so no warp is left with a second round of samples)
           const int n_idle_now = __popc(m_idle);
-          int want = (S - pool_end) / (2 * (int)(gridDim.x * (blockDim.x >> 5)));
+          int want = (S - pool_end) / (2 * T.nb * (int)(blockDim.x >> 5));
           want = want < n_idle_now ? n_idle_now : (want > KP_KEY_BATCH ? KP_KEY_BATCH : want);
           int base = 0;
           if (lane == 0) base = atomicAdd(&P.ctl->work_next, want);
@@ -494,13 +498,13 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const unsigned ch
 // Publishes the block's accepted count and adds the valid count to the
 // pass; returns this thread's offset among the block's accepted samples
 // (kept in a register across the grid barrier).
-__device__ __forceinline__ void phase_scores(const KParams& P, int nch, double* sd);
+__device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, int nch, double* sd);
 
-__device__ __forceinline__ int phase_accept(const KParams& P, int S, int nch, double* sd,
-                                            LoopShared& sh) {
-  if (threadIdx.x < 32) phase_scores(P, nch, sd);
+__device__ __forceinline__ int phase_accept(const KParams& P, const Team& T, int S, int nch,
+                                            double* sd, LoopShared& sh) {
+  if (threadIdx.x < 32) phase_scores(P, T, nch, sd);
   int k0, k1, r0, r1;
-  chunk_of(S, &k0, &k1);
+  chunk_of(T, S, &k0, &k1);
   scan_run(k0, k1, &r0, &r1);
   int acc_n = 0;
   unsigned long long valid_n = 0;
@@ -524,8 +528,8 @@ __device__ __forceinline__ int phase_accept(const KParams& P, int S, int nch, do
   unsigned long long b, dummy;
   block_sum2(valid_n, 0, sh.red, &b, &dummy);
   if (threadIdx.x == 0) {
-    if (blockIdx.x == 0) P.ctl->work_next = 0;  // the expand phase is over
-    P.blk_a[blockIdx.x] = (uint32_t)block_acc;
+    if (T.b == 0) P.ctl->work_next = 0;  // the expand phase is over
+    P.blk_a[T.b] = (uint32_t)block_acc;
     if (b) atomicAdd(&P.ctl->it_valid, (uint32_t)b);
   }
   return off;
@@ -550,11 +554,11 @@ __device__ __forceinline__ void warp_pairwise(double* buf, int n) {
 // FreeVol = ((delta + nv) vol) / ((delta + nv) + ni),
 // f4 = (FreeVol FreeVol)(FreeVol FreeVol),
 // Score = f4 / ((1 + Cov)(1 + (nv + ni)(nv + ni))).
-__device__ __forceinline__ void phase_scores(const KParams& P, int nch, double* sd) {
-  if ((int)blockIdx.x >= nch) return;
+__device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, int nch, double* sd) {
+  if (T.b >= nch) return;
   const int lane = (int)(threadIdx.x & 31u);
   const int ch = P.R_pad / nch;
-  const int r0 = blockIdx.x * ch;
+  const int r0 = T.b * ch;
   for (int i = lane; i < ch; i += 32) {
     const int r = r0 + i;
     double sc = 0.0;
@@ -575,7 +579,7 @@ __device__ __forceinline__ void phase_scores(const KParams& P, int nch, double* 
   warp_pairwise(sd, ch);
   int last = 0;
   if (lane == 0) {
-    P.chunk_sum[blockIdx.x] = sd[0];
+    P.chunk_sum[T.b] = sd[0];
     __threadfence();
     last = atomicAdd(&P.ctl->s_done, 1u) == (uint32_t)(nch - 1);
   }
@@ -594,11 +598,11 @@ __device__ __forceinline__ void phase_scores(const KParams& P, int nch, double* 
 
 // Phase T (warp 0): P_accept and the integer threshold of this block's
 // region chunk (Eq. 5), from the sum the last chunk published.
-__device__ __forceinline__ void phase_thresholds(const KParams& P, int nch) {
-  if ((int)blockIdx.x >= nch) return;
+__device__ __forceinline__ void phase_thresholds(const KParams& P, const Team& T, int nch) {
+  if (T.b >= nch) return;
   const double sum = __ldcg(&P.ctl->score_sum);
   const int ch = P.R_pad / nch;
-  const int r0 = blockIdx.x * ch;
+  const int r0 = T.b * ch;
   for (int i = (int)(threadIdx.x & 31u); i < ch; i += 32) {
     const int r = r0 + i;
     if (r >= P.R) break;
@@ -621,18 +625,18 @@ __device__ __forceinline__ void phase_thresholds(const KParams& P, int nch) {
 // each thread writes the accepted samples of its own run from its offset.
 // Phase T (warp 0) runs alongside.  No block-wide synchronisation.
 template <int SYS, bool LOG>
-__device__ __forceinline__ void phase_append(const KParams& P, int S, int lam, int t_old,
-                                             int nch, int thread_off, int* total_out) {
+__device__ __forceinline__ void phase_append(const KParams& P, const Team& T, int S, int lam,
+                                             int t_old, int nch, int thread_off, int* total_out) {
   constexpr int D = System<SYS>::D, N = System<SYS>::N;
   unsigned long long off, total;
-  warp_prefix(P.blk_a, &off, &total);
+  warp_prefix(T, P.blk_a, &off, &total);
   *total_out = (int)total;
   if (threadIdx.x < 32) {
-    phase_thresholds(P, nch);
+    phase_thresholds(P, T, nch);
     return;
   }
   int k0, k1, r0, r1;
-  chunk_of(S, &k0, &k1);
+  chunk_of(T, S, &k0, &k1);
   scan_run(k0, k1, &r0, &r1);
   int id = t_old + (int)off + thread_off;
   for (int key = r0; key < r1; ++key) {
@@ -683,10 +687,10 @@ __device__ __forceinline__ void phase_append(const KParams& P, int S, int lam, i
 // Phase N: Algorithm 4 node sets, one draw per old node (counter: it, v, 0,
 // purpose 2) against the threshold of its region; new nodes are in V_E.
 // Returns this thread's offset among the block's V_E members.
-__device__ __forceinline__ int phase_nodesets(const KParams& P, uint32_t it, int t_old,
-                                              int t_new, LoopShared& sh) {
+__device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, uint32_t it,
+                                              int t_old, int t_new, LoopShared& sh) {
   int v0, v1, r0, r1;
-  chunk_of(t_new, &v0, &v1);
+  chunk_of(T, t_new, &v0, &v1);
   thread_run(v0, v1, &r0, &r1);
   int c = 0;
   for (int v = r0; v < r1; ++v) {
@@ -700,30 +704,21 @@ __device__ __forceinline__ int phase_nodesets(const KParams& P, uint32_t it, int
   }
   int tot;
   const int off = block_exclusive_scan(c, sh.scan, &tot);
-  if (threadIdx.x == 0) P.blk_b[blockIdx.x] = (uint32_t)tot;
+  if (threadIdx.x == 0) P.blk_b[T.b] = (uint32_t)tot;
   return off;
 }
 
-#ifndef KP_MIN_BLOCKS
-#define KP_MIN_BLOCKS 1
-#endif
+// The loop of one query (Algorithm 1 body, repeated) run by a team of
+// blocks, with the query's obstacle blob already in shared memory.  Stops
+// when a goal node is appended, Eq. 6 gives lambda = 0, or the pass or time
+// budget is spent.  Returns false when a bounded wait expired.
 template <int SYS, bool LOG>
-__global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParams P, int max_iters,
-                                                           uint64_t max_ns) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ LoopShared sh;
-  float4* sbox = reinterpret_cast<float4*>(smem);
+__device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsigned char* smem,
+                                         LoopShared& sh, int max_iters, uint64_t max_ns) {
   double* sd = reinterpret_cast<double*>(smem + (size_t)P.blob_bytes);
   KCtl* ctl = P.ctl;
-  const uint32_t G = gridDim.x;
   const uint64_t t_start = global_ns();
-
-  if (ctl->state != KP_DEV_RUNNING) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_run = 0;
-    return;
-  }
-  if (!stage_boxes(P, sbox, sh)) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (T.b == 0 && threadIdx.x == 0) {
     ctl->it_valid = 0;
     ctl->stop = 0;
     ctl->n_run = 0;
@@ -735,22 +730,22 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParam
   const int nch = P.nch;
 
   // V_E list from the stored node sets
-  int ve_off = count_ve(P, n_tree, sh);
-  if (!grid_sync(ctl, G, P.wait_ns, 10)) return;
-  int n_ve = write_ve(P, n_tree, sh, ve_off);
-  if (!grid_sync(ctl, G, P.wait_ns, 11)) return;
+  int ve_off = count_ve(P, T, n_tree, sh);
+  if (!team_sync(T, ctl, P.wait_ns, 10)) return false;
+  int n_ve = write_ve(P, T, n_tree, sh, ve_off);
+  if (!team_sync(T, ctl, P.wait_ns, 11)) return false;
   int lam = eq6_lambda(P.t_e, n_tree, n_ve, P.lambda_max);
   if (n_ve > 0 && lam == 0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (T.b == 0 && threadIdx.x == 0) {
       ctl->state = KP_DEV_FULL;
       ctl->n_ve = n_ve;
     }
-    return;
+    return true;
   }
 
   int run = 0;
   // block 0 stamps the device clock between phases and barriers
-  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  const bool timer = T.b == 0 && threadIdx.x == 0;
   uint64_t t_mark = timer ? global_ns() : 0;
   int32_t phase_ns[12];
   int32_t prev_wait = 0;
@@ -764,8 +759,8 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParam
   unsigned char* mtile = smem + P.blob_bytes + P.sd_bytes;
   for (;;) {
     if (P.features_on) {
-      phase_features(P, n_ve, mtile);
-      if (!grid_sync(ctl, G, P.wait_ns, 19)) return;
+      phase_features(P, T, n_ve, mtile);
+      if (!team_sync(T, ctl, P.wait_ns, 19)) return false;
     }
     if (timer) {  // network time goes to slot 3
       const uint64_t now = global_ns();
@@ -773,31 +768,31 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParam
       t_mark = now;
     }
     const int S = n_ve > 0 ? n_ve * lam : 0;
-    phase_expand<SYS, LOG>(P, smem, it, lam, S, sh);
+    phase_expand<SYS, LOG>(P, T, smem, it, lam, S, sh);
     stamp(0);
-    if (!grid_sync(ctl, G, P.wait_ns, 20)) return;
+    if (!team_sync(T, ctl, P.wait_ns, 20)) return false;
     stamp(1);
-    const int acc_off = phase_accept(P, S, nch, sd, sh);
+    const int acc_off = phase_accept(P, T, S, nch, sd, sh);
     stamp(2);
-    if (!grid_sync(ctl, G, P.wait_ns, 21)) return;
+    if (!team_sync(T, ctl, P.wait_ns, 21)) return false;
     stamp(4);
     int n_acc;
-    phase_append<SYS, LOG>(P, S, lam, n_tree, nch, acc_off, &n_acc);
+    phase_append<SYS, LOG>(P, T, S, lam, n_tree, nch, acc_off, &n_acc);
     stamp(5);
     if (timer) phase_ns[6] = 0;
-    if (!grid_sync(ctl, G, P.wait_ns, 22)) return;
+    if (!team_sync(T, ctl, P.wait_ns, 22)) return false;
     stamp(7);
     const int t_old = n_tree;
     n_tree = t_old + n_acc;
-    ve_off = phase_nodesets(P, it, t_old, n_tree, sh);
+    ve_off = phase_nodesets(P, T, it, t_old, n_tree, sh);
     stamp(8);
-    if (!grid_sync(ctl, G, P.wait_ns, 23)) return;
+    if (!team_sync(T, ctl, P.wait_ns, 23)) return false;
     stamp(9);
     const int ve_prev = n_ve, lam_prev = lam;
-    n_ve = write_ve(P, n_tree, sh, ve_off);
+    n_ve = write_ve(P, T, n_tree, sh, ve_off);
     lam = eq6_lambda(P.t_e, n_tree, n_ve, P.lambda_max);
     ++run;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (T.b == 0 && threadIdx.x == 0) {
       const int goal = *((volatile int*)&ctl->goal_node);
       const bool solved = goal != KP_NO_GOAL;
       const bool full = n_ve > 0 && lam == 0;
@@ -824,19 +819,39 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParam
     }
     ++it;
     const uint64_t t_l = timer ? global_ns() : 0;
-    if (!grid_sync(ctl, G, P.wait_ns, 24)) return;
+    if (!team_sync(T, ctl, P.wait_ns, 24)) return false;
     if (timer) {
       t_mark = global_ns();
       prev_wait = (int32_t)(t_mark - t_l);  // reported with the next pass
     }
     if (*((volatile int*)&ctl->stop)) break;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (T.b == 0 && threadIdx.x == 0) {
     ctl->n_nodes = n_tree;
     ctl->n_ve = n_ve;
     ctl->iteration = (int)it;
     ctl->n_run = run;
   }
+  return true;
+}
+
+#ifndef KP_MIN_BLOCKS
+#define KP_MIN_BLOCKS 1
+#endif
+// Single-query launch: the whole grid is one team.
+template <int SYS, bool LOG>
+__global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParams P, int max_iters,
+                                                                         uint64_t max_ns) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ LoopShared sh;
+  KCtl* ctl = P.ctl;
+  if (ctl->state != KP_DEV_RUNNING) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_run = 0;
+    return;
+  }
+  if (!stage_boxes(P, reinterpret_cast<float4*>(smem), sh)) return;
+  const Team T{(int)blockIdx.x, (int)gridDim.x, &ctl->bar_count, &ctl->bar_gen};
+  run_loop<SYS, LOG>(P, T, smem, sh, max_iters, max_ns);
 }
 
 // Algorithm 1, lines 1-3 on the device (after the host cleared the tables):
