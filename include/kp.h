@@ -369,6 +369,64 @@ kp_status kp_attach_mlp(kp_ctx *ctx, const kp_mlp *mlp, float mix);
 kp_status kp_set_harvest(kp_ctx *ctx, float *dev_feat, float *dev_target,
                          int32_t capacity, uint32_t *dev_count);
 
+/* ---- server: many queries in one persistent launch ------------------------
+ * A server runs one persistent cooperative launch whose grid is split into
+ * teams of team_blocks blocks; each team plans one query at a time (the
+ * Algorithm 1 loop of kp_plan) and then takes the next.  Queries of any
+ * system, obstacle count and t_e are submitted while others run (continuous
+ * batching): a query is admitted when a descriptor slot and a slice of the
+ * device pool for its arena (kp_required_bytes) are free, else it waits in
+ * submission order.  A query's result depends only on its own inputs, so it
+ * is the same alone or among others.  Teams that find no work for idle_ms
+ * leave; the server launches again when work arrives.  All device memory
+ * comes from the caller's pool (kp_server_required_bytes for the control
+ * area plus the query arenas); host memory holds the rings and results.
+ * Per query: at most 1,500 obstacle boxes (blob of 48 KB) and
+ * kp_required_bytes regions up to 1024 * team_blocks in the padded count;
+ * no sample log, learned proposal or harvest. */
+typedef struct kp_server kp_server;
+typedef struct {
+  int32_t team_blocks;  /* blocks per team (>= 1); the grid is the resident
+                           maximum rounded down to whole teams           */
+  int32_t max_slots;    /* queries resident at once (1 .. 4096)          */
+  double idle_ms;       /* a team leaves after this long without work    */
+} kp_server_config;
+typedef struct {
+  int64_t id;
+  int32_t status;       /* kp_status: KP_OK solved, KP_NO_SOLUTION, error */
+  int32_t n_edges, iterations, n_nodes;
+  int64_t samples;      /* samples propagated and checked                */
+  double device_ms;     /* device time from its team's start to its end  */
+  double latency_ms;    /* host time from submission to completion seen  */
+} kp_server_done;
+typedef struct {
+  int32_t teams, team_blocks, pending, resident;
+  int64_t submitted, completed;
+  size_t pool_free;
+  int32_t device_error;  /* first device-side error (code | site << 8)    */
+  int32_t running;       /* 1 while the persistent launch is running      */
+} kp_server_stats;
+size_t kp_server_required_bytes(int32_t max_slots);
+kp_status kp_server_create(const kp_server_config *cfg, void *dev_pool,
+                           size_t pool_bytes, void *cuda_stream,
+                           kp_server **out);
+/* Copies every input; returns the query id in *id. */
+kp_status kp_server_submit(kp_server *srv, const kp_system *sys,
+                           const kp_workspace *ws, const kp_obstacles *obs,
+                           const kp_params *prm, const float *x_init,
+                           const kp_goal *goal, const kp_budget *budget,
+                           int64_t *id);
+/* Completed queries since the last call (up to capacity records); admits
+ * waiting queries into the freed resources. */
+kp_status kp_server_poll(kp_server *srv, kp_server_done *out, int32_t capacity,
+                         int32_t *n_out);
+/* Trajectory of a completed, solved query (once; KP_ERR_ARG if unknown or
+ * if traj->capacity is too small, n_edges then holds the size needed). */
+kp_status kp_server_result(kp_server *srv, int64_t id, kp_traj *traj);
+kp_status kp_server_stats_get(kp_server *srv, kp_server_stats *out);
+/* Asks the teams to leave after their current query and waits for them. */
+void kp_server_destroy(kp_server *srv);
+
 /* Last error message of the context (never NULL). */
 const char *kp_last_error(const kp_ctx *ctx);
 

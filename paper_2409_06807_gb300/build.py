@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkinopax.so")
 ROOT = os.path.dirname(HERE)
-UNITS = ["kp_api.cu", "kp_sys_di.cu", "kp_sys_dubins.cu", "kp_sys_quad.cu", "kp_mlp.cu"]
+UNITS = ["kp_api.cu", "kp_sys_di.cu", "kp_sys_dubins.cu", "kp_sys_quad.cu", "kp_mlp.cu", "kp_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

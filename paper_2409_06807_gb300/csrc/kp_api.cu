@@ -8,9 +8,14 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <atomic>
+#include <chrono>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -22,6 +27,8 @@ struct kp_mlp;
 namespace kp {
 void mlp_device_weights(const kp_mlp* n, const void** W1, const float** b1, const void** W2,
                         const float** b2, const void** W3, const float** b3);
+cudaError_t server_occupancy(size_t smem, int* blocks_per_sm);
+cudaError_t launch_server(const KServerArgs& A, int grid, size_t smem, cudaStream_t stream);
 // launchers defined in kp_sys_*.cu
 #define KP_DECLARE_SYS(name)                                                                   \
   cudaError_t loop_occupancy_##name(bool log, size_t smem, int* blocks_per_sm);                \
@@ -360,7 +367,7 @@ int host_bp_cell(float v, float lo, float scale, int g) {
 // sets the blob fields of P.  The grid is the finest of 16^3, 8^3, 4^3,
 // 2^3, 1 cells whose entry count fits KP_BP_MAX_IDS (1 cell = every box).
 size_t build_blob(unsigned char* blob, const float* boxes, int nb, const kp_workspace& ws,
-                  KParams& P) {
+                  KParams& P, size_t max_bytes = KP_BLOB_BYTES) {
   const int pad = (nb + 7) / 8 * 8;
   float* fb = reinterpret_cast<float*>(blob);
   for (int b = 0; b < pad; ++b) {
@@ -389,7 +396,9 @@ size_t build_blob(unsigned char* blob, const float* boxes, int nb, const kp_work
                  host_bp_cell(fb[b * 8 + a], ws.lo[a], scale[a], g) + 1;
       entries += cells;
     }
-    if (entries <= KP_BP_MAX_IDS || g == 1) break;
+    const size_t bytes = (size_t)pad * 32 + round16((size_t)(g * g * g + 1) * 4) +
+                         round16((size_t)entries * 2);
+    if ((entries <= KP_BP_MAX_IDS && bytes <= max_bytes) || g == 1) break;
   }
   const int C = g * g * g;
   const size_t start_off = (size_t)pad * 32;
@@ -1254,3 +1263,459 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   }
   return KP_OK;
 }
+
+// ---------------------------------------------------------------------------
+// server: host runtime
+// ---------------------------------------------------------------------------
+
+namespace {
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct PendingQuery {
+  int64_t id;
+  kp_system sys;
+  kp_workspace ws;
+  kp_params prm;
+  std::vector<float> boxes;
+  RootState root;
+  kp_goal goal;
+  kp_budget budget;
+  double t_submit;
+};
+
+struct SlotState {
+  bool used = false;
+  int64_t id = -1;
+  size_t off = 0, bytes = 0;
+  Layout lay{};
+  double t_submit = 0;
+};
+
+struct StoredResult {
+  kp_status status;
+  std::vector<float> rows;  // n_edges x 17
+  int32_t n_edges;
+};
+
+}  // namespace
+
+struct kp_server {
+  kp_server_config cfg{};
+  char* pool = nullptr;
+  size_t pool_bytes = 0;
+  cudaStream_t stream = nullptr;  // the persistent launch
+  cudaStream_t copy = nullptr;    // uploads and read-backs beside it
+  KServerDev* dev = nullptr;
+  KQuery* queries = nullptr;
+  KServerHost* host_h = nullptr;  // host view of the mapped area
+  KServerHost* host_d = nullptr;  // device view
+  int team_blocks = 0, n_teams = 0, grid = 0, num_sms = 0;
+  size_t smem = 0;
+  std::map<size_t, size_t> free_list;  // offset -> bytes
+  std::vector<SlotState> slots;
+  std::deque<PendingQuery> pending;
+  std::unordered_map<int64_t, StoredResult> results;
+  std::deque<kp_server_done> ready;
+  uint32_t posted = 0, consumed = 0;
+  int64_t next_id = 0, submitted = 0, completed = 0;
+  cudaEvent_t ev_kernel = nullptr;
+  bool launched = false;
+  bool poisoned = false;
+  std::vector<unsigned char> blob;
+};
+
+namespace {
+
+size_t server_ctl_bytes(int max_slots) {
+  return align256(sizeof(KServerDev)) + align256((size_t)max_slots * sizeof(KQuery));
+}
+
+// First fit in the pool's free list (256-byte granules).
+bool pool_alloc(kp_server* s, size_t bytes, size_t* off) {
+  bytes = align256(bytes);
+  for (auto it = s->free_list.begin(); it != s->free_list.end(); ++it) {
+    if (it->second >= bytes) {
+      *off = it->first;
+      const size_t rest = it->second - bytes;
+      const size_t o = it->first + bytes;
+      s->free_list.erase(it);
+      if (rest) s->free_list[o] = rest;
+      return true;
+    }
+  }
+  return false;
+}
+
+void pool_free(kp_server* s, size_t off, size_t bytes) {
+  bytes = align256(bytes);
+  auto it = s->free_list.emplace(off, bytes).first;
+  auto next = std::next(it);
+  if (next != s->free_list.end() && it->first + it->second == next->first) {
+    it->second += next->second;
+    s->free_list.erase(next);
+  }
+  if (it != s->free_list.begin()) {
+    auto prev = std::prev(it);
+    if (prev->first + prev->second == it->first) {
+      prev->second += it->second;
+      s->free_list.erase(it);
+    }
+  }
+}
+
+void finish_now(kp_server* s, int64_t id, kp_status st, double t_submit) {
+  kp_server_done d{};
+  d.id = id;
+  d.status = st;
+  d.latency_ms = now_ms() - t_submit;
+  s->ready.push_back(d);
+  s->results[id] = StoredResult{st, {}, 0};
+  s->completed += 1;
+}
+
+// Admits the query if a slot and pool memory are free: uploads its blob and
+// descriptor (copy stream) and publishes it.  Returns false to keep it
+// waiting; an invalid query completes at once with KP_ERR_ARG.
+bool try_admit(kp_server* s, PendingQuery& q) {
+  int slot = -1;
+  for (int i = 0; i < (int)s->slots.size(); ++i)
+    if (!s->slots[i].used) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) return false;
+  Dims d{};
+  if (check_inputs(&q.sys, &q.ws, (int)(q.boxes.size() / 6), &q.prm, &d)) {
+    finish_now(s, q.id, KP_ERR_ARG, q.t_submit);
+    return true;
+  }
+  const Layout lay = make_layout(d);
+  size_t off = 0;
+  if (!pool_alloc(s, lay.total, &off)) {
+    if (s->free_list.empty() || lay.total > s->pool_bytes) {
+      finish_now(s, q.id, KP_ERR_OOM, q.t_submit);
+      return true;
+    }
+    return false;
+  }
+  KQuery kq{};
+  KParams& P = kq.P;
+  fill_params(P, d, lay, &q.sys, &q.ws, &q.prm, s->pool + off);
+  for (int a = 0; a < 3; ++a) P.goal_c[a] = q.goal.center[a];
+  P.goal_r2 = (float)((double)q.goal.radius * (double)q.goal.radius);
+  P.seed_lo = (uint32_t)(q.prm.seed & 0xffffffffu);
+  P.seed_hi = (uint32_t)(q.prm.seed >> 32);
+  P.wait_ns = 2000000000ull;
+  int nch = 1;
+  while (nch * 2 <= s->team_blocks && nch * 2 <= d.R_pad && nch * 2 <= 1024) nch *= 2;
+  P.nch = nch;
+  P.sd_bytes = KS_SD_DOUBLES * 8;
+  const size_t blob_bytes = build_blob(s->blob.data(), q.boxes.empty() ? nullptr : q.boxes.data(),
+                                       (int)(q.boxes.size() / 6), q.ws, P, KS_BLOB_MAX);
+  if (blob_bytes > (size_t)KS_BLOB_MAX || d.R_pad / nch > KS_SD_DOUBLES) {
+    pool_free(s, off, lay.total);
+    finish_now(s, q.id, KP_ERR_ARG, q.t_submit);
+    return true;
+  }
+  kq.root = q.root;
+  kq.max_iters = q.budget.max_iters;
+  kq.id = (int32_t)q.id;
+  kq.max_ns = q.budget.max_ms > 0.0 ? (uint64_t)(q.budget.max_ms * 1e6) : 0ull;
+  bool ok = cudaMemcpyAsync(s->pool + off + lay.boxes, s->blob.data(), blob_bytes,
+                            cudaMemcpyHostToDevice, s->copy) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(s->queries + slot, &kq, sizeof(KQuery), cudaMemcpyHostToDevice,
+                             s->copy) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(s->copy) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    s->poisoned = true;
+    pool_free(s, off, lay.total);
+    finish_now(s, q.id, KP_ERR_CUDA, q.t_submit);
+    return true;
+  }
+  SlotState& ss = s->slots[slot];
+  ss.used = true;
+  ss.id = q.id;
+  ss.off = off;
+  ss.bytes = lay.total;
+  ss.lay = lay;
+  ss.t_submit = q.t_submit;
+  // publish: ring entry first, then the count
+  s->host_h->ring[s->posted % KS_RING] = (uint32_t)slot;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
+  reinterpret_cast<volatile uint32_t*>(&s->host_h->posted)[0] = s->posted + 1;
+  s->posted += 1;
+  return true;
+}
+
+void admit_pending(kp_server* s) {
+  while (!s->pending.empty()) {
+    if (!try_admit(s, s->pending.front())) break;
+    s->pending.pop_front();
+  }
+}
+
+bool any_resident(const kp_server* s) {
+  for (const auto& ss : s->slots)
+    if (ss.used) return true;
+  return false;
+}
+
+// Launches the persistent server when queries are resident and no launch
+// is running (teams leave after idle_ms without work).
+kp_status ensure_running(kp_server* s) {
+  if (reinterpret_cast<volatile int32_t*>(&s->host_h->error)[0] != 0) {
+    s->poisoned = true;  // a bounded device wait expired: no relaunch
+    return KP_ERR_TIMEOUT;
+  }
+  if (s->launched) {
+    const cudaError_t q = cudaEventQuery(s->ev_kernel);
+    if (q == cudaErrorNotReady) return KP_OK;
+    if (q != cudaSuccess) {
+      cudaGetLastError();
+      s->poisoned = true;
+      return KP_ERR_CUDA;
+    }
+    s->launched = false;
+  }
+  if (!any_resident(s)) return KP_OK;
+  KServerArgs A{};
+  A.dev = s->dev;
+  A.host = s->host_d;
+  A.queries = s->queries;
+  A.team_blocks = s->team_blocks;
+  A.idle_ns = (uint64_t)(s->cfg.idle_ms * 1e6);
+  A.wait_ns = 2000000000ull;
+  if (launch_server(A, s->grid, s->smem, s->stream) != cudaSuccess ||
+      cudaEventRecord(s->ev_kernel, s->stream) != cudaSuccess) {
+    cudaGetLastError();
+    s->poisoned = true;
+    return KP_ERR_CUDA;
+  }
+  s->launched = true;
+  return KP_OK;
+}
+
+// Reads new completion records; frees their slots and pool memory.
+kp_status collect(kp_server* s) {
+  for (;;) {
+    KDone* d = &s->host_h->done[s->consumed % KS_RING];
+    const uint32_t seq = reinterpret_cast<volatile uint32_t*>(&d->seq)[0];
+    if (seq != s->consumed + 1) break;
+    std::atomic_thread_fence(std::memory_order_acquire);
+    const KDone r = *d;
+    s->consumed += 1;
+    if (r.slot < 0 || r.slot >= (int)s->slots.size() || !s->slots[r.slot].used) {
+      s->poisoned = true;
+      return KP_ERR_STATE;
+    }
+    SlotState& ss = s->slots[r.slot];
+    kp_status st = r.err ? KP_ERR_TIMEOUT
+                         : (r.state == KP_DEV_SOLVED ? KP_OK
+                                                     : (r.state == KP_DEV_BAD_ROOT ? KP_ERR_ARG
+                                                                                   : KP_NO_SOLUTION));
+    StoredResult res{st, {}, 0};
+    if (st == KP_OK && r.n_edges >= 0 && r.n_edges <= KP_TRAJ_ROWS) {
+      res.n_edges = r.n_edges;
+      res.rows.resize((size_t)r.n_edges * 17);
+      if (r.n_edges > 0 &&
+          (cudaMemcpyAsync(res.rows.data(), s->pool + ss.off + ss.lay.traj,
+                           (size_t)r.n_edges * 17 * 4, cudaMemcpyDeviceToHost,
+                           s->copy) != cudaSuccess ||
+           cudaStreamSynchronize(s->copy) != cudaSuccess)) {
+        cudaGetLastError();
+        s->poisoned = true;
+        return KP_ERR_CUDA;
+      }
+    }
+    kp_server_done out{};
+    out.id = ss.id;
+    out.status = st;
+    out.n_edges = r.n_edges;
+    out.iterations = r.iterations;
+    out.n_nodes = r.n_nodes;
+    out.samples = (int64_t)r.samples;
+    out.device_ms = (double)(r.t_end_ns - r.t_start_ns) * 1e-6;
+    out.latency_ms = now_ms() - ss.t_submit;
+    s->ready.push_back(out);
+    s->results[ss.id] = std::move(res);
+    s->completed += 1;
+    pool_free(s, ss.off, ss.bytes);
+    ss = SlotState{};
+  }
+  return KP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t kp_server_required_bytes(int32_t max_slots) {
+  if (max_slots < 1 || max_slots > KS_RING) return 0;
+  return server_ctl_bytes(max_slots);
+}
+
+kp_status kp_server_create(const kp_server_config* cfg, void* dev_pool, size_t pool_bytes,
+                           void* cuda_stream, kp_server** out) {
+  if (!cfg || !out || !dev_pool || ((uintptr_t)dev_pool & 255u)) return KP_ERR_ARG;
+  *out = nullptr;
+  if (cfg->team_blocks < 1 || cfg->max_slots < 1 || cfg->max_slots > KS_RING ||
+      !(cfg->idle_ms > 0.0))
+    return KP_ERR_ARG;
+  const size_t ctl = server_ctl_bytes(cfg->max_slots);
+  if (pool_bytes < ctl + 256) return KP_ERR_OOM;
+  kp_server* s = new (std::nothrow) kp_server();
+  if (!s) return KP_ERR_OOM;
+  s->cfg = *cfg;
+  s->pool = static_cast<char*>(dev_pool);
+  s->pool_bytes = pool_bytes;
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  s->dev = reinterpret_cast<KServerDev*>(s->pool);
+  s->queries = reinterpret_cast<KQuery*>(s->pool + align256(sizeof(KServerDev)));
+  s->free_list[ctl] = (pool_bytes - ctl) & ~(size_t)255;
+  s->slots.resize(cfg->max_slots);
+  s->blob.resize(KP_BLOB_BYTES);
+  s->team_blocks = cfg->team_blocks;
+  auto bad = [&](kp_status st) {
+    cudaGetLastError();
+    if (s->host_h) cudaFreeHost(s->host_h);
+    if (s->copy) cudaStreamDestroy(s->copy);
+    if (s->ev_kernel) cudaEventDestroy(s->ev_kernel);
+    delete s;
+    return st;
+  };
+  int dev = 0, bps = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return bad(KP_ERR_CUDA);
+  s->smem = ((sizeof(KParams) + 127) & ~(size_t)127) + (size_t)KS_BLOB_MAX +
+            (size_t)KS_SD_DOUBLES * 8;
+  if (server_occupancy(s->smem, &bps) != cudaSuccess || bps < 1) return bad(KP_ERR_CUDA);
+  const int resident = bps * s->num_sms;
+  s->n_teams = resident / s->team_blocks;
+  if (s->n_teams < 1) return bad(KP_ERR_ARG);
+  if (s->n_teams > KS_MAX_TEAMS) s->n_teams = KS_MAX_TEAMS;
+  s->grid = s->n_teams * s->team_blocks;
+  if (cudaHostAlloc(reinterpret_cast<void**>(&s->host_h), sizeof(KServerHost),
+                    cudaHostAllocMapped) != cudaSuccess)
+    return bad(KP_ERR_CUDA);
+  std::memset(s->host_h, 0, sizeof(KServerHost));
+  if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->host_d), s->host_h, 0) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_kernel, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMemsetAsync(s->dev, 0, sizeof(KServerDev), s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return bad(KP_ERR_CUDA);
+  *out = s;
+  return KP_OK;
+}
+
+kp_status kp_server_submit(kp_server* s, const kp_system* sys, const kp_workspace* ws,
+                           const kp_obstacles* obs, const kp_params* prm, const float* x_init,
+                           const kp_goal* goal, const kp_budget* budget, int64_t* id) {
+  if (!s || !sys || !ws || !prm || !x_init || !goal || !budget || !id) return KP_ERR_ARG;
+  if (s->poisoned) return KP_ERR_STATE;
+  const int nb = obs ? obs->n_boxes : 0;
+  Dims d{};
+  if (check_inputs(sys, ws, nb, prm, &d)) return KP_ERR_ARG;
+  if (nb > 0 && (!obs->boxes || check_boxes(obs->boxes, nb))) return KP_ERR_ARG;
+  if (budget->max_iters < 1 || !(goal->radius >= 0.0f)) return KP_ERR_ARG;
+  for (int i = 0; i < d.D; ++i)
+    if (std::isnan(x_init[i])) return KP_ERR_ARG;
+  PendingQuery q;
+  q.id = s->next_id++;
+  q.sys = *sys;
+  q.ws = *ws;
+  q.prm = *prm;
+  if (nb > 0) q.boxes.assign(obs->boxes, obs->boxes + (size_t)nb * 6);
+  q.root = RootState{};
+  for (int i = 0; i < d.D; ++i) q.root.x[i] = x_init[i];
+  q.goal = *goal;
+  q.budget = *budget;
+  q.t_submit = now_ms();
+  *id = q.id;
+  s->submitted += 1;
+  s->pending.push_back(std::move(q));
+  admit_pending(s);
+  return ensure_running(s);
+}
+
+kp_status kp_server_poll(kp_server* s, kp_server_done* out, int32_t capacity, int32_t* n_out) {
+  if (!s || !n_out || capacity < 0 || (capacity > 0 && !out)) return KP_ERR_ARG;
+  *n_out = 0;
+  if (s->poisoned) return KP_ERR_STATE;
+  kp_status st = collect(s);
+  if (st != KP_OK) return st;
+  admit_pending(s);
+  st = ensure_running(s);
+  if (st != KP_OK) return st;
+  int n = 0;
+  while (n < capacity && !s->ready.empty()) {
+    out[n++] = s->ready.front();
+    s->ready.pop_front();
+  }
+  *n_out = n;
+  return KP_OK;
+}
+
+kp_status kp_server_result(kp_server* s, int64_t id, kp_traj* traj) {
+  if (!s || !traj) return KP_ERR_ARG;
+  auto it = s->results.find(id);
+  if (it == s->results.end()) return KP_ERR_ARG;
+  const StoredResult& r = it->second;
+  traj->n_edges = r.n_edges;
+  if (r.status != KP_OK) {
+    const kp_status st = r.status;
+    s->results.erase(it);
+    return st;
+  }
+  if (r.n_edges > traj->capacity) return KP_ERR_ARG;
+  for (int e = 0; e < r.n_edges; ++e) {
+    std::memcpy(traj->states + (size_t)e * 12, r.rows.data() + (size_t)e * 17, 12 * 4);
+    std::memcpy(traj->ctrls + (size_t)e * 4, r.rows.data() + (size_t)e * 17 + 12, 4 * 4);
+    traj->steps[e] = (int32_t)r.rows[(size_t)e * 17 + 16];
+  }
+  s->results.erase(it);
+  return KP_OK;
+}
+
+kp_status kp_server_stats_get(kp_server* s, kp_server_stats* out) {
+  if (!s || !out) return KP_ERR_ARG;
+  out->teams = s->n_teams;
+  out->team_blocks = s->team_blocks;
+  out->pending = (int32_t)s->pending.size();
+  int res = 0;
+  for (const auto& ss : s->slots) res += ss.used ? 1 : 0;
+  out->resident = res;
+  out->submitted = s->submitted;
+  out->completed = s->completed;
+  size_t f = 0;
+  for (const auto& kv : s->free_list) f += kv.second;
+  out->pool_free = f;
+  out->device_error = reinterpret_cast<volatile int32_t*>(&s->host_h->error)[0];
+  out->running = s->launched && cudaEventQuery(s->ev_kernel) == cudaErrorNotReady ? 1 : 0;
+  cudaGetLastError();
+  return KP_OK;
+}
+
+void kp_server_destroy(kp_server* s) {
+  if (!s) return;
+  if (s->host_h) {
+    reinterpret_cast<volatile uint32_t*>(&s->host_h->stop)[0] = 1u;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+  }
+  cudaStreamSynchronize(s->stream);
+  if (s->copy) {
+    cudaStreamSynchronize(s->copy);
+    cudaStreamDestroy(s->copy);
+  }
+  if (s->ev_kernel) cudaEventDestroy(s->ev_kernel);
+  if (s->host_h) cudaFreeHost(s->host_h);
+  delete s;
+}
+
+}  // extern "C"

@@ -188,4 +188,63 @@ struct KParams {
   int32_t hv_cap;
 };
 
+// ---------------------------------------------------------------------------
+// server: many queries in one persistent launch (teams of blocks)
+// ---------------------------------------------------------------------------
+
+constexpr int KS_MAX_TEAMS = 1024;
+constexpr int KS_RING = 4096;          // submission / completion ring entries
+constexpr uint32_t KS_EXIT = 0xffffffffu;
+constexpr int KS_SD_DOUBLES = 1024;    // score scratch of a server block
+constexpr int KS_BLOB_MAX = 49152;     // obstacle blob of a server query (bytes)
+
+// One admitted query, written by the host into its descriptor slot.
+struct KQuery {
+  KParams P;           // constants and the query's arena slices
+  RootState root;
+  int32_t max_iters;
+  int32_t id;
+  uint64_t max_ns;
+};
+
+// Completion record, written by the device into host-mapped memory.
+struct KDone {
+  int32_t slot, state, err, n_edges;
+  int32_t iterations, n_nodes, goal_node, pad;
+  unsigned long long samples, t_start_ns, t_end_ns;
+  uint32_t seq;        // written last: index + 1 of this record
+  uint32_t pad2[3];
+};
+
+// Host-mapped area: submissions (host writes) and completions (device
+// writes).
+struct KServerHost {
+  uint32_t posted;     // queries published so far
+  uint32_t stop;       // the host asks the teams to leave
+  int32_t error;       // device: first server error (code | site << 8), 0 if none
+  uint32_t pad[29];
+  uint32_t ring[KS_RING];  // descriptor slot of the i-th published query
+  KDone done[KS_RING];
+};
+
+// Device control area of a server.
+struct KServerDev {
+  KCtl sctl;           // server-level error word and barrier scratch
+  uint32_t taken;      // published queries claimed by teams
+  uint32_t done_seq;   // completion records published
+  uint32_t pad[30];
+  uint32_t team_slot[KS_MAX_TEAMS];
+  uint32_t team_bar[KS_MAX_TEAMS][64];  // [0] count, [32] generation
+};
+
+struct KServerArgs {
+  KServerDev* dev;
+  KServerHost* host;   // device alias of the host-mapped area
+  const KQuery* queries;
+  int32_t team_blocks;
+  int32_t pad;
+  uint64_t idle_ns;    // a team leaves after this long without work
+  uint64_t wait_ns;    // bound of every other device wait
+};
+
 }  // namespace kp

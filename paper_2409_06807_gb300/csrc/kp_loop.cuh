@@ -89,6 +89,9 @@ __device__ __forceinline__ bool stage_boxes(const KParams& P, float4* sbox, Loop
         if (done || global_ns() - t1 > P.wait_ns) break;
       }
     }
+    // invalidate the object so that a later staging (the server stages one
+    // blob per query) initialises a fresh mbarrier
+    if (ok) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
     sh.flag = ok;
   }
   __syncthreads();
@@ -854,16 +857,13 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParam
   run_loop<SYS, LOG>(P, T, smem, sh, max_iters, max_ns);
 }
 
-// Algorithm 1, lines 1-3 on the device (after the host cleared the tables):
-// block 0 thread 0 checks and bins x_init and writes the root; every thread
-// sets P_accept = 1 (threshold 2^32) for its regions.
+// Root of a query (thread 0): x_init checked (state box, no obstacle box
+// contains it) and binned; tree, decomposition and control block set to
+// Algorithm 1, lines 1-3.  Thresholds and cleared tables are the caller's.
 template <int SYS>
-__global__ void kp_reset_kernel(KParams P, RootState root) {
+__device__ void init_root(const KParams& P, const RootState& root) {
   using Sys = System<SYS>;
   constexpr int D = Sys::D;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.R; r += gridDim.x * blockDim.x)
-    P.thr[r] = 1ull << 32;
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
   KCtl* ctl = P.ctl;
   float x[D];
   for (int i = 0; i < D; ++i) x[i] = root.x[i];
@@ -875,7 +875,6 @@ __global__ void kp_reset_kernel(KParams P, RootState root) {
   ctl->it_valid = 0;
   ctl->err = 0;
   ctl->err_where = 0;
-  ctl->bar_count = 0;
   ctl->iteration = 0;
   ctl->n_edges = 0;
   ctl->tot_samples = 0;
@@ -909,6 +908,18 @@ __global__ void kp_reset_kernel(KParams P, RootState root) {
   const bool in_goal = dx * dx + dy * dy + dz * dz <= P.goal_r2;
   ctl->goal_node = in_goal ? 0 : KP_NO_GOAL;
   ctl->state = in_goal ? KP_DEV_SOLVED : KP_DEV_RUNNING;
+}
+
+// Algorithm 1, lines 1-3 on the device (after the host cleared the tables):
+// every thread sets P_accept = 1 (threshold 2^32) for its regions, block 0
+// thread 0 writes the root.
+template <int SYS>
+__global__ void kp_reset_kernel(KParams P, RootState root) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.R; r += gridDim.x * blockDim.x)
+    P.thr[r] = 1ull << 32;
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  P.ctl->bar_count = 0;
+  init_root<SYS>(P, root);
 }
 
 }  // namespace kp

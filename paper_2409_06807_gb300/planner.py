@@ -134,6 +134,15 @@ SIGNATURES = {
     "kp_mlp_destroy": (None, [_vp]),
     "kp_attach_mlp": (C.c_int, [_vp, _vp, C.c_float]),
     "kp_set_harvest": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp]),
+    "kp_server_required_bytes": (C.c_size_t, [C.c_int32]),
+    "kp_server_create": (C.c_int, [C.c_void_p, _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
+    "kp_server_submit": (C.c_int, [_vp, C.POINTER(System), C.POINTER(Workspace),
+                                   C.POINTER(Obstacles), C.POINTER(Params), C.POINTER(C.c_float),
+                                   C.POINTER(Goal), C.POINTER(Budget), C.POINTER(C.c_int64)]),
+    "kp_server_poll": (C.c_int, [_vp, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "kp_server_result": (C.c_int, [_vp, C.c_int64, C.POINTER(Traj)]),
+    "kp_server_stats_get": (C.c_int, [_vp, C.c_void_p]),
+    "kp_server_destroy": (None, [_vp]),
     "kp_last_error": (C.c_char_p, [_vp]),
     "kp_destroy": (None, [_vp]),
 }

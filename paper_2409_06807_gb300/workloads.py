@@ -268,4 +268,36 @@ def tiny(system: int = DI, seed: int = 0, n_boxes: int = 2, **kw) -> Workload:
     return w.with_(**kw) if kw else w
 
 
+def serving_mix(n: int = 512, rate_hz: float = 2000.0, seed: int = 0, t_e_range=(16384, 1 << 20),
+                box_range=(10, 1000)):
+    """Arrival process of mixed queries: Poisson arrivals at rate_hz; system
+    uniform over the three; obstacle count and node cap log-uniform in the
+    given ranges; each layout from its system's generator (random boxes,
+    forest or building walls, with the count drawn).  Returns a list of
+    (arrival time in s, Workload)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n))
+    out = []
+    for i in range(n):
+        system = int(rng.integers(0, 3))
+        nb = int(round(np.exp(rng.uniform(np.log(box_range[0]), np.log(box_range[1])))))
+        t_e = int(round(np.exp(rng.uniform(np.log(t_e_range[0]), np.log(t_e_range[1])))))
+        s = int(rng.integers(0, 2 ** 31))
+        if system == DI:
+            w = c1(s).with_(t_e=t_e)
+            w = w.with_(boxes=random_boxes(s, nb, keep_clear=[(tuple(w.x_init[:3]), 0.0),
+                                                              (tuple(w.goal_c), float(w.goal_r))]))
+        elif system == DUBINS:
+            w = c2(s).with_(t_e=t_e)
+            w = w.with_(boxes=forest_boxes(s, nb, keep_clear=[(tuple(w.x_init[:3]), 0.03),
+                                                              (tuple(w.goal_c), float(w.goal_r))]))
+        else:
+            w = c3(s).with_(t_e=t_e)
+            per_wall = max(1, nb // 3)
+            walls = building_boxes(s)
+            w = w.with_(boxes=np.concatenate([walls[k * 400:k * 400 + per_wall] for k in range(3)]))
+        out.append((float(t[i]), w.with_(name=f"{w.name}_q{i}")))
+    return out
+
+
 BY_NAME = {"c1": c1, "c2": c2, "c3": c3}
