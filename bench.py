@@ -147,14 +147,19 @@ class ClockSampler:
 
 
 def dist_setup(n_gpus):
+    """Rank, world and local rank from the launcher's environment; joins the
+    process group (NCCL when a GPU is visible, gloo otherwise)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
     return world, rank, local
 
 
@@ -164,24 +169,36 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _reduce(x, world, op):
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    import torch.distributed as dist
+    return _reduce(x, world, dist.ReduceOp.MAX)
 
 
 def sum_over_ranks(x, world):
-    if world <= 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.SUM)
+
+
+def rank_seeds(rank, n):
+    """Layout seeds of one rank's warm-up and timed steps: every rank plans
+    its own independent queries (replicas, no data-path exchange)."""
+    return [rank * 100_000 + i for i in range(n)]
+
+
+def whole_job_rate(units, ms, world):
+    """Units of all ranks over the slowest rank's time (units per second)."""
+    return sum_over_ranks(float(units), world) / (max_over_ranks(float(ms), world) / 1e3)
 
 
 def workload_config(w):
@@ -248,10 +265,11 @@ def run_reference(args, world, rank):
     w = make(0)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(w),
+        "config": {**workload_config(w), "l2": "n/a (host cores)",
+                   "parallelism": "rank 0 only, one host thread"},
         "cpu_baseline": {"value": v, "unit": "samples/s", "cores": 1, "kind": "oracle",
                          "sample": "each step: first 3 loop passes of one seeded layout"},
         "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0,
@@ -273,7 +291,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     make = W.BY_NAME[args.workload]
     n_total = args.warmup + args.steps
-    seeds = [rank * 100_000 + i for i in range(n_total)]
+    seeds = rank_seeds(rank, n_total)
     layouts = [make(s) for s in seeds]
     w0 = layouts[0]
     pl = P.Planner(w0, device=f"cuda:{local}")
