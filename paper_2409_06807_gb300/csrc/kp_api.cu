@@ -471,7 +471,7 @@ kp_status configure_launch(kp_ctx* ctx) {
   const int sd = min_ch > 1024 ? min_ch : 1024;
   ctx->P.sd_bytes = sd * 8;
   ctx->smem = (size_t)ctx->P.blob_bytes + (size_t)sd * 8 +
-              (ctx->P.features_on ? (size_t)MLP_TILE_SMEM : 0);
+              (ctx->P.features_on ? (size_t)MLP_LOOP_TILE_SMEM : 0);
   for (int log = 0; log < 2; ++log) {
     int bps = 0;
     KP_CUDA(occupancy(d.sys, log != 0, ctx->smem, &bps));

@@ -36,6 +36,7 @@ struct LoopShared {
   unsigned long long red[64];
   uint64_t mbar;
   int flag;
+  int32_t phase_ns[12];  // per-pass phase timers (block 0, thread 0)
 };
 
 // Stage the obstacle blob (boxes and broad-phase grid) into shared memory
@@ -202,54 +203,72 @@ __device__ __forceinline__ int write_ve(const KParams& P, const Team& T, int n, 
 // learned proposal: node features and the network (6D systems)
 // ---------------------------------------------------------------------------
 
-// The 32 features of node v (the last 12 zero) under the current region
-// tables: bounded state entries mapped to [-1, 1], an unbounded one wrapped
-// to [-pi, pi) and divided by pi; goal minus position; Cov / n'; FreeVol /
-// vol; log(1 + n_valid); log(1 + n_invalid); P_accept of the node's region
-// and of its six face neighbours in the position grid (0 outside).
-__device__ __forceinline__ void node_features(const KParams& P, int v, float* f) {
-#pragma unroll
-  for (int i = 0; i < 32; ++i) f[i] = 0.0f;
-  float x[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) x[i] = P.st[(size_t)i * P.t_e + v];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    if (P.feat_scale[i] > 0.0f) {
-      f[i] = (x[i] - P.x_lo[i]) * P.feat_scale[i] - 1.0f;
-    } else {
-      const float y = x[i] - 6.28318530717958648f * floorf((x[i] + 3.14159265358979324f) *
-                                                           0.159154943091895336f);
-      f[i] = y * 0.318309886183790672f;
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) f[6 + a] = P.goal_c[a] - x[a];
-  const int r = P.region[v];
-  const float nv = (float)P.n_valid[r], ni = (float)P.n_invalid[r], dl = (float)P.delta;
-  f[9] = (float)P.cov[r] / (float)P.n_sub_per;
-  f[10] = (dl + nv) / (dl + nv + ni);
-  f[11] = log1pf(nv);
-  f[12] = log1pf(ni);
-  const float inv32 = 2.3283064365386963e-10f;
-  f[13] = (float)P.thr[r] * inv32;
+// Features 2q and 2q+1 (q = 0..15) of node v under the current region
+// tables; the 32 features are: bounded state entries mapped to [-1, 1], an
+// unbounded one wrapped to [-pi, pi) and divided by pi; goal minus
+// position; Cov / n'; FreeVol / vol; log(1 + n_valid); log(1 + n_invalid);
+// P_accept of the node's region and of its six face neighbours in the
+// position grid (0 outside); zeros from feature 20 on.
+__device__ __forceinline__ float state_feature(const KParams& P, int i, float x) {
+  if (P.feat_scale[i] > 0.0f) return (x - P.x_lo[i]) * P.feat_scale[i] - 1.0f;
+  const float y = x - 6.28318530717958648f * floorf((x + 3.14159265358979324f) *
+                                                    0.159154943091895336f);
+  return y * 0.318309886183790672f;
+}
+
+__device__ __forceinline__ float neighbour_accept(const KParams& P, int r, int k) {
   const int gx = P.grid[0], gy = P.grid[1], gz = P.grid[2];
   const int cx = r % gx, cy = (r / gx) % gy, cz = (r / (gx * gy)) % gz, sb = r / (gx * gy * gz);
-  const int dx[6] = {-1, 1, 0, 0, 0, 0}, dy[6] = {0, 0, -1, 1, 0, 0}, dz[6] = {0, 0, 0, 0, -1, 1};
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const int nx = cx + dx[k], ny = cy + dy[k], nz = cz + dz[k];
-    if (nx < 0 || nx >= gx || ny < 0 || ny >= gy || nz < 0 || nz >= gz) continue;
-    f[14 + k] = (float)P.thr[nx + gx * (ny + gy * (nz + gz * sb))] * inv32;
+  const int nx = cx + (k == 0 ? -1 : k == 1 ? 1 : 0);
+  const int ny = cy + (k == 2 ? -1 : k == 3 ? 1 : 0);
+  const int nz = cz + (k == 4 ? -1 : k == 5 ? 1 : 0);
+  if (nx < 0 || nx >= gx || ny < 0 || ny >= gy || nz < 0 || nz >= gz) return 0.0f;
+  return (float)P.thr[nx + gx * (ny + gy * (nz + gz * sb))] * 2.3283064365386963e-10f;
+}
+
+__device__ __forceinline__ void node_feature_pair(const KParams& P, int v, int q, float* f2) {
+  f2[0] = f2[1] = 0.0f;
+  if (q < 3) {
+    f2[0] = state_feature(P, 2 * q, P.st[(size_t)(2 * q) * P.t_e + v]);
+    f2[1] = state_feature(P, 2 * q + 1, P.st[(size_t)(2 * q + 1) * P.t_e + v]);
+    return;
+  }
+  if (q == 3) {
+    f2[0] = P.goal_c[0] - P.st[v];
+    f2[1] = P.goal_c[1] - P.st[(size_t)P.t_e + v];
+    return;
+  }
+  if (q >= 10) return;
+  const int r = P.region[v];
+  const float nv = (float)P.n_valid[r], ni = (float)P.n_invalid[r], dl = (float)P.delta;
+  switch (q) {
+    case 4:
+      f2[0] = P.goal_c[2] - P.st[(size_t)2 * P.t_e + v];
+      f2[1] = (float)P.cov[r] / (float)P.n_sub_per;
+      break;
+    case 5:
+      f2[0] = (dl + nv) / (dl + nv + ni);
+      f2[1] = log1pf(nv);
+      break;
+    case 6:
+      f2[0] = log1pf(ni);
+      f2[1] = (float)P.thr[r] * 2.3283064365386963e-10f;
+      break;
+    default:  // q = 7, 8, 9: neighbours 2(q-7) and 2(q-7)+1
+      f2[0] = neighbour_accept(P, r, 2 * (q - 7));
+      f2[1] = neighbour_accept(P, r, 2 * (q - 7) + 1);
   }
 }
 
 // Phase F: features of every V_E position (kept for the harvest) and, with
-// a network attached, its outputs, in tiles of 32 positions per block.
-__device__ __forceinline__ void phase_features(const KParams& P, const Team& T, int n_ve,
-                                               unsigned char* mtile) {
+// a network attached, its outputs, in tiles of 32 positions per block; 16
+// threads share the features of one position.  Not inlined: it runs once
+// per pass, and as a call it gets the register budget of the loop kernel
+// to itself instead of sharing it with the loop state live around it.
+static __device__ __noinline__ void phase_features(const KParams& P, const Team& T, int n_ve,
+                                                   unsigned char* mtile) {
   __nv_bfloat16* sX = reinterpret_cast<__nv_bfloat16*>(mtile);
-  __nv_bfloat16* sH = sX + MLP_TILE * MLP_XS;
+  __nv_bfloat16* sH = sX + MLP_LOOP_TILE * MLP_XS;
   MlpWeights w;
   w.W1 = reinterpret_cast<const __nv_bfloat16*>(P.mlp_W1);
   w.b1 = P.mlp_b1;
@@ -257,28 +276,23 @@ __device__ __forceinline__ void phase_features(const KParams& P, const Team& T, 
   w.b2 = P.mlp_b2;
   w.W3 = reinterpret_cast<const __nv_bfloat16*>(P.mlp_W3);
   w.b3 = P.mlp_b3;
-  const int n_tiles = (n_ve + MLP_TILE - 1) / MLP_TILE;
+  const int n_tiles = (n_ve + MLP_LOOP_TILE - 1) / MLP_LOOP_TILE;
+  const int q = threadIdx.x & 15;  // 16 rows x 16 feature pairs per round
   for (int tile = T.b; tile < n_tiles; tile += T.nb) {
-    const int p0 = tile * MLP_TILE;
-    const int rows = n_ve - p0 < MLP_TILE ? n_ve - p0 : MLP_TILE;
-    if (threadIdx.x < MLP_TILE) {
-      float f[32];
-      if ((int)threadIdx.x < rows) {
-        node_features(P, P.ve[p0 + threadIdx.x], f);
-      } else {
+    const int p0 = tile * MLP_LOOP_TILE;
+    const int rows = n_ve - p0 < MLP_LOOP_TILE ? n_ve - p0 : MLP_LOOP_TILE;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) f[i] = 0.0f;
-      }
-#pragma unroll
-      for (int c = 0; c < 32; c += 2) {
-        const uint32_t v2 = pack_bf16(f[c], f[c + 1]);
-        *reinterpret_cast<uint32_t*>(sX + threadIdx.x * MLP_XS + c) = v2;
-        if ((int)threadIdx.x < rows)
-          *reinterpret_cast<uint32_t*>(P.feat + (size_t)(p0 + threadIdx.x) * 32 + c) = v2;
-      }
+    for (int rr = 0; rr < MLP_LOOP_TILE; rr += 16) {
+      const int row = rr + (threadIdx.x >> 4);
+      float f2[2] = {0.0f, 0.0f};
+      if (row < rows) node_feature_pair(P, P.ve[p0 + row], q, f2);
+      const uint32_t v2 = pack_bf16(f2[0], f2[1]);
+      *reinterpret_cast<uint32_t*>(sX + row * MLP_XS + 2 * q) = v2;
+      if (row < rows) *reinterpret_cast<uint32_t*>(P.feat + (size_t)(p0 + row) * 32 + 2 * q) = v2;
     }
     __syncthreads();
-    if (P.mix_thr) mlp_tile_forward(w, sX, sH, P.net_raw, p0, rows, nullptr, nullptr);
+    if (P.mix_thr)
+      mlp_tile_forward<MLP_LOOP_TILE / 16, true>(w, sX, sH, P.net_raw, p0, rows, nullptr, nullptr);
     __syncthreads();
   }
 }
@@ -750,7 +764,7 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
   // block 0 stamps the device clock between phases and barriers
   const bool timer = T.b == 0 && threadIdx.x == 0;
   uint64_t t_mark = timer ? global_ns() : 0;
-  int32_t phase_ns[12];
+  int32_t* phase_ns = sh.phase_ns;
   int32_t prev_wait = 0;
   auto stamp = [&](int ph) {
     if (timer) {
@@ -763,12 +777,11 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
   for (;;) {
     if (P.features_on) {
       phase_features(P, T, n_ve, mtile);
+      stamp(3);
       if (!team_sync(T, ctl, P.wait_ns, 19)) return false;
-    }
-    if (timer) {  // network time goes to slot 3
-      const uint64_t now = global_ns();
-      phase_ns[3] = (int32_t)(now - t_mark);
-      t_mark = now;
+      stamp(6);
+    } else if (timer) {
+      phase_ns[3] = phase_ns[6] = 0;
     }
     const int S = n_ve > 0 ? n_ve * lam : 0;
     phase_expand<SYS, LOG>(P, T, smem, it, lam, S, sh);
@@ -782,7 +795,6 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     int n_acc;
     phase_append<SYS, LOG>(P, T, S, lam, n_tree, nch, acc_off, &n_acc);
     stamp(5);
-    if (timer) phase_ns[6] = 0;
     if (!team_sync(T, ctl, P.wait_ns, 22)) return false;
     stamp(7);
     const int t_old = n_tree;

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) kp_mlp_forward_kernel(MlpWeights w, const
     if (xb && r < rows) xb[(size_t)(row0 + r) * MLP_IN + c] = v;
   }
   __syncthreads();
-  mlp_tile_forward(w, sX, sH, raw, row0, rows, h1, h2);
+  mlp_tile_forward<MLP_TILE / 16>(w, sX, sH, raw, row0, rows, h1, h2);
   if (heads && threadIdx.x < rows) {
     const int r = row0 + threadIdx.x;
     float mean[MLP_NQ], ls[MLP_NQ];
@@ -186,9 +186,27 @@ __global__ void __launch_bounds__(128) kp_mlp_gemm_kernel(const bf16* A, int lda
 }
 
 // Adam on the FP32 master vector; refreshes the BF16 weight copies.
+// Parameter i rounded to BF16 into the row-major weight copy (training
+// kernels) and into the fragment-order copy (the planner's loop kernel).
+__device__ __forceinline__ void store_weight(int i, float pi, bf16* wb, bf16* wf) {
+  const bf16 b = __float2bfloat16_rn(pi);
+  if (i < OFF_B1) {
+    wb[i] = b;
+    wf[frag_index_hidden(i / MLP_IN, i % MLP_IN, MLP_IN)] = b;
+  } else if (i >= OFF_W2 && i < OFF_B2) {
+    const int j = i - OFF_W2;
+    wb[MLP_H * MLP_IN + j] = b;
+    wf[MLP_H * MLP_IN + frag_index_hidden(j / MLP_H, j % MLP_H, MLP_H)] = b;
+  } else if (i >= OFF_W3 && i < OFF_B3) {
+    const int j = i - OFF_W3;
+    wb[MLP_H * MLP_IN + MLP_H * MLP_H + j] = b;
+    wf[MLP_H * MLP_IN + MLP_H * MLP_H + frag_index_out(j / MLP_H, j % MLP_H)] = b;
+  }
+}
+
 __global__ void kp_mlp_adam_kernel(float* p, const float* g, float* m, float* v, int n, float lr,
                                    float beta1, float beta2, float eps, float c1, float c2,
-                                   bf16* wb) {
+                                   bf16* wb, bf16* wf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float gi = g[i];
@@ -198,21 +216,13 @@ __global__ void kp_mlp_adam_kernel(float* p, const float* g, float* m, float* v,
   v[i] = vi;
   const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
   p[i] = pi;
-  int wi = -1;  // position in the BF16 weight copy
-  if (i < OFF_B1) wi = i;
-  else if (i >= OFF_W2 && i < OFF_B2) wi = MLP_H * MLP_IN + (i - OFF_W2);
-  else if (i >= OFF_W3 && i < OFF_B3) wi = MLP_H * MLP_IN + MLP_H * MLP_H + (i - OFF_W3);
-  if (wi >= 0) wb[wi] = __float2bfloat16_rn(pi);
+  store_weight(i, pi, wb, wf);
 }
 
-__global__ void kp_mlp_round_kernel(const float* p, bf16* wb) {
+__global__ void kp_mlp_round_kernel(const float* p, bf16* wb, bf16* wf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N_PARAMS) return;
-  int wi = -1;
-  if (i < OFF_B1) wi = i;
-  else if (i >= OFF_W2 && i < OFF_B2) wi = MLP_H * MLP_IN + (i - OFF_W2);
-  else if (i >= OFF_W3 && i < OFF_B3) wi = MLP_H * MLP_IN + MLP_H * MLP_H + (i - OFF_W3);
-  if (wi >= 0) wb[wi] = __float2bfloat16_rn(p[i]);
+  store_weight(i, p[i], wb, wf);
 }
 
 }  // namespace kp
@@ -230,7 +240,8 @@ struct kp_mlp {
   int max_batch;
   int step;
   float *p, *m, *v, *g;
-  bf16* wb;  // W1 | W2 | W3 in BF16
+  bf16* wb;  // W1 | W2 | W3 in BF16, row-major
+  bf16* wf;  // the same in fragment order (planner loop)
   float *raw, *d_raw, *loss;
   bf16 *xb, *h1, *h2, *d_raw_b, *dh2, *dh1;
 };
@@ -238,7 +249,7 @@ struct kp_mlp {
 namespace {
 
 struct MlpLayout {
-  size_t p, m, v, g, wb, loss, raw, d_raw, xb, h1, h2, d_raw_b, dh2, dh1, total;
+  size_t p, m, v, g, wb, wf, loss, raw, d_raw, xb, h1, h2, d_raw_b, dh2, dh1, total;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -256,6 +267,7 @@ MlpLayout mlp_layout(int B) {
   L.v = take((size_t)N_PARAMS * 4);
   L.g = take((size_t)N_PARAMS * 4);
   L.wb = take((size_t)N_WEIGHTS_BF16 * 2);
+  L.wf = take((size_t)N_WEIGHTS_BF16 * 2);
   L.loss = take(16);
   L.raw = take((size_t)B * MLP_OUT * 4);
   L.d_raw = take((size_t)B * MLP_OUT * 4);
@@ -366,6 +378,7 @@ kp_status kp_mlp_create(void* dev_arena, size_t arena_bytes, int32_t max_batch,
   n->v = reinterpret_cast<float*>(A + L.v);
   n->g = reinterpret_cast<float*>(A + L.g);
   n->wb = reinterpret_cast<bf16*>(A + L.wb);
+  n->wf = reinterpret_cast<bf16*>(A + L.wf);
   n->loss = reinterpret_cast<float*>(A + L.loss);
   n->raw = reinterpret_cast<float*>(A + L.raw);
   n->d_raw = reinterpret_cast<float*>(A + L.d_raw);
@@ -392,7 +405,7 @@ kp_status kp_mlp_set_params(kp_mlp* n, const float* host_params) {
                            n->stream));
   MLP_CUDA(cudaMemsetAsync(n->m, 0, (size_t)N_PARAMS * 4, n->stream));
   MLP_CUDA(cudaMemsetAsync(n->v, 0, (size_t)N_PARAMS * 4, n->stream));
-  kp_mlp_round_kernel<<<(N_PARAMS + 255) / 256, 256, 0, n->stream>>>(n->p, n->wb);
+  kp_mlp_round_kernel<<<(N_PARAMS + 255) / 256, 256, 0, n->stream>>>(n->p, n->wb, n->wf);
   MLP_CUDA(cudaGetLastError());
   MLP_CUDA(cudaStreamSynchronize(n->stream));
   n->step = 0;
@@ -442,7 +455,7 @@ kp_status kp_mlp_train_step(kp_mlp* n, const float* dev_x, const float* dev_t, i
   const float c1 = 1.0f - powf(b1, (float)n->step), c2 = 1.0f - powf(b2, (float)n->step);
   kp_mlp_adam_kernel<<<(N_PARAMS + 255) / 256, 256, 0, n->stream>>>(n->p, n->g, n->m, n->v,
                                                                     N_PARAMS, lr, b1, b2, 1e-8f,
-                                                                    c1, c2, n->wb);
+                                                                    c1, c2, n->wb, n->wf);
   MLP_CUDA(cudaGetLastError());
   if (host_loss) {
     MLP_CUDA(cudaMemcpyAsync(host_loss, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
@@ -456,10 +469,15 @@ void kp_mlp_destroy(kp_mlp* n) { delete n; }
 }  // extern "C"
 
 namespace kp {
-// Device pointers of the network's weights, for the planner's loop kernel.
+// Device pointers of the network's weights for the planner's loop kernel:
+// BF16 weights in fragment order (frag_index_hidden / frag_index_out), FP32
+// biases.
 void mlp_device_weights(const kp_mlp* n, const void** W1, const float** b1, const void** W2,
                         const float** b2, const void** W3, const float** b3) {
-  const MlpWeights w = weights_of(n);
+  MlpWeights w = weights_of(n);
+  w.W1 = n->wf;
+  w.W2 = n->wf + MLP_H * MLP_IN;
+  w.W3 = n->wf + MLP_H * MLP_IN + MLP_H * MLP_H;
   *W1 = w.W1;
   *b1 = w.b1;
   *W2 = w.W2;

@@ -14,12 +14,13 @@
 namespace kp {
 
 constexpr int MLP_IN = 32, MLP_H = 256, MLP_OUT = 8, MLP_NQ = 4;
-constexpr int MLP_TILE = 32;           // rows per block tile
+constexpr int MLP_TILE = 32;           // rows per block tile (standalone kernels)
+constexpr int MLP_LOOP_TILE = 32;      // rows per block tile inside the planner loop
 constexpr int MLP_XS = MLP_IN + 8;     // padded smem row (bf16) of the input tile
 constexpr int MLP_HS = MLP_H + 8;      // padded smem row (bf16) of a hidden tile
 constexpr float MLP_LOGSTD_MIN = -4.0f, MLP_LOGSTD_MAX = 1.0f;
-// shared memory of one tile: input rows + hidden rows (bf16)
-constexpr int MLP_TILE_SMEM = MLP_TILE * MLP_XS * 2 + MLP_TILE * MLP_HS * 2;
+// shared memory of one loop tile: input rows + hidden rows (bf16)
+constexpr int MLP_LOOP_TILE_SMEM = MLP_LOOP_TILE * MLP_XS * 2 + MLP_LOOP_TILE * MLP_HS * 2;
 
 struct MlpWeights {
   const __nv_bfloat16* W1;  // [256][32]
@@ -69,18 +70,47 @@ __device__ __forceinline__ void frag_b(const __nv_bfloat16* W, int ld, int n0, i
   b[1] = ld_u32(W + (n0 + g) * ld + k0 + 2 * t + 8);
 }
 
-// One dense ReLU layer on a 32-row tile: out[32][256] = relu(in * W^T + b),
+// Fragment order of a hidden layer's weights W[n][k] (N = 256 outputs, K
+// inputs): for the warp owning columns 32w.. and k-step s, each lane keeps
+// its B fragments of the four 8-column blocks as eight consecutive 32-bit
+// words (block ni, register h), so that a lane fetches them with two 16-byte
+// loads.  Returns the bf16 index of W[n][k] in that order.
+__host__ __device__ __forceinline__ int frag_index_hidden(int n, int k, int K) {
+  const int w = n >> 5, ni = (n & 31) >> 3, g = n & 7;
+  const int s = k >> 4, kk = k & 15, h = kk >> 3, t = (kk & 7) >> 1, e = kk & 1;
+  return (((w * (K >> 4) + s) * 32 + g * 4 + t) * 16) + ni * 4 + h * 2 + e;
+}
+
+// Fragment order of the output layer W3[8][256]: warp w uses k-steps 2w and
+// 2w+1; a lane's four words for them are consecutive (one 16-byte load).
+__host__ __device__ __forceinline__ int frag_index_out(int n, int k) {
+  const int s = k >> 4, kk = k & 15, h = kk >> 3, t = (kk & 7) >> 1, e = kk & 1;
+  return (((s >> 1) * 32 + n * 4 + t) * 8) + (s & 1) * 4 + h * 2 + e;
+}
+
+// B fragments of the four 8-column blocks of this warp at k-step s, from a
+// hidden layer's weights in fragment order.
+__device__ __forceinline__ void frag_b4_ordered(const __nv_bfloat16* Wf, int K, int s,
+                                                uint32_t b[4][2]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint4* q = reinterpret_cast<const uint4*>(Wf) + (((warp * (K >> 4) + s) * 32 + lane) * 2);
+  const uint4 u0 = __ldg(q), u1 = __ldg(q + 1);
+  b[0][0] = u0.x; b[0][1] = u0.y; b[1][0] = u0.z; b[1][1] = u0.w;
+  b[2][0] = u1.x; b[2][1] = u1.y; b[3][0] = u1.z; b[3][1] = u1.w;
+}
+
+// One dense ReLU layer on a tile of 16*MI rows: out = relu(in * W^T + b),
 // every warp producing 32 output columns.  'in' is a bf16 smem tile (row
 // stride ld_in, K columns).  Results stay in registers (acc) until the
 // caller stores them.
-template <int K>
+template <int K, int MI, bool ORDERED = false>
 __device__ __forceinline__ void layer_relu(const __nv_bfloat16* in, int ld_in,
                                            const __nv_bfloat16* W, const float* bias,
-                                           float acc[2][4][4]) {
+                                           float acc[MI][4][4]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = lane & 3;
   const int n_base = warp * 32;
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+  for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
     for (int ni = 0; ni < 4; ++ni) {
       const float b0 = bias[n_base + ni * 8 + 2 * t], b1 = bias[n_base + ni * 8 + 2 * t + 1];
@@ -91,18 +121,22 @@ __device__ __forceinline__ void layer_relu(const __nv_bfloat16* in, int ld_in,
     }
 #pragma unroll 4
   for (int k0 = 0; k0 < K; k0 += 16) {
-    uint32_t a[2][4], b[4][2];
+    uint32_t a[MI][4], b[4][2];
+    if (ORDERED) {
+      frag_b4_ordered(W, K, k0 >> 4, b);
+    } else {
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi) frag_a(in, ld_in, mi * 16, k0, a[mi]);
+      for (int ni = 0; ni < 4; ++ni) frag_b(W, K, n_base + ni * 8, k0, b[ni]);
+    }
 #pragma unroll
-    for (int ni = 0; ni < 4; ++ni) frag_b(W, K, n_base + ni * 8, k0, b[ni]);
+    for (int mi = 0; mi < MI; ++mi) frag_a(in, ld_in, mi * 16, k0, a[mi]);
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
+    for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
       for (int ni = 0; ni < 4; ++ni) mma_bf16_16816(acc[mi][ni], a[mi], b[ni]);
   }
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+  for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
     for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
@@ -111,11 +145,12 @@ __device__ __forceinline__ void layer_relu(const __nv_bfloat16* in, int ld_in,
 
 // Writes a layer's register results as bf16 into a smem tile (and, when
 // given, into global rows row0.. of a [rows][256] bf16 array).
-__device__ __forceinline__ void store_hidden(const float acc[2][4][4], __nv_bfloat16* s,
+template <int MI>
+__device__ __forceinline__ void store_hidden(const float acc[MI][4][4], __nv_bfloat16* s,
                                              __nv_bfloat16* g, int row0, int rows_valid) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gi = lane >> 2, t = lane & 3;
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+  for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
     for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
@@ -128,42 +163,67 @@ __device__ __forceinline__ void store_hidden(const float acc[2][4][4], __nv_bflo
       }
 }
 
-// Forward pass of one 32-row tile.  sX holds the bf16 inputs (row stride
-// MLP_XS), sH is scratch (MLP_TILE x MLP_HS bf16).  Writes the 8 raw
+// Forward pass of one tile of 16*MI rows.  sX holds the bf16 inputs (row
+// stride MLP_XS), sH is scratch (16*MI x MLP_HS bf16).  Writes the 8 raw
 // outputs of valid rows to raw[(row0 + r) * 8 ..] and, when g_h1/g_h2 are
 // given, the hidden activations (training).  Every thread of the block
 // (256) must call it.
+//
+// The output layer (K = 256, 8 columns) is split over K: warp w multiplies
+// the 16-row blocks by k-steps 2w and 2w+1 and leaves its partial sums in
+// shared memory (over sH, once every warp has read h2); the partials are
+// then added in warp order.  Two dependent products per warp instead of
+// sixteen keep the tile's latency short.
+template <int MI, bool ORDERED = false>
 __device__ __forceinline__ void mlp_tile_forward(const MlpWeights& w, const __nv_bfloat16* sX,
                                                  __nv_bfloat16* sH, float* raw, int row0,
                                                  int rows_valid, __nv_bfloat16* g_h1,
                                                  __nv_bfloat16* g_h2) {
-  float acc[2][4][4];
-  layer_relu<MLP_IN>(sX, MLP_XS, w.W1, w.b1, acc);
-  store_hidden(acc, sH, g_h1, row0, rows_valid);
+  float acc[MI][4][4];
+  layer_relu<MLP_IN, MI, ORDERED>(sX, MLP_XS, w.W1, w.b1, acc);
+  store_hidden<MI>(acc, sH, g_h1, row0, rows_valid);
   __syncthreads();
-  layer_relu<MLP_H>(sH, MLP_HS, w.W2, w.b2, acc);
+  layer_relu<MLP_H, MI, ORDERED>(sH, MLP_HS, w.W2, w.b2, acc);
   __syncthreads();  // every warp has read h1
-  store_hidden(acc, sH, g_h2, row0, rows_valid);
+  store_hidden<MI>(acc, sH, g_h2, row0, rows_valid);
   __syncthreads();
-  // output layer: warps 0 and 1 each take 16 rows x 8 outputs, K = 256
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gi = lane >> 2, t = lane & 3;
-  if (warp < 2) {
-    float d[4] = {w.b3[2 * t], w.b3[2 * t + 1], w.b3[2 * t], w.b3[2 * t + 1]};
-#pragma unroll 4
-    for (int k0 = 0; k0 < MLP_H; k0 += 16) {
-      uint32_t a[4], b[2];
-      frag_a(sH, MLP_HS, warp * 16, k0, a);
-      frag_b(w.W3, MLP_H, 0, k0, b);
-      mma_bf16_16816(d, a, b);
+  float d[MI][4];
+  uint32_t b[2][2];
+  if (ORDERED) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(w.W3) + warp * 32 + lane);
+    b[0][0] = u.x; b[0][1] = u.y; b[1][0] = u.z; b[1][1] = u.w;
+  } else {
+    frag_b(w.W3, MLP_H, 0, warp * 32, b[0]);
+    frag_b(w.W3, MLP_H, 0, warp * 32 + 16, b[1]);
+  }
+#pragma unroll
+  for (int mi = 0; mi < MI; ++mi) {
+    d[mi][0] = d[mi][1] = d[mi][2] = d[mi][3] = 0.0f;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      uint32_t a[4];
+      frag_a(sH, MLP_HS, mi * 16, warp * 32 + ks * 16, a);
+      mma_bf16_16816(d[mi], a, b[ks]);
     }
+  }
+  __syncthreads();  // every warp has read h2: sH now holds the partials
+  float* part = reinterpret_cast<float*>(sH);  // [8 warps][16*MI rows][8]
+#pragma unroll
+  for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int r = warp * 16 + gi + 8 * h;
-      if (r < rows_valid) {
-        raw[(size_t)(row0 + r) * MLP_OUT + 2 * t] = d[2 * h];
-        raw[(size_t)(row0 + r) * MLP_OUT + 2 * t + 1] = d[2 * h + 1];
-      }
+      const int r = mi * 16 + gi + 8 * h;
+      part[(warp * 16 * MI + r) * MLP_OUT + 2 * t] = d[mi][2 * h];
+      part[(warp * 16 * MI + r) * MLP_OUT + 2 * t + 1] = d[mi][2 * h + 1];
     }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 16 * MI * MLP_OUT; e += blockDim.x) {
+    const int r = e / MLP_OUT, c = e % MLP_OUT;
+    float s = w.b3[c];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += part[(q * 16 * MI + r) * MLP_OUT + c];
+    if (r < rows_valid) raw[(size_t)(row0 + r) * MLP_OUT + c] = s;
   }
   __syncthreads();
 }
