@@ -282,6 +282,188 @@ def run_reference(args, world, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+MLP_FLOPS_FWD = 2 * (32 * 256 + 256 * 256 + 256 * 8)  # per row, one forward pass
+
+
+def timed_query(pl, w, flush, max_iters, cap=4096):
+    """One query through the single-query launch, L2 flushed first; returns
+    (status, device ms from the reset to the trajectory, info)."""
+    import torch
+    pl.set_obstacles(w.boxes)
+    pl.w = w
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(pl.stream)
+    pl.plan_async(max_iters=max_iters, capacity=cap)
+    e1.record(pl.stream)
+    st, _ = pl.plan_result()
+    return st, e0.elapsed_time(e1), pl.info()
+
+
+def mode_summary(rows, ok_status):
+    ms = np.array([r[1] for r in rows])
+    samples = sum(r[2]["n_samples"] for r in rows)
+    steps = sum(r[2]["n_steps"] for r in rows)
+    return {"success": sum(r[0] == ok_status for r in rows) / len(rows),
+            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "mean_ms": float(ms.mean()), "samples_per_s": samples / (ms.sum() / 1e3),
+            "mean_samples": samples / len(rows), "steps_per_sample": steps / max(1, samples)}
+
+
+def steady_state_leg(local, peak_ops, n_frontier=65536, reps=20):
+    """One expand iteration over a fixed frontier: a Dubins-forest tree
+    grown by the plain loop (goal moved out of reach) to n_frontier nodes,
+    every node put in V_E, t_e large enough that lambda = lambda_max; the
+    same tree is imported before each repetition and one pass is timed
+    (the loop launch, CUDA events).  Isolates the per-sample throughput of
+    the expand / accept / append / node-set pass from small-frontier
+    latency."""
+    from paper_2409_06807_gb300 import planner as P
+    w = W.c2(0).with_(t_e=1 << 23)
+    pl = P.Planner(w, device=f"cuda:{local}")
+    far = P.goal_struct(w.with_(goal_c=np.array([5.0, 5.0, 5.0], np.float32)))
+    pl.reset(goal=far)
+    while pl.info()["n_nodes"] < n_frontier:
+        pl.expand_step(1)
+    tree = pl.export_tree()
+    n = n_frontier
+    keep = {k: (v[:n] if k in ("state", "parent", "ctrl", "steps", "region", "sub", "in_ve")
+                else v) for k, v in tree.items()}
+    keep["n_nodes"] = n
+    keep["in_ve"] = np.ones(n, np.uint8)
+    vis = np.zeros_like(tree["visited"])
+    vis[keep["sub"]] = 1
+    keep["visited"] = vis
+    ms, rows = [], []
+    for i in range(reps + 3):
+        pl.import_tree(keep)
+        st = pl.expand_step(1)
+        if i >= 3:
+            ms.append(pl.last_launch_ms())
+            rows.append((pl.info(), st[0]))
+    pl.close()
+    inf, s0 = rows[0]
+    med = float(np.median(ms))
+    ops = alg_ops(w.system, inf["n_samples"], inf["n_steps"], inf["n_hull_checks"],
+                  inf["n_box_tests"])
+    achieved = ops / (med / 1e3) / 1e12
+    return {"workload": f"Dubins forest seed 0, |V_E| = {n}, lambda = {s0['lambda']}, "
+                        f"{s0['n_samples']} samples, one pass, median of {reps}",
+            "ms": med, "samples_per_s": s0["n_samples"] / (med / 1e3),
+            "steps_per_sample": inf["n_steps"] / max(1, inf["n_samples"]),
+            "accepted": s0["n_accepted"],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops,
+                         "unit": "Top/s", "frac": achieved / peak_ops}}
+
+
+def learned_leg(n_layouts, local, flush, peak_tflops):
+    """Learned proposal against the plain planner on the Dubins forest: the
+    network is trained on pairs harvested from plain runs (layout seeds from
+    0) and both planners then solve the same held-out layouts (seeds from
+    10000), with the same random stream."""
+    import torch
+    from paper_2409_06807_gb300 import mlp as M
+    from paper_2409_06807_gb300 import planner as P
+    t0 = time.perf_counter()
+    feats, targs = M.harvest(W.c2, list(range(0, 1000)), 2_000_000)
+    t_harvest = time.perf_counter() - t0
+    net = M.Mlp(max_batch=4096)
+    epochs, batch = 4, 4096
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hist = M.train(net, feats, targs, epochs=epochs, batch=batch, lr=1e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    rows_trained = epochs * (feats.shape[0] // batch) * batch
+    # forward, backward through activations and weights: three products per layer
+    train_tflops = 3 * MLP_FLOPS_FWD * rows_trained / (train_ms / 1e3) / 1e12
+    seeds = list(range(10_000, 10_000 + n_layouts))
+    pl = P.Planner(W.c2(seeds[0]), device=f"cuda:{local}")
+    out = {}
+    for mode, mix in (("plain", 0.0), ("learned", 0.5)):
+        pl.attach_mlp(net if mix > 0 else None, mix)
+        timed_query(pl, W.c2(seeds[0]), flush, MAX_ITERS)  # warm
+        rows = [timed_query(pl, W.c2(s), flush, MAX_ITERS) for s in seeds]
+        out[mode] = mode_summary(rows, P.OK)
+    pl.close()
+    return {
+        "workload": f"Dubins forest (200 boxes), {n_layouts} held-out layouts (seeds "
+                    f"{seeds[0]}..{seeds[-1]}), mix 0.5 learned / uniform draws",
+        "harvest": {"pairs": int(feats.shape[0]), "seconds": t_harvest,
+                    "layout_seeds": "plain runs from seed 0"},
+        "training": {"epochs": epochs, "batch": batch, "loss_per_epoch": hist,
+                     "ms": train_ms, "tflops": train_tflops,
+                     "frac_of_bf16_peak": train_tflops / peak_tflops},
+        **out,
+        "learned_over_plain": {
+            "samples": out["learned"]["mean_samples"] / out["plain"]["mean_samples"],
+            "p50_ms": out["learned"]["p50_ms"] / out["plain"]["p50_ms"],
+            "success": out["learned"]["success"] - out["plain"]["success"]},
+    }
+
+
+def serving_leg(n_queries, rate_hz, pool_gb, local, flush):
+    """Continuous batching: Poisson arrivals of mixed queries (three systems,
+    10-1000 boxes, node caps 16K-1M) submitted in real time to one
+    persistent launch whose team size and per-system branching factor come
+    from the autotuner; the same queries then run one at a time through the
+    single-query launch for comparison."""
+    from paper_2409_06807_gb300 import planner as P
+    from paper_2409_06807_gb300 import serve as S
+    tune_sample = [w for _, w in W.serving_mix(24, rate_hz, seed=6)]
+    team_blocks, lam, meas = S.autotune(tune_sample, pool_bytes=int(pool_gb * (1 << 30)),
+                                        max_iters=MAX_ITERS)
+    arrivals = [(t, w.with_(lambda_max=lam[w.system]))
+                for t, w in W.serving_mix(n_queries, rate_hz, seed=5)]
+    srv = S.Server(int(pool_gb * (1 << 30)), team_blocks=team_blocks, max_slots=1024,
+                   idle_ms=200.0)
+    t0 = time.perf_counter()
+    recs = S.run_arrivals(srv, arrivals, max_iters=MAX_ITERS)
+    wall = time.perf_counter() - t0
+    batched = S.summarize(recs, wall)
+    batched["teams"] = srv.stats()["teams"]
+    srv.close()
+    # the same queries, one at a time on the whole GPU
+    rows = []
+    cache = {}
+    for _, w in arrivals:
+        key = (w.system, w.t_e, w.lambda_max)
+        if key not in cache:
+            if len(cache) > 8:
+                for v in cache.values():
+                    v.close()
+                cache.clear()
+            cache[key] = P.Planner(w, device=f"cuda:{local}", box_capacity=1024)
+        rows.append(timed_query(cache[key], w, flush, MAX_ITERS))
+    for v in cache.values():
+        v.close()
+    seq = mode_summary(rows, P.OK)
+    seq["queries_per_s"] = len(rows) / (sum(r[1] for r in rows) / 1e3)
+    # arrival-to-completion latency had these queries been served first come,
+    # first served one at a time at the measured solve times
+    done, lat = 0.0, []
+    for (t_arr, _), r in zip(arrivals, rows):
+        done = max(done, t_arr) + r[1] / 1e3
+        lat.append(1e3 * (done - t_arr))
+    seq["fifo_latency_p50_ms"] = float(np.percentile(lat, 50))
+    seq["fifo_latency_p99_ms"] = float(np.percentile(lat, 99))
+    return {
+        "workload": f"{n_queries} queries, Poisson {rate_hz:.0f}/s, systems uniform over "
+                    "double integrator / Dubins / quadrotor, boxes log-uniform 10-1000, "
+                    "node caps log-uniform 16K-1M",
+        "pool_gb": pool_gb,
+        "autotune": {"team_blocks": team_blocks, "lambda_max": {str(k): v for k, v in lam.items()},
+                     "team_queries_per_s": {str(k): v for k, v in meas["team"].items()}},
+        "batched": batched,
+        "one_at_a_time": seq,
+    }
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2409_06807_gb300.build import build_planner
@@ -369,6 +551,15 @@ def run_ours(args, world, rank, local):
 
     if rank != 0:
         return
+    extra = {}
+    if args.steady:
+        extra["steady_state"] = steady_state_leg(local, peak_ops)
+    if args.learned_layouts > 0:
+        extra["learned"] = learned_leg(args.learned_layouts, local, flush,
+                                       float(pk.get("bf16_tflops", 1891.8)))
+    if args.serve_queries > 0:
+        extra["serving"] = serving_leg(args.serve_queries, 2000.0, args.serve_pool_gb, local,
+                                       flush)
     cpu = cpu_baseline(make) if world == 1 and not args.no_cpu else None
     pct = np.percentile(step_ms, [50, 99])
     line = {
@@ -395,6 +586,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
         "wall_s": t_wall,
+        **extra,
     }
     print(json.dumps(line), flush=True)
 
@@ -407,6 +599,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(W.BY_NAME))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--learned-layouts", type=int, default=1000,
+                    help="held-out layouts of the learned-vs-plain comparison (0: skip)")
+    ap.add_argument("--serve-queries", type=int, default=512,
+                    help="queries of the continuous-batching run (0: skip)")
+    ap.add_argument("--serve-pool-gb", type=float, default=16.0,
+                    help="device pool the serving run admits queries into")
+    ap.add_argument("--no-steady", dest="steady", action="store_false",
+                    help="skip the fixed-frontier single-pass microbench")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
