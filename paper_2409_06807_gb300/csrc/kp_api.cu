@@ -116,7 +116,7 @@ struct Dims {
 };
 
 struct Layout {
-  size_t ctl, boxes, st, parent, ctrl, steps, region, sub, in_ve, cst, cctrl, ck, cr, cs, flags,
+  size_t ctl, boxes, st, parent, ctrl, steps, region, sub, in_ve, cs, flags, acc_key, acc_list,
       n_valid, n_invalid, cov, avail, visited, claim, score, thr, ve, blk_a, blk_b, chunk_sum,
       stats, traj, feat, net_raw, total;
 };
@@ -141,12 +141,10 @@ Layout make_layout(const Dims& d) {
   L.region = take(te * 4);
   L.sub = take(te * 4);
   L.in_ve = take(te);
-  L.cst = take(te * d.D * 4);
-  L.cctrl = take(te * d.N * 4);
-  L.ck = take(te);
-  L.cr = take(te * 4);
   L.cs = take(te * 4);
   L.flags = take(te);
+  L.acc_key = take(te * 4);
+  L.acc_list = take(te * 4);
   L.n_valid = take((size_t)d.R * 4);
   L.n_invalid = take((size_t)d.R * 4);
   L.cov = take((size_t)d.R * 4);
@@ -562,11 +560,9 @@ void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* 
   P.region = reinterpret_cast<int32_t*>(A + lay.region);
   P.node_sub = reinterpret_cast<int32_t*>(A + lay.sub);
   P.in_ve = reinterpret_cast<uint8_t*>(A + lay.in_ve);
-  P.cst = reinterpret_cast<float*>(A + lay.cst);
-  P.cctrl = reinterpret_cast<float*>(A + lay.cctrl);
-  P.ck = reinterpret_cast<uint8_t*>(A + lay.ck);
-  P.cr = reinterpret_cast<int32_t*>(A + lay.cr);
   P.cs = reinterpret_cast<int32_t*>(A + lay.cs);
+  P.acc_key = reinterpret_cast<uint32_t*>(A + lay.acc_key);
+  P.acc_list = reinterpret_cast<uint32_t*>(A + lay.acc_list);
   P.flags = reinterpret_cast<uint8_t*>(A + lay.flags);
   P.n_valid = reinterpret_cast<uint32_t*>(A + lay.n_valid);
   P.n_invalid = reinterpret_cast<uint32_t*>(A + lay.n_invalid);
@@ -597,6 +593,9 @@ kp_status check_launch(kp_ctx* ctx, const KCtl& h) {
   if (h.err == KP_DEV_ERR_TIMEOUT)
     return fail(ctx, KP_ERR_TIMEOUT, "device wait exceeded %llu ns (site %d)",
                 (unsigned long long)ctx->wait_ns, h.err_where);
+  if (h.err == KP_DEV_ERR_REPLAY)
+    return fail(ctx, KP_ERR_STATE, "appended sample differs from its first derivation (site %d)",
+                h.err_where);
   if (h.err != 0) return fail(ctx, KP_ERR_CUDA, "device error %d", h.err);
   return KP_OK;
 }

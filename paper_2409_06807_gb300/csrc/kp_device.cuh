@@ -210,14 +210,20 @@ __device__ __forceinline__ float unit24(uint32_t w) {
 // exact for |k| < 2^11 (|x| below ~1.2e4 rad); then the hardware sin/cos
 // approximations on r in [-pi, pi] (absolute error below 1e-6).
 __device__ __forceinline__ void sincos_reduced(float x, float* s, float* c) {
-  const float k = rintf(x * 0.159154943091895336f);
-  float r = fmaf(-k, 6.28318548202514648f, x);
-  r = fmaf(-k, -1.74845560007448838e-07f, r);
+  const float k = rintf(__fmul_rn(x, 0.159154943091895336f));
+  float r = __fmaf_rn(-k, 6.28318548202514648f, x);
+  r = __fmaf_rn(-k, -1.74845560007448838e-07f, r);
   __sincosf(r, s, c);
 }
 
 // ---------------------------------------------------------------------------
 // systems (Sec. II, Eq. 1-2), FP32 in registers
+//
+// Every product and sum is written with an explicitly rounded operation
+// (__fmul_rn, __fadd_rn, __fmaf_rn), which the compiler neither fuses nor
+// splits: the integrators give the same bits wherever they are inlined, so
+// a sample re-derived from its key when it is appended equals the sample
+// the expand phase checked and binned.
 // ---------------------------------------------------------------------------
 
 template <int SYS>
@@ -231,16 +237,36 @@ struct System<KP_SYS_DI> {
                                               const KParams&) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const float p = x[i] + h * x[3 + i];
-      const float v = x[3 + i] + h * u[i];
+      const float p = __fmaf_rn(h, x[3 + i], x[i]);
+      const float v = __fmaf_rn(h, u[i], x[3 + i]);
       x[i] = p;
       x[3 + i] = v;
     }
   }
   __device__ __forceinline__ static float speed(const float* x) {
-    return sqrtf(x[3] * x[3] + x[4] * x[4] + x[5] * x[5]);
+    return sqrtf(__fmaf_rn(x[5], x[5], __fmaf_rn(x[4], x[4], __fmul_rn(x[3], x[3]))));
   }
 };
+
+// The classic RK4 combination x + h/6 (k1 + 2 k2 + 2 k3 + k4) and its
+// stage points, in one fixed order.
+template <int D>
+__device__ __forceinline__ void rk4_stage(const float* x, const float* k, float a, float* t) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) t[i] = __fmaf_rn(a, k[i], x[i]);
+}
+
+template <int D>
+__device__ __forceinline__ void rk4_combine(float* x, const float* k1, const float* k2,
+                                            const float* k3, const float* k4, float h6) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float s = __fmaf_rn(2.0f, k2[i], k1[i]);
+    s = __fmaf_rn(2.0f, k3[i], s);
+    s = __fadd_rn(s, k4[i]);
+    x[i] = __fmaf_rn(h6, s, x[i]);
+  }
+}
 
 // 6D Dubins airplane (Chitsaz & LaValle 2007); classic RK4.
 template <>
@@ -250,9 +276,9 @@ struct System<KP_SYS_DUBINS> {
     float sp, cp, st, ct;
     sincos_reduced(x[3], &sp, &cp);
     sincos_reduced(x[4], &st, &ct);
-    dx[0] = x[5] * cp * ct;
-    dx[1] = x[5] * sp * ct;
-    dx[2] = x[5] * st;
+    dx[0] = __fmul_rn(__fmul_rn(x[5], cp), ct);
+    dx[1] = __fmul_rn(__fmul_rn(x[5], sp), ct);
+    dx[2] = __fmul_rn(x[5], st);
     dx[3] = u[0];
     dx[4] = u[1];
     dx[5] = u[2];
@@ -260,19 +286,15 @@ struct System<KP_SYS_DUBINS> {
   __device__ __forceinline__ static void step(float* x, const float* u, float h,
                                               const KParams&) {
     float k1[6], k2[6], k3[6], k4[6], t[6];
+    const float hh = __fmul_rn(0.5f, h);
     f(x, u, k1);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) t[i] = x[i] + 0.5f * h * k1[i];
+    rk4_stage<6>(x, k1, hh, t);
     f(t, u, k2);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) t[i] = x[i] + 0.5f * h * k2[i];
+    rk4_stage<6>(x, k2, hh, t);
     f(t, u, k3);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) t[i] = x[i] + h * k3[i];
+    rk4_stage<6>(x, k3, h, t);
     f(t, u, k4);
-    const float h6 = h / 6.0f;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) x[i] = x[i] + h6 * (k1[i] + 2.0f * k2[i] + 2.0f * k3[i] + k4[i]);
+    rk4_combine<6>(x, k1, k2, k3, k4, __fdiv_rn(h, 6.0f));
   }
   __device__ __forceinline__ static float speed(const float* x) { return fabsf(x[5]); }
 };
@@ -291,48 +313,47 @@ struct System<KP_SYS_QUAD> {
     sincos_reduced(x[3], &sphi, &cphi);
     sincos_reduced(x[4], &sth, &cth);
     sincos_reduced(x[5], &sps, &cps);
-    const float sec = 1.0f / cth;
-    const float tth = sth * sec;
+    const float sec = __frcp_rn(cth);
+    const float tth = __fmul_rn(sth, sec);
     const float p = x[9], q = x[10], r = x[11];
     dx[0] = x[6];
     dx[1] = x[7];
     dx[2] = x[8];
-    dx[3] = p + sphi * tth * q + cphi * tth * r;
-    dx[4] = cphi * q - sphi * r;
-    dx[5] = (sphi * q + cphi * r) * sec;
-    const float thrust = u[0] + u[1] + u[2] + u[3];
-    const float a = thrust * P.recip[0];
-    dx[6] = a * (cphi * sth * cps + sphi * sps);
-    dx[7] = a * (cphi * sth * sps - sphi * cps);
-    dx[8] = a * (cphi * cth) - g;
-    const float tx = l * (u[1] - u[3]);
-    const float ty = l * (u[2] - u[0]);
-    const float tz = c * (u[0] - u[1] + u[2] - u[3]);
-    const float Lx = Ix * p, Ly = Iy * q, Lz = Iz * r;
-    dx[9] = (tx - (q * Lz - r * Ly)) * P.recip[1];
-    dx[10] = (ty - (r * Lx - p * Lz)) * P.recip[2];
-    dx[11] = (tz - (p * Ly - q * Lx)) * P.recip[3];
+    // Euler-angle rates W(phi, theta) omega
+    dx[3] = __fmaf_rn(__fmul_rn(cphi, tth), r, __fmaf_rn(__fmul_rn(sphi, tth), q, p));
+    dx[4] = __fmaf_rn(-sphi, r, __fmul_rn(cphi, q));
+    dx[5] = __fmul_rn(__fmaf_rn(cphi, r, __fmul_rn(sphi, q)), sec);
+    // world acceleration R(phi, theta, psi) (0, 0, sum T) / m - g e3
+    const float thrust = __fadd_rn(__fadd_rn(__fadd_rn(u[0], u[1]), u[2]), u[3]);
+    const float a = __fmul_rn(thrust, P.recip[0]);
+    const float cs = __fmul_rn(cphi, sth);
+    dx[6] = __fmul_rn(a, __fmaf_rn(cs, cps, __fmul_rn(sphi, sps)));
+    dx[7] = __fmul_rn(a, __fmaf_rn(cs, sps, -__fmul_rn(sphi, cps)));
+    dx[8] = __fmaf_rn(a, __fmul_rn(cphi, cth), -g);
+    // body torques and I omega' = tau - omega x (I omega)
+    const float tx = __fmul_rn(l, __fsub_rn(u[1], u[3]));
+    const float ty = __fmul_rn(l, __fsub_rn(u[2], u[0]));
+    const float tz = __fmul_rn(c, __fsub_rn(__fadd_rn(__fsub_rn(u[0], u[1]), u[2]), u[3]));
+    const float Lx = __fmul_rn(Ix, p), Ly = __fmul_rn(Iy, q), Lz = __fmul_rn(Iz, r);
+    dx[9] = __fmul_rn(__fsub_rn(tx, __fmaf_rn(q, Lz, -__fmul_rn(r, Ly))), P.recip[1]);
+    dx[10] = __fmul_rn(__fsub_rn(ty, __fmaf_rn(r, Lx, -__fmul_rn(p, Lz))), P.recip[2]);
+    dx[11] = __fmul_rn(__fsub_rn(tz, __fmaf_rn(p, Ly, -__fmul_rn(q, Lx))), P.recip[3]);
   }
   __device__ __forceinline__ static void step(float* x, const float* u, float h,
                                               const KParams& P) {
     float k1[12], k2[12], k3[12], k4[12], t[12];
+    const float hh = __fmul_rn(0.5f, h);
     f(x, u, P, k1);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) t[i] = x[i] + 0.5f * h * k1[i];
+    rk4_stage<12>(x, k1, hh, t);
     f(t, u, P, k2);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) t[i] = x[i] + 0.5f * h * k2[i];
+    rk4_stage<12>(x, k2, hh, t);
     f(t, u, P, k3);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) t[i] = x[i] + h * k3[i];
+    rk4_stage<12>(x, k3, h, t);
     f(t, u, P, k4);
-    const float h6 = h / 6.0f;
-#pragma unroll
-    for (int i = 0; i < 12; ++i)
-      x[i] = x[i] + h6 * (k1[i] + 2.0f * k2[i] + 2.0f * k3[i] + k4[i]);
+    rk4_combine<12>(x, k1, k2, k3, k4, __fdiv_rn(h, 6.0f));
   }
   __device__ __forceinline__ static float speed(const float* x) {
-    return sqrtf(x[6] * x[6] + x[7] * x[7] + x[8] * x[8]);
+    return sqrtf(__fmaf_rn(x[8], x[8], __fmaf_rn(x[7], x[7], __fmul_rn(x[6], x[6]))));
   }
 };
 

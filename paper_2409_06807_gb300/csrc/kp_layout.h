@@ -13,7 +13,9 @@ enum { KP_SYS_DI = 0, KP_SYS_DUBINS = 1, KP_SYS_QUAD = 2 };
 // planner state stored in KCtl::state
 enum { KP_DEV_RUNNING = 0, KP_DEV_SOLVED = 1, KP_DEV_FULL = 2, KP_DEV_BAD_ROOT = -1 };
 // launch errors stored in KCtl::err
-enum { KP_DEV_OK = 0, KP_DEV_ERR_TIMEOUT = 1 };
+// KP_DEV_ERR_REPLAY: with the sample log on, an accepted sample re-derived
+// from its key when it is appended differed from its first derivation.
+enum { KP_DEV_OK = 0, KP_DEV_ERR_TIMEOUT = 1, KP_DEV_ERR_REPLAY = 2 };
 // per-sample flag bits
 enum {
   KP_F_VALID = 1,
@@ -49,7 +51,7 @@ struct KCtl {
   int32_t n_edges;     // trajectory extraction: edges on the chain
   int32_t work_next;   // next sample key handed out in the expand phase
   uint32_t s_done;     // region chunks whose Score partial sum is written
-  int32_t pad_sd;
+  int32_t mat_next;    // next accepted sample handed out for materialising
   double score_sum;    // sum of Eq. 5 over R_avail, this pass
   // work counters since the last reset (samples, integrator steps run,
   // segment hulls tested against the obstacle set)
@@ -143,13 +145,15 @@ struct KParams {
   int32_t* region;
   int32_t* node_sub;  // global sub-region index of each node
   uint8_t* in_ve;
-  // per-sample candidates, indexed by sample key (< t_e)
-  float* cst;         // [D][t_e]
-  float* cctrl;       // [N][t_e]
-  uint8_t* ck;
-  int32_t* cr;
-  int32_t* cs;
-  uint8_t* flags;
+  // per-sample scratch, indexed by sample key (< t_e)
+  int32_t* cs;        // sub-region of a contender (claim check)
+  uint8_t* flags;     // KP_F_* of the sample
+  // accepted samples: each accept warp compacts its keys (winner flag in
+  // bit 31) at the start of its own key range in acc_key; the append
+  // copies them to acc_list in key order, i.e. acc_list[i] becomes node
+  // t_old + i
+  uint32_t* acc_key;
+  uint32_t* acc_list;
   // decomposition tables
   uint32_t* n_valid;
   uint32_t* n_invalid;

@@ -313,6 +313,49 @@ __device__ __forceinline__ void box_muller4(uint4 w, float* z) {
   }
 }
 
+// The draw of sample key (V_E position p = key / lam, j = key - p lam) in
+// pass it (Algorithm 2: random control in U, random duration): loads the
+// parent's state into x and returns the parent's node id.  Counter (it,
+// node, j, purpose): purpose 0 the control words (kept in wr), purpose 1
+// (duration, accept word, selector); with a network attached and the
+// selector below the mix threshold, the control and duration come from the
+// node's Gaussian with normals from purpose 3.  The expand phase and the
+// append (which re-derives accepted samples from their keys) both draw
+// through this function, so both see the same numbers.
+template <int SYS>
+__device__ __forceinline__ int draw_sample(const KParams& P, uint32_t it, int key, int lam, float* x,
+                                           float* u, int* k, uint32_t* wacc, uint32_t* wr) {
+  constexpr int D = System<SYS>::D, N = System<SYS>::N;
+  const int p = key / lam;
+  const int j = key - p * lam;
+  const int v = P.ve[p];
+#pragma unroll
+  for (int d = 0; d < D; ++d) x[d] = P.st[(size_t)d * P.t_e + v];
+  const uint4 w0 = philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 0u), P.seed_lo, P.seed_hi);
+  const uint4 w1 = philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 1u), P.seed_lo, P.seed_hi);
+  wr[0] = w0.x; wr[1] = w0.y; wr[2] = w0.z; wr[3] = w0.w;
+#pragma unroll
+  for (int d = 0; d < N; ++d) u[d] = __fmaf_rn(P.u_scale[d], unit24(wr[d]), P.u_lo[d]);
+  *k = P.k_min + (int)__umulhi(w1.x, P.k_span);
+  if (w1.z < P.mix_thr) {
+    // learned draw from the node's Gaussian (normals: purpose 3)
+    const uint4 w3 = philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 3u), P.seed_lo, P.seed_hi);
+    float z[4], mean[MLP_NQ], ls[MLP_NQ], q[4];
+    box_muller4(w3, z);
+    mlp_heads(P.net_raw + (size_t)p * MLP_OUT, mean, ls);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) q[d] = fminf(fmaxf(__fmaf_rn(expf(ls[d]), z[d], mean[d]), -1.0f), 1.0f);
+#pragma unroll
+    for (int d = 0; d < N; ++d)
+      u[d] = __fmaf_rn(P.u_scale[d], __fmul_rn(__fadd_rn(q[d], 1.0f), 0.5f), P.u_lo[d]);
+    const int kk = P.k_min + (int)floorf(__fmaf_rn((float)(P.k_span - 1),
+                                                   __fmul_rn(__fadd_rn(q[3], 1.0f), 0.5f), 0.5f));
+    *k = kk < P.k_min + (int)P.k_span - 1 ? kk : P.k_min + (int)P.k_span - 1;
+  }
+  *wacc = w1.y;
+  return v;
+}
+
 // Phase E: Algorithm 2 for every sample key in [0, S).
 //
 // Lanes integrate step by step and are refilled as they finish: a warp
@@ -387,15 +430,10 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
             f |= KP_F_BERN;
             P.avail[r] = 1;
           }
-          if (cont || bern) {
-#pragma unroll
-            for (int d = 0; d < D; ++d) P.cst[(size_t)d * P.t_e + key] = x[d];
-#pragma unroll
-            for (int d = 0; d < N; ++d) P.cctrl[(size_t)d * P.t_e + key] = u[d];
-            P.ck[key] = (uint8_t)k;
-            P.cr[key] = r;
-            P.cs[key] = s;
-          }
+          // an accepted sample is re-derived from its key when it is
+          // appended; only a contender's sub-region is kept for the claim
+          // check
+          if (cont) P.cs[key] = s;
         } else {
           atomicAdd(&P.n_invalid[r], 1u);
         }
@@ -438,35 +476,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
         const int rank = __popc(m_idle & lt);
         if (key < 0 && rank < avail) {
           key = pool_next + rank;
-          // random control in U and duration k * dt (counter: it, node, j, purpose)
-          const int p = key / lam;
-          const int j = key - p * lam;
-          v = P.ve[p];
-#pragma unroll
-          for (int d = 0; d < D; ++d) x[d] = P.st[(size_t)d * P.t_e + v];
-          const uint4 w0 =
-              philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 0u), P.seed_lo, P.seed_hi);
-          const uint4 w1 =
-              philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 1u), P.seed_lo, P.seed_hi);
-          wr[0] = w0.x; wr[1] = w0.y; wr[2] = w0.z; wr[3] = w0.w;
-#pragma unroll
-          for (int d = 0; d < N; ++d) u[d] = fmaf(P.u_scale[d], unit24(wr[d]), P.u_lo[d]);
-          k = P.k_min + (int)__umulhi(w1.x, P.k_span);
-          if (w1.z < P.mix_thr) {
-            // learned draw from the node's Gaussian (normals: purpose 3)
-            const uint4 w3 =
-                philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 3u), P.seed_lo, P.seed_hi);
-            float z[4], mean[MLP_NQ], ls[MLP_NQ], q[4];
-            box_muller4(w3, z);
-            mlp_heads(P.net_raw + (size_t)p * MLP_OUT, mean, ls);
-#pragma unroll
-            for (int d = 0; d < 4; ++d) q[d] = fminf(fmaxf(mean[d] + expf(ls[d]) * z[d], -1.0f), 1.0f);
-#pragma unroll
-            for (int d = 0; d < N; ++d) u[d] = P.u_lo[d] + P.u_scale[d] * ((q[d] + 1.0f) * 0.5f);
-            const int kk = P.k_min + (int)floorf((float)(P.k_span - 1) * ((q[3] + 1.0f) * 0.5f) + 0.5f);
-            k = kk < P.k_min + (int)P.k_span - 1 ? kk : P.k_min + (int)P.k_span - 1;
-          }
-          wacc = w1.y;
+          v = draw_sample<SYS>(P, it, key, lam, x, u, &k, &wacc, wr);
           i = 0;
           fail = 0;
           done = false;
@@ -510,46 +520,94 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
   }
 }
 
-// Phase A (warps 1..): accept flags of this block's key chunk, each thread
-// over a contiguous run of keys; phase S (warp 0) runs alongside.
-// Publishes the block's accepted count and adds the valid count to the
-// pass; returns this thread's offset among the block's accepted samples
-// (kept in a register across the grid barrier).
+// Contiguous key range [a, b) of warp w >= 1 inside the block's chunk
+// [c0, c1) (warp 0 runs the region estimates and gets none).
+__device__ __forceinline__ void warp_range(int c0, int c1, int* a, int* b) {
+  const int nw = (int)(blockDim.x >> 5) - 1;
+  const int w = (int)(threadIdx.x >> 5) - 1;
+  if (w < 0) {
+    *a = *b = c0;
+    return;
+  }
+  const int per = (c1 - c0 + nw - 1) / nw;
+  const long long lo = (long long)c0 + (long long)w * per;
+  *a = (int)(lo < c1 ? lo : c1);
+  *b = (int)(lo + per < c1 ? lo + per : c1);
+}
+
+// Phase A (warps 1..): accept decisions of this block's key chunk.  Each
+// warp walks its own key range in tiles of 32 x KP_ACC_KPL keys (lane l
+// takes keys t0 + 32q + l: every load is coalesced), with the loads of a
+// tile's flags, contenders' sub-regions and their claims issued together,
+// and compacts its accepted keys (claim winners marked in bit 31) in key
+// order at the start of its range in acc_key.  Phase S (warp 0) runs
+// alongside.  Publishes the block's accepted count, adds the valid count to
+// the pass, and returns the warp's accepted count and its offset among the
+// block's accepted samples (kept in registers across the grid barrier).
+constexpr int KP_ACC_KPL = 8;
+
 __device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, int nch, double* sd);
 
-__device__ __forceinline__ int phase_accept(const KParams& P, const Team& T, int S, int nch,
-                                            double* sd, LoopShared& sh) {
+template <bool LOG>
+__device__ __forceinline__ void phase_accept(const KParams& P, const Team& T, int S, int nch,
+                                             double* sd, LoopShared& sh, int* warp_off,
+                                             int* warp_n) {
   if (threadIdx.x < 32) phase_scores(P, T, nch, sd);
-  int k0, k1, r0, r1;
+  const uint32_t FULL = 0xffffffffu;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt = (1u << lane) - 1u;
+  int k0, k1, a, b;
   chunk_of(T, S, &k0, &k1);
-  scan_run(k0, k1, &r0, &r1);
-  int acc_n = 0;
-  unsigned long long valid_n = 0;
-  for (int key = r0; key < r1; ++key) {
-    uint32_t f = P.flags[key];
-    if (f & KP_F_VALID) {
-      ++valid_n;
-      bool win = false;
-      if (f & KP_F_CONTENDER) win = P.claim[P.cs[key]] == (uint32_t)key;
-      const bool acc = win || (f & KP_F_BERN);
-      if (win) f |= KP_F_WINNER;
-      if (acc) {
-        f |= KP_F_ACCEPTED;
-        ++acc_n;
-      }
-      P.flags[key] = (uint8_t)f;
+  warp_range(k0, k1, &a, &b);
+  int n_acc = 0;
+  uint32_t n_valid = 0;
+  for (int t0 = a; t0 < b; t0 += 32 * KP_ACC_KPL) {
+    uint32_t f[KP_ACC_KPL], c[KP_ACC_KPL];
+    int s[KP_ACC_KPL];
+#pragma unroll
+    for (int q = 0; q < KP_ACC_KPL; ++q) {
+      const int key = t0 + 32 * q + (int)lane;
+      f[q] = key < b ? P.flags[key] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < KP_ACC_KPL; ++q)
+      s[q] = (f[q] & KP_F_CONTENDER) ? P.cs[t0 + 32 * q + (int)lane] : 0;
+#pragma unroll
+    for (int q = 0; q < KP_ACC_KPL; ++q) c[q] = (f[q] & KP_F_CONTENDER) ? P.claim[s[q]] : 0u;
+#pragma unroll
+    for (int q = 0; q < KP_ACC_KPL; ++q) {
+      const int key = t0 + 32 * q + (int)lane;
+      const bool valid = (f[q] & KP_F_VALID) != 0;
+      n_valid += valid ? 1u : 0u;
+      const bool win = (f[q] & KP_F_CONTENDER) && c[q] == (uint32_t)key;
+      const bool acc = valid && (win || (f[q] & KP_F_BERN));
+      const uint32_t m = __ballot_sync(FULL, acc);
+      if (acc) P.acc_key[a + n_acc + __popc(m & lt)] = (uint32_t)key | (win ? 0x80000000u : 0u);
+      n_acc += __popc(m);
+      if (LOG && key < b && key < P.log.capacity)
+        P.log.flags[key] =
+            (uint8_t)(f[q] | (win ? KP_F_WINNER : 0u) | (acc ? KP_F_ACCEPTED : 0u));
     }
   }
-  int block_acc;
-  const int off = block_exclusive_scan(acc_n, sh.scan, &block_acc);
-  unsigned long long b, dummy;
-  block_sum2(valid_n, 0, sh.red, &b, &dummy);
+  // warp counts -> offsets in key order (warps own ascending ranges)
+  const int w = (int)(threadIdx.x >> 5);
+  if (lane == 0) sh.scan.warp[w] = n_acc;
+  __syncthreads();
+  int off = 0, block_acc = 0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+    const int cq = sh.scan.warp[q];
+    off += q < w ? cq : 0;
+    block_acc += cq;
+  }
+  *warp_off = off;
+  *warp_n = n_acc;
+  unsigned long long bv, dummy;
+  block_sum2((unsigned long long)n_valid, 0, sh.red, &bv, &dummy);
   if (threadIdx.x == 0) {
     if (T.b == 0) P.ctl->work_next = 0;  // the expand phase is over
     P.blk_a[T.b] = (uint32_t)block_acc;
-    if (b) atomicAdd(&P.ctl->it_valid, (uint32_t)b);
+    if (bv) atomicAdd(&P.ctl->it_valid, (uint32_t)bv);
   }
-  return off;
 }
 
 // Pairwise sum of buf[0..n), n a power of two, by one warp (bottom-up
@@ -638,74 +696,104 @@ __device__ __forceinline__ void phase_thresholds(const KParams& P, const Team& T
   }
 }
 
-// Phase P (warps 1..): append this block's accepted samples in key order;
-// each thread writes the accepted samples of its own run from its offset.
-// Phase T (warp 0) runs alongside.  No block-wide synchronisation.
-template <int SYS, bool LOG>
-__device__ __forceinline__ void phase_append(const KParams& P, const Team& T, int S, int lam,
-                                             int t_old, int nch, int thread_off, int* total_out) {
-  constexpr int D = System<SYS>::D, N = System<SYS>::N;
+// Phase P (warps 1..): each warp copies its compacted accepted keys to
+// their place in key order, acc_list[block offset + warp offset + i]
+// (acc_list[i] becomes node t_old + i).  Phase T (warp 0) runs alongside.
+__device__ __forceinline__ void phase_append(const KParams& P, const Team& T, int S, int nch,
+                                             int warp_off, int warp_n, int* total_out) {
   unsigned long long off, total;
   warp_prefix(T, P.blk_a, &off, &total);
   *total_out = (int)total;
   if (threadIdx.x < 32) {
+    if (T.b == 0 && threadIdx.x == 0) P.ctl->mat_next = 0;
     phase_thresholds(P, T, nch);
     return;
   }
-  int k0, k1, r0, r1;
+  int k0, k1, a, b;
   chunk_of(T, S, &k0, &k1);
-  scan_run(k0, k1, &r0, &r1);
-  int id = t_old + (int)off + thread_off;
-  for (int key = r0; key < r1; ++key) {
-    uint32_t f = P.flags[key];
-    if (f & KP_F_ACCEPTED) {
-      float pos[3];
+  warp_range(k0, k1, &a, &b);
+  const int base = (int)off + warp_off;
+  for (int i = (int)(threadIdx.x & 31u); i < warp_n; i += 32) P.acc_list[base + i] = P.acc_key[a + i];
+}
+
+// Materialises the new nodes t_old .. t_old + n_new - 1: every accepted
+// sample is re-derived from its key (the same draw and the same integrator
+// steps as in the expand phase, so the same numbers) and written to the
+// tree with its parent, control, duration, region and sub-region; visited
+// and the goal test (closed ball on position; the smallest new goal node
+// wins) follow.  Warps take batches of 32 from a grid-wide counter, so long
+// and short samples spread over the whole team.  With the sample log on,
+// the re-derived state is compared with the logged one.
+template <int SYS, bool LOG>
+__device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int t_old, int n_new,
+                                            int lam) {
+  using Sys = System<SYS>;
+  constexpr int D = Sys::D, N = Sys::N;
+  const uint32_t lane = threadIdx.x & 31u;
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&P.ctl->mat_next, 32);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n_new) break;
+    const int i = base + (int)lane;
+    if (i >= n_new) continue;
+    const uint32_t e = P.acc_list[i];
+    const int key = (int)(e & 0x7fffffffu);
+    const int id = t_old + i;
+    float x[D], u[N];
+    int k;
+    uint32_t wacc, wr[4];
+    const int v = draw_sample<SYS>(P, it, key, lam, x, u, &k, &wacc, wr);
+    for (int st = 0; st < k; ++st) Sys::step(x, u, P.dt, P);
+    int r, s;
+    bin_state<SYS>(x, P, &r, &s);
 #pragma unroll
-      for (int i = 0; i < D; ++i) {
-        const float xi = P.cst[(size_t)i * P.t_e + key];
-        P.st[(size_t)i * P.t_e + id] = xi;
-        if (i < 3) pos[i] = xi;
-      }
+    for (int d = 0; d < D; ++d) P.st[(size_t)d * P.t_e + id] = x[d];
 #pragma unroll
-      for (int i = 0; i < N; ++i) P.ctrl[(size_t)i * P.t_e + id] = P.cctrl[(size_t)i * P.t_e + key];
-      const int s = P.cs[key];
-      const int pos_ve = key / lam;
-      P.steps[id] = P.ck[key];
-      P.parent[id] = P.ve[pos_ve];
-      if (P.hv_cap > 0 && (f & KP_F_WINNER)) {
-        // training pair: the parent's features and this sample's draw
-        const uint32_t h = atomicAdd(P.hv_count, 1u);
-        if (h < (uint32_t)P.hv_cap) {
-          const __nv_bfloat16* fr = reinterpret_cast<const __nv_bfloat16*>(P.feat) + (size_t)pos_ve * 32;
-          for (int c = 0; c < 32; ++c) P.hv_feat[(size_t)h * 32 + c] = __bfloat162float(fr[c]);
+    for (int d = 0; d < N; ++d) P.ctrl[(size_t)d * P.t_e + id] = u[d];
+    P.steps[id] = (uint8_t)k;
+    P.parent[id] = v;
+    P.region[id] = r;
+    P.node_sub[id] = s;
+    P.in_ve[id] = 1;
+    P.visited[s] = 1;
+    const float dx = __fsub_rn(x[0], P.goal_c[0]), dy = __fsub_rn(x[1], P.goal_c[1]),
+                dz = __fsub_rn(x[2], P.goal_c[2]);
+    const bool goal = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) <= P.goal_r2;
+    if (goal) atomicMin(&P.ctl->goal_node, id);
+    if (P.hv_cap > 0 && (e & 0x80000000u)) {
+      // training pair: the parent's features and this sample's draw
+      const uint32_t h = atomicAdd(P.hv_count, 1u);
+      if (h < (uint32_t)P.hv_cap) {
+        const __nv_bfloat16* fr =
+            reinterpret_cast<const __nv_bfloat16*>(P.feat) + (size_t)(key / lam) * 32;
+        for (int c = 0; c < 32; ++c) P.hv_feat[(size_t)h * 32 + c] = __bfloat162float(fr[c]);
 #pragma unroll
-          for (int d = 0; d < 3; ++d)
-            P.hv_target[(size_t)h * 4 + d] =
-                2.0f * (P.cctrl[(size_t)d * P.t_e + key] - P.u_lo[d]) / P.u_scale[d] - 1.0f;
-          P.hv_target[(size_t)h * 4 + 3] =
-              P.k_span > 1 ? 2.0f * (float)(P.ck[key] - P.k_min) / (float)(P.k_span - 1) - 1.0f : 0.0f;
-        }
+        for (int d = 0; d < 3; ++d)
+          P.hv_target[(size_t)h * 4 + d] = 2.0f * (u[d] - P.u_lo[d]) / P.u_scale[d] - 1.0f;
+        P.hv_target[(size_t)h * 4 + 3] =
+            P.k_span > 1 ? 2.0f * (float)(k - P.k_min) / (float)(P.k_span - 1) - 1.0f : 0.0f;
       }
-      P.region[id] = P.cr[key];
-      P.node_sub[id] = s;
-      P.in_ve[id] = 1;
-      P.visited[s] = 1;
-      const float dx = pos[0] - P.goal_c[0], dy = pos[1] - P.goal_c[1], dz = pos[2] - P.goal_c[2];
-      if (dx * dx + dy * dy + dz * dz <= P.goal_r2) {
-        f |= KP_F_GOAL;
-        atomicMin(&P.ctl->goal_node, id);
-      }
-      ++id;
     }
-    if (LOG && key < P.log.capacity) P.log.flags[key] = (uint8_t)f;
+    if (LOG && key < P.log.capacity) {
+      if (goal) P.log.flags[key] |= (uint8_t)KP_F_GOAL;
+      bool same = P.log.region[key] == r && P.log.sub[key] == s;
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+        same = same && __float_as_uint(P.log.state[12 * (size_t)key + d]) == __float_as_uint(x[d]);
+      if (!same) raise_error(P.ctl, KP_DEV_ERR_REPLAY, 40);
+    }
   }
 }
 
 // Phase N: Algorithm 4 node sets, one draw per old node (counter: it, v, 0,
 // purpose 2) against the threshold of its region; new nodes are in V_E.
 // Returns this thread's offset among the block's V_E members.
+// The new nodes (ids from t_old) are materialised here as well; they are
+// counted as V_E members without reading their sets.
+template <int SYS, bool LOG>
 __device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, uint32_t it,
-                                              int t_old, int t_new, LoopShared& sh) {
+                                              int t_old, int t_new, int lam, LoopShared& sh) {
   int v0, v1, r0, r1;
   chunk_of(T, t_new, &v0, &v1);
   thread_run(v0, v1, &r0, &r1);
@@ -722,6 +810,7 @@ __device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, u
   int tot;
   const int off = block_exclusive_scan(c, sh.scan, &tot);
   if (threadIdx.x == 0) P.blk_b[T.b] = (uint32_t)tot;
+  materialise<SYS, LOG>(P, it, t_old, t_new - t_old, lam);
   return off;
 }
 
@@ -788,18 +877,19 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     stamp(0);
     if (!team_sync(T, ctl, P.wait_ns, 20)) return false;
     stamp(1);
-    const int acc_off = phase_accept(P, T, S, nch, sd, sh);
+    int warp_off, warp_n;
+    phase_accept<LOG>(P, T, S, nch, sd, sh, &warp_off, &warp_n);
     stamp(2);
     if (!team_sync(T, ctl, P.wait_ns, 21)) return false;
     stamp(4);
     int n_acc;
-    phase_append<SYS, LOG>(P, T, S, lam, n_tree, nch, acc_off, &n_acc);
+    phase_append(P, T, S, nch, warp_off, warp_n, &n_acc);
     stamp(5);
     if (!team_sync(T, ctl, P.wait_ns, 22)) return false;
     stamp(7);
     const int t_old = n_tree;
     n_tree = t_old + n_acc;
-    ve_off = phase_nodesets(P, T, it, t_old, n_tree, sh);
+    ve_off = phase_nodesets<SYS, LOG>(P, T, it, t_old, n_tree, lam, sh);
     stamp(8);
     if (!team_sync(T, ctl, P.wait_ns, 23)) return false;
     stamp(9);
