@@ -50,9 +50,13 @@ struct Team {
 // must stop.  Sense is carried by a generation counter: a block reads the
 // generation, arrives, and the last arriver resets the count and publishes
 // the next generation with release semantics.
-__device__ __forceinline__ bool team_sync(const Team& T, KCtl* ctl, uint64_t limit_ns, int where) {
+// With 'watch' given, thread 0 also reads that word after the barrier and
+// the block gets its value in *watched (one load per block instead of one
+// per thread on a word every block reads).
+__device__ __forceinline__ bool team_sync(const Team& T, KCtl* ctl, uint64_t limit_ns, int where,
+                                          const int* watch = nullptr, int* watched = nullptr) {
   const uint32_t nblocks = (uint32_t)T.nb;
-  __shared__ int s_ok;
+  __shared__ int s_ok, s_watch;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -80,8 +84,10 @@ __device__ __forceinline__ bool team_sync(const Team& T, KCtl* ctl, uint64_t lim
     __threadfence();
     if (ok && *((volatile int*)&ctl->err) != 0) ok = 0;
     s_ok = ok;
+    if (watch) s_watch = *((volatile const int*)watch);
   }
   __syncthreads();
+  if (watch) *watched = s_watch;
   return s_ok != 0;
 }
 

@@ -36,6 +36,7 @@ struct LoopShared {
   unsigned long long red[64];
   uint64_t mbar;
   int flag;
+  int bcast[2];
   int32_t phase_ns[12];  // per-pass phase timers (block 0, thread 0)
 };
 
@@ -459,18 +460,28 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
           // out of work together
           // (at the very end a warp takes only what its idle lanes can
           // start now, so no warp is left with a second round of samples)
+          // (the batch is sized from the counter's current value: a warp
+          // that last took keys long ago must not size it from a stale
+          // position and leave with a large batch just before the end)
           const int n_idle_now = __popc(m_idle);
-          int want = (S - pool_end) / (2 * T.nb * (int)(blockDim.x >> 5));
-          want = want < n_idle_now ? n_idle_now : (want > KP_KEY_BATCH ? KP_KEY_BATCH : want);
           int base = 0;
-          if (lane == 0) base = atomicAdd(&P.ctl->work_next, want);
+          if (lane == 0) {
+            // (a warp's first batch of the pass is sized from the start)
+            const int cur = pool_end == 0 ? 0 : *((volatile int*)&P.ctl->work_next);
+            int want = (S - cur) / (2 * T.nb * (int)(blockDim.x >> 5));
+            want = want < n_idle_now ? n_idle_now : (want > KP_KEY_BATCH ? KP_KEY_BATCH : want);
+            base = atomicAdd(&P.ctl->work_next, want);
+            base = base < S ? base : S;
+            pool_end = base + want < S ? base + want : S;
+          }
           base = __shfl_sync(FULL, base, 0);
+          const int end_now = __shfl_sync(FULL, pool_end, 0);
           if (base >= S) {
             exhausted = true;
             break;
           }
           pool_next = base;
-          pool_end = base + want < S ? base + want : S;
+          pool_end = end_now;
         }
         const int avail = pool_end - pool_next;
         const int rank = __popc(m_idle & lt);
@@ -831,8 +842,14 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     ctl->work_next = 0;
     ctl->s_done = 0;
   }
-  int n_tree = ctl->n_nodes;
-  uint32_t it = (uint32_t)ctl->iteration;
+  // the loop state, read once per block
+  if (threadIdx.x == 0) {
+    sh.bcast[0] = ctl->n_nodes;
+    sh.bcast[1] = ctl->iteration;
+  }
+  __syncthreads();
+  int n_tree = sh.bcast[0];
+  uint32_t it = (uint32_t)sh.bcast[1];
   const int nch = P.nch;
 
   // V_E list from the stored node sets
@@ -924,12 +941,13 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     }
     ++it;
     const uint64_t t_l = timer ? global_ns() : 0;
-    if (!team_sync(T, ctl, P.wait_ns, 24)) return false;
+    int stop;
+    if (!team_sync(T, ctl, P.wait_ns, 24, &ctl->stop, &stop)) return false;
     if (timer) {
       t_mark = global_ns();
       prev_wait = (int32_t)(t_mark - t_l);  // reported with the next pass
     }
-    if (*((volatile int*)&ctl->stop)) break;
+    if (stop) break;
   }
   if (T.b == 0 && threadIdx.x == 0) {
     ctl->n_nodes = n_tree;
