@@ -239,6 +239,9 @@ struct System;
 template <>
 struct System<KP_SYS_DI> {
   static constexpr int D = 6, N = 3;
+  // finished lanes a warp waits for before it finalises and refills them
+  // (measured on the GB300: cheap steps favour large refill groups)
+  static constexpr int REFILL_MIN = 28;
   __device__ __forceinline__ static void step(float* x, const float* u, float h,
                                               const KParams&) {
 #pragma unroll
@@ -278,6 +281,7 @@ __device__ __forceinline__ void rk4_combine(float* x, const float* k1, const flo
 template <>
 struct System<KP_SYS_DUBINS> {
   static constexpr int D = 6, N = 3;
+  static constexpr int REFILL_MIN = 20;
   __device__ __forceinline__ static void f(const float* x, const float* u, float* dx) {
     float sp, cp, st, ct;
     sincos_reduced(x[3], &sp, &cp);
@@ -310,6 +314,7 @@ struct System<KP_SYS_DUBINS> {
 template <>
 struct System<KP_SYS_QUAD> {
   static constexpr int D = 12, N = 4;
+  static constexpr int REFILL_MIN = 8;
   __device__ __forceinline__ static void f(const float* x, const float* u, const KParams& P,
                                            float* dx) {
     // phys: m g l c Ixx Iyy Izz; recip: 1/m 1/Ixx 1/Iyy 1/Izz

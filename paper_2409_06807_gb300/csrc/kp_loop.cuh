@@ -367,7 +367,6 @@ __device__ __forceinline__ int draw_sample(const KParams& P, uint32_t it, int ke
 // finalise / start-up work is shared by many lanes and no lane idles while
 // a long sample runs next to it.  Every sample's arithmetic depends on its
 // key alone, so the result does not depend on which lane ran it.
-constexpr int KP_REFILL_MIN = 8;  // lanes that must be free before a refill
 constexpr int KP_KEY_BATCH = 128; // keys a warp takes from the grid counter
 
 template <int SYS, bool LOG>
@@ -406,7 +405,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
       }
     }
     const uint32_t m_free = __ballot_sync(FULL, key < 0 || done);
-    if (__popc(m_free) >= KP_REFILL_MIN || (exhausted && m_free)) {
+    if (__popc(m_free) >= Sys::REFILL_MIN || (exhausted && m_free)) {
       // ---- finalise the lanes that finished -------------------------------
       if (key >= 0 && done) {
         int r, s;
