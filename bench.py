@@ -607,10 +607,23 @@ def main():
                     help="device pool the serving run admits queries into")
     ap.add_argument("--no-steady", dest="steady", action="store_false",
                     help="skip the fixed-frontier single-pass microbench")
+    ap.add_argument("--only-steady", action="store_true",
+                    help="run only the fixed-frontier single-pass microbench (for profiling: "
+                         "6 tree-growth loop launches, then 23 single-pass launches)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_setup(args.gpus)
+    if args.only_steady:
+        import torch
+        from paper_2409_06807_gb300.build import build_planner
+        build_planner()
+        torch.cuda.set_device(local)
+        pk, _ = peaks()
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_ops = n_sm * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        print(json.dumps({"steady_state": steady_state_leg(local, peak_ops)}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:
