@@ -354,6 +354,17 @@ kp_status kp_mlp_gradients(kp_mlp *mlp, const float *dev_x, const float *dev_t,
 kp_status kp_mlp_train_step(kp_mlp *mlp, const float *dev_x,
                             const float *dev_t, int32_t M, float lr,
                             float *host_loss);
+/* One epoch of the same training on the device: rows perm[0..rows) of
+ * dev_x [rows][32] / dev_t [rows][4] in mini-batches of max_batch rows (a
+ * tail shorter than a batch is skipped), each batch gathered into the
+ * network's own buffers and its whole step (forward, backward, Adam) run
+ * as one CUDA graph launch; the graph is captured on the first call and
+ * reused.  dev_perm is a device array of row indices.  host_loss (nullable)
+ * receives the mean mini-batch loss.  Synchronises; KP_ERR_TIMEOUT if a
+ * tensor-core kernel's bounded wait expired. */
+kp_status kp_mlp_train_epoch(kp_mlp *mlp, const float *dev_x, const float *dev_t,
+                             const int32_t *dev_perm, int64_t rows, float lr,
+                             float *host_loss);
 void kp_mlp_destroy(kp_mlp *mlp);
 /* Planner use of a network (6D systems): each pass evaluates the network on
  * the features of every V_E node; a sample whose selector draw falls below

@@ -111,6 +111,18 @@ class Mlp:
                   "kp_mlp_gradients")
         return g, loss.value
 
+    def train_epoch(self, x, t, perm, lr=1e-3):
+        """One epoch over rows perm of (x, t) in mini-batches of max_batch
+        rows, driven on the device; returns the mean mini-batch loss."""
+        import torch
+        perm = perm.to(device=x.device, dtype=torch.int32).contiguous()
+        loss = C.c_float()
+        self._chk(lib().kp_mlp_train_epoch(self._ctx, x.contiguous().data_ptr(),
+                                           t.contiguous().data_ptr(), perm.data_ptr(),
+                                           int(perm.shape[0]), float(lr), C.byref(loss)),
+                  "kp_mlp_train_epoch")
+        return loss.value
+
     def train_step(self, x, t, lr=1e-3, want_loss=False):
         loss = C.c_float()
         self._chk(lib().kp_mlp_train_step(self._ctx, x.data_ptr(), t.data_ptr(), x.shape[0],
@@ -155,6 +167,9 @@ def train(mlp, feats, targs, epochs=3, batch=4096, lr=1e-3, seed=0, log_every=0)
     hist = []
     for ep in range(epochs):
         perm = torch.randperm(n, generator=g).to(feats.device)
+        if batch == mlp.max_batch:
+            hist.append(mlp.train_epoch(feats, targs, perm, lr))
+            continue
         losses = []
         for i in range(0, n - batch + 1, batch):
             idx = perm[i:i + batch]

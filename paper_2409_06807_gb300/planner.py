@@ -131,6 +131,8 @@ SIGNATURES = {
     "kp_mlp_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.POINTER(C.c_float),
                                    C.POINTER(C.c_float)]),
     "kp_mlp_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_float, C.POINTER(C.c_float)]),
+    "kp_mlp_train_epoch": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_float,
+                                     C.POINTER(C.c_float)]),
     "kp_mlp_destroy": (None, [_vp]),
     "kp_attach_mlp": (C.c_int, [_vp, _vp, C.c_float]),
     "kp_set_harvest": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp]),

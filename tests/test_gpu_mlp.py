@@ -180,3 +180,33 @@ def test_learned_plan_revalidated(M):
             assert np.max(np.abs(x_end - traj["states"][e]) / scale) <= 1e-4
             prev = traj["states"][e].astype(np.float64)
         assert np.linalg.norm(prev[:3] - w.goal_c) <= float(w.goal_r) * (1 + 1e-6)
+
+
+def test_device_epoch_matches_step_loop(M):
+    """One epoch driven on the device (gather + step as one graph launch per
+    mini-batch) against the same mini-batches stepped from the host: equal
+    mean loss and parameters up to the rounding of FP32 atomic sums; the
+    graph is reused by later epochs, which keep lowering the loss."""
+    import torch
+    mlp, _ = M
+    rng = np.random.default_rng(21)
+    n = 512 * 6 + 100  # the ragged tail is skipped by both
+    x = np.zeros((n, 32), np.float32)
+    x[:, :20] = rng.normal(0, 1, (n, 20))
+    t = np.tanh(x[:, :4] * 0.5 + 0.05 * rng.normal(0, 1, (n, 4))).astype(np.float32)
+    X, T = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    perm = torch.from_numpy(rng.permutation(n).astype(np.int64)).cuda()
+    p0 = mlp.init_params(8)
+    a = mlp.Mlp(p0, max_batch=512)
+    b = mlp.Mlp(p0, max_batch=512)
+    loss_a = a.train_epoch(X, T, perm, 1e-3)
+    losses = []
+    for i in range(0, n - 512 + 1, 512):
+        idx = perm[i:i + 512]
+        losses.append(b.train_step(X.index_select(0, idx).contiguous(),
+                                   T.index_select(0, idx).contiguous(), 1e-3, want_loss=True))
+    assert abs(loss_a - np.mean(losses)) <= 1e-3 * abs(np.mean(losses)) + 1e-4
+    pa, pb = a.params(), b.params()
+    assert np.max(np.abs(pa - pb)) < 5e-3
+    later = [a.train_epoch(X, T, perm, 1e-3) for _ in range(2)]
+    assert later[-1] < loss_a
