@@ -394,17 +394,19 @@ size_t build_blob(unsigned char* blob, const float* boxes, int nb, const kp_work
                  host_bp_cell(fb[b * 8 + a], ws.lo[a], scale[a], g) + 1;
       entries += cells;
     }
-    const size_t bytes = (size_t)pad * 32 + round16((size_t)(g * g * g + 1) * 4) +
+    const size_t bytes = (size_t)pad * 32 + round16((size_t)(g * g * g + 1) * 2) +
                          round16((size_t)entries * 2);
     if ((entries <= KP_BP_MAX_IDS && bytes <= max_bytes) || g == 1) break;
   }
   const int C = g * g * g;
   const size_t start_off = (size_t)pad * 32;
-  const size_t ids_off = start_off + round16((size_t)(C + 1) * 4);
-  int* start = reinterpret_cast<int*>(blob + start_off);
+  const size_t ids_off = start_off + round16((size_t)(C + 1) * 2);
+  // cell starts fit in 16 bits: at most KP_BP_MAX_IDS (< 65536) ids, or the
+  // box count for the single-cell grid
+  uint16_t* start16 = reinterpret_cast<uint16_t*>(blob + start_off);
   uint16_t* ids = reinterpret_cast<uint16_t*>(blob + ids_off);
   std::vector<int> lo3((size_t)nb * 3), hi3((size_t)nb * 3);
-  for (int c = 0; c <= C; ++c) start[c] = 0;
+  std::vector<int> start((size_t)C + 1, 0);
   for (int b = 0; b < nb; ++b) {
     for (int a = 0; a < 3; ++a) {
       lo3[b * 3 + a] = host_bp_cell(fb[b * 8 + a], ws.lo[a], scale[a], g);
@@ -415,7 +417,8 @@ size_t build_blob(unsigned char* blob, const float* boxes, int nb, const kp_work
         for (int x = lo3[b * 3]; x <= hi3[b * 3]; ++x) start[x + g * (y + g * z) + 1] += 1;
   }
   for (int c = 0; c < C; ++c) start[c + 1] += start[c];
-  std::vector<int> cursor(start, start + C);
+  for (int c = 0; c <= C; ++c) start16[c] = (uint16_t)start[c];
+  std::vector<int> cursor(start.begin(), start.begin() + C);
   for (int b = 0; b < nb; ++b)
     for (int z = lo3[b * 3 + 2]; z <= hi3[b * 3 + 2]; ++z)
       for (int y = lo3[b * 3 + 1]; y <= hi3[b * 3 + 1]; ++y)
@@ -464,26 +467,36 @@ kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
 
 kp_status configure_launch(kp_ctx* ctx) {
   const Dims& d = ctx->dims;
-  // shared memory: boxes + the double scratch of the region-score sums
-  const int min_ch = d.R_pad / (d.R_pad < 128 ? d.R_pad : 128);
-  const int sd = min_ch > 1024 ? min_ch : 1024;
-  ctx->P.sd_bytes = sd * 8;
-  ctx->smem = (size_t)ctx->P.blob_bytes + (size_t)sd * 8 +
-              (ctx->P.features_on ? (size_t)MLP_LOOP_TILE_SMEM : 0);
-  for (int log = 0; log < 2; ++log) {
-    int bps = 0;
-    KP_CUDA(occupancy(d.sys, log != 0, ctx->smem, &bps));
-    if (bps < 1) return fail(ctx, KP_ERR_ARG, "loop kernel cannot be resident");
-    int g = bps * ctx->num_sms;
-    if (g > KP_MAX_GRID) g = KP_MAX_GRID;
-    ctx->grid[log] = g;
-  }
+  // shared memory: boxes + the double scratch of the region-score sums (a
+  // chunk's scores, then the chunk sums) + the network tile (learned form)
+  auto grids = [&](int sd) -> kp_status {
+    ctx->P.sd_bytes = sd * 8;
+    ctx->smem = (size_t)ctx->P.blob_bytes + (size_t)sd * 8 +
+                (ctx->P.features_on ? (size_t)MLP_LOOP_TILE_SMEM : 0);
+    for (int log = 0; log < 2; ++log) {
+      int bps = 0;
+      KP_CUDA(occupancy(d.sys, log != 0, ctx->smem, &bps));
+      if (bps < 1) return fail(ctx, KP_ERR_ARG, "loop kernel cannot be resident");
+      int g = bps * ctx->num_sms;
+      if (g > KP_MAX_GRID) g = KP_MAX_GRID;
+      ctx->grid[log] = g;
+    }
+    return KP_OK;
+  };
+  // first with room for any chunking (chunks of at least R_pad / 1024
+  // regions, at most 1024 chunk sums) ...
+  const int min_ch = d.R_pad / (d.R_pad < 1024 ? d.R_pad : 1024);
+  kp_status s = grids(min_ch > 1024 ? min_ch : 1024);
+  if (s != KP_OK) return s;
   // region chunks: a power of two <= the smaller grid, <= R_pad, <= 1024
   const int gmin = ctx->grid[0] < ctx->grid[1] ? ctx->grid[0] : ctx->grid[1];
   int nch = 1;
   while (nch * 2 <= gmin && nch * 2 <= d.R_pad && nch * 2 <= 1024) nch *= 2;
   ctx->P.nch = nch;
-  return KP_OK;
+  // ... then with the scratch this chunking needs (smaller shared memory
+  // never lowers the grid, so nch stays at most the grid)
+  const int need = d.R_pad / nch > nch ? d.R_pad / nch : nch;
+  return grids(need);
 }
 
 kp_status clear_tables(kp_ctx* ctx) {
@@ -1088,7 +1101,7 @@ void* g_static_base[kStaticMaxDevices];  // device address of the scratch, per d
 __global__ void kp_static_blob_kernel(unsigned char* blob, const float* raw, int n, int pad,
                                       int start_off, int ids_off) {
   float* dst = reinterpret_cast<float*>(blob);
-  int* start = reinterpret_cast<int*>(blob + start_off);
+  uint16_t* start = reinterpret_cast<uint16_t*>(blob + start_off);
   uint16_t* ids = reinterpret_cast<uint16_t*>(blob + ids_off);
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < pad; b += gridDim.x * blockDim.x) {
     float* o = dst + (size_t)b * 8;
@@ -1105,7 +1118,7 @@ __global__ void kp_static_blob_kernel(unsigned char* blob, const float* raw, int
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     start[0] = 0;
-    start[1] = n;
+    start[1] = (uint16_t)n;
   }
 }
 

@@ -459,7 +459,7 @@ __device__ __forceinline__ int bp_cell(float v, float lo, float scale, int g) {
 // box is in one of the visited lists: the verdict equals testing every box.
 // 'tests' counts the box tests made.
 __device__ __forceinline__ bool hull_hits_grid(const KParams& P, const float4* __restrict__ sbox,
-                                               const int* __restrict__ sstart,
+                                               const uint16_t* __restrict__ sstart,
                                                const uint16_t* __restrict__ sids, float lx,
                                                float ly, float lz, float hx, float hy, float hz,
                                                uint32_t* tests) {

@@ -376,7 +376,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
   using Sys = System<SYS>;
   constexpr int D = Sys::D, N = Sys::N;
   const float4* sbox = reinterpret_cast<const float4*>(sblob);
-  const int* sstart = reinterpret_cast<const int*>(sblob + P.bp_start_off);
+  const uint16_t* sstart = reinterpret_cast<const uint16_t*>(sblob + P.bp_start_off);
   const uint16_t* sids = reinterpret_cast<const uint16_t*>(sblob + P.bp_ids_off);
   const uint32_t FULL = 0xffffffffu;
   const uint32_t lane = threadIdx.x & 31u;

@@ -210,3 +210,20 @@ def test_device_epoch_matches_step_loop(M):
     assert np.max(np.abs(pa - pb)) < 5e-3
     later = [a.train_epoch(X, T, perm, 1e-3) for _ in range(2)]
     assert later[-1] < loss_a
+
+
+def test_gradients_match_oracle_large_ragged_batch(M):
+    """A batch of 4133 rows (65 k tiles of the tensor-core weight-gradient
+    GEMMs over several splits, a partial last row tile): every parameter
+    block's gradient against the FP64 oracle."""
+    import torch
+    mlp, _ = M
+    p = mlp.init_params(12)
+    net = mlp.Mlp(p, max_batch=4200)
+    x, t = _data(4133, 13)
+    g, loss = net.gradients(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    ref_loss, ref = kpo.mlp_loss_grad(_oracle_params(p), _bf16(x), t.astype(np.float64))
+    assert abs(loss - ref_loss) <= 2e-2 * abs(ref_loss) + 1e-3
+    for blk_g, blk_r in zip(mlp.split(g), kpo.mlp_split(ref)):
+        err = np.linalg.norm(blk_g - blk_r) / max(np.linalg.norm(blk_r), 1e-12)
+        assert err < 3e-2, err
