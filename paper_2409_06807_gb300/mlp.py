@@ -166,7 +166,8 @@ def train(mlp, feats, targs, epochs=3, batch=4096, lr=1e-3, seed=0, log_every=0)
     g = torch.Generator(device="cpu").manual_seed(seed)
     hist = []
     for ep in range(epochs):
-        perm = torch.randperm(n, generator=g).to(feats.device)
+        # drawn as int32 on the host: only a copy reaches the device
+        perm = torch.randperm(n, generator=g, dtype=torch.int32).to(feats.device)
         if batch == mlp.max_batch:
             hist.append(mlp.train_epoch(feats, targs, perm, lr))
             continue
