@@ -99,31 +99,6 @@ struct ScanSmem {
   int warp[33];
 };
 
-// Exclusive rank of 'flag' among the block's threads in thread order; total
-// set in *total.  Must be called by every thread of the block.
-__device__ __forceinline__ int block_rank(bool flag, ScanSmem& sm, int* total) {
-  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-  const unsigned m = __ballot_sync(0xffffffffu, flag);
-  int r = __popc(m & ((1u << lane) - 1u));
-  if (lane == 0) sm.warp[w] = __popc(m);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    const int nw = blockDim.x >> 5;
-    for (int i = 0; i < nw; ++i) {
-      int c = sm.warp[i];
-      sm.warp[i] = acc;
-      acc += c;
-    }
-    sm.warp[32] = acc;
-  }
-  __syncthreads();
-  r += sm.warp[w];
-  *total = sm.warp[32];
-  __syncthreads();
-  return r;
-}
-
 // Exclusive prefix sum of one int per thread in thread order; total in
 // *total.  Must be called by every thread of the block.
 __device__ __forceinline__ int block_exclusive_scan(int v, ScanSmem& sm, int* total) {

@@ -4,24 +4,26 @@
 //
 // One pass of the loop body (Algorithm 1) runs as five grid phases separated
 // by bounded grid barriers, with no host involvement:
-//   E  Propagate (Algorithm 2): one thread per sample (V_E position, j);
-//      draw u and k, integrate k steps in FP32 registers, check each step
-//      against the state box and the obstacle boxes staged in shared memory,
-//      bin the end (or first invalid) state, count n_valid / n_invalid,
-//      claim newly reached sub-regions (smallest sample key wins) and keep
-//      the candidates' payload.
-//   A  accept flags per contiguous key chunk (representative or P_accept
-//      draw) and their per-block counts;
+//   E  Propagate (Algorithm 2): lanes carry one sample (V_E position, j)
+//      each and are refilled from a grid-wide key counter; draw u and k,
+//      integrate k steps in FP32 registers, check each step against the
+//      state box and the obstacle boxes staged in shared memory, bin the
+//      end (or first invalid) state, count n_valid / n_invalid, claim newly
+//      reached sub-regions (smallest sample key wins).
+//   A  accept decisions (representative or P_accept draw), accepted keys
+//      compacted per warp in key order; alongside, on warp 0:
 //   S  Score per region (Eq. 3-4, FP64, rounded exactly as written) and
 //      pairwise partial sums per aligned region chunk (Eq. 5's sum).
-//   P  append the accepted samples in key order (Algorithm 4, new nodes to
-//      T and V_E) with goal test;
+//   P  accepted keys copied to their place in key order; alongside:
 //   T  P_accept and the integer accept threshold per region (Eq. 5).
 //   N  one selection draw per old node against its region's new threshold
-//      (Algorithm 4, V_E <-> V_O) and per-block V_E counts;
+//      (Algorithm 4, V_E <-> V_O), per-block V_E counts, and the new nodes
+//      (Algorithm 4, to T and V_E) re-derived from their keys with the goal
+//      test.
 //   L  V_E list in ascending node id, lambda for the next pass (Eq. 6),
 //      stop decision.
-// Phases A+S and P+T share a barrier interval.
+// With a network attached (learned proposal) a phase F before E evaluates
+// it on every V_E node.
 #pragma once
 
 #include <cstdint>
@@ -120,21 +122,6 @@ __device__ __forceinline__ void chunk_of(const Team& T, int n, int* c0, int* c1)
 __device__ __forceinline__ void thread_run(int c0, int c1, int* r0, int* r1) {
   const int per = (c1 - c0 + (int)blockDim.x - 1) / (int)blockDim.x;
   const long long a = (long long)c0 + (long long)threadIdx.x * per;
-  *r0 = (int)(a < c1 ? a : c1);
-  *r1 = (int)(a + per < c1 ? a + per : c1);
-}
-
-// The accept and append phases run on warps 1.. of each block while warp 0
-// does the region estimates (FP64, long latency) alongside them.
-__device__ __forceinline__ void scan_run(int c0, int c1, int* r0, int* r1) {
-  const int nt = (int)blockDim.x - 32;
-  const int t = (int)threadIdx.x - 32;
-  if (t < 0) {
-    *r0 = *r1 = c0;
-    return;
-  }
-  const int per = (c1 - c0 + nt - 1) / nt;
-  const long long a = (long long)c0 + (long long)t * per;
   *r0 = (int)(a < c1 ? a : c1);
   *r1 = (int)(a + per < c1 ? a + per : c1);
 }
@@ -363,10 +350,10 @@ __device__ __forceinline__ int draw_sample(const KParams& P, uint32_t it, int ke
 // takes keys in batches from a grid-wide counter, every lane carries one
 // sample (k steps, or fewer when a step is invalid), and when enough lanes
 // of the warp have finished they are finalised (binning, counters, claim,
-// candidate payload) and given new keys together, so that the divergent
-// finalise / start-up work is shared by many lanes and no lane idles while
-// a long sample runs next to it.  Every sample's arithmetic depends on its
-// key alone, so the result does not depend on which lane ran it.
+// flags) and given new keys together, so that the divergent finalise /
+// start-up work is shared by many lanes and no lane idles while a long
+// sample runs next to it.  Every sample's arithmetic depends on its key
+// alone, so the result does not depend on which lane ran it.
 constexpr int KP_KEY_BATCH = 128; // keys a warp takes from the grid counter
 
 template <int SYS, bool LOG>
