@@ -358,6 +358,49 @@ def steady_state_leg(local, peak_ops, n_frontier=65536, reps=20):
                          "unit": "Top/s", "frac": achieved / peak_ops}}
 
 
+def te_sweep_leg(local, flush, n_layouts=20):
+    """Node-cap experiment (Sec. VI-C, Fig. 4) on the 12D quadrotor: for each
+    cap the failures within the pass budget, the solve time and the tree
+    size at the solution, on the same seeded building layouts; then the
+    adaptive cap (Remark 1) starting from the smallest one and doubling
+    whenever the tree fills without a solution."""
+    from paper_2409_06807_gb300 import planner as P
+    seeds = list(range(40_000, 40_000 + n_layouts))
+    caps = [1 << 15, 1 << 16, 1 << 17, 1 << 18, 1 << 19, 1 << 20]
+    rows = []
+    for cap in caps:
+        pl = P.Planner(W.c3(seeds[0], t_e=cap), device=f"cuda:{local}")
+        timed_query(pl, W.c3(seeds[0], t_e=cap), flush, MAX_ITERS)  # warm
+        res = [timed_query(pl, W.c3(s, t_e=cap), flush, MAX_ITERS) for s in seeds]
+        pl.close()
+        ok = [r for r in res if r[0] == P.OK]
+        rows.append({"t_e": cap, "failures": len(res) - len(ok),
+                     "p50_ms": float(np.median([r[1] for r in ok])) if ok else None,
+                     "mean_ms": float(np.mean([r[1] for r in ok])) if ok else None,
+                     "nodes_over_t_e": float(np.mean([r[2]["n_nodes"] for r in ok]) / cap)
+                     if ok else None})
+    import torch
+    ms, ok, grown = [], 0, []
+    for s in seeds:
+        pl = P.Planner(W.c3(s, t_e=caps[0]), device=f"cuda:{local}")
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, _, g = pl.plan_adaptive(max_iters=MAX_ITERS, growth=2.0, t_e_max=1 << 22)
+        torch.cuda.synchronize()
+        ms.append(1e3 * (time.perf_counter() - t0))
+        ok += st == P.OK
+        grown.append(g)
+        pl.close()
+    return {"workload": f"quadrotor building (1,200 boxes), {n_layouts} layouts (seeds "
+                        f"{seeds[0]}..{seeds[-1]}), {MAX_ITERS} passes",
+            "fixed_caps": rows,
+            "adaptive": {"start_t_e": caps[0], "growth": 2.0, "success": ok / len(seeds),
+                         "p50_wall_ms": float(np.median(ms)), "mean_growths": float(np.mean(grown)),
+                         "note": "wall time through the Python API: includes the arena "
+                                 "allocation and the device copy of each growth"}}
+
+
 def learned_leg(n_layouts, local, flush, peak_tflops):
     """Learned proposal against the plain planner on the Dubins forest: the
     network is trained on pairs harvested from plain runs (layout seeds from
@@ -554,6 +597,8 @@ def run_ours(args, world, rank, local):
     extra = {}
     if args.steady:
         extra["steady_state"] = steady_state_leg(local, peak_ops)
+    if args.te_layouts > 0:
+        extra["t_e_sweep"] = te_sweep_leg(local, flush, args.te_layouts)
     if args.learned_layouts > 0:
         extra["learned"] = learned_leg(args.learned_layouts, local, flush,
                                        float(pk.get("bf16_tflops", 1891.8)))
@@ -601,6 +646,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--learned-layouts", type=int, default=1000,
                     help="held-out layouts of the learned-vs-plain comparison (0: skip)")
+    ap.add_argument("--te-layouts", type=int, default=20,
+                    help="layouts of the node-cap sweep on the quadrotor (0: skip)")
     ap.add_argument("--serve-queries", type=int, default=512,
                     help="queries of the continuous-batching run (0: skip)")
     ap.add_argument("--serve-pool-gb", type=float, default=16.0,

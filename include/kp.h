@@ -275,6 +275,20 @@ kp_status kp_import_tree(kp_ctx *ctx, const kp_tree_view *host_in);
 /* Enables (log != NULL) or disables per-sample records of each pass.  A
  * pass with more samples than log->capacity records only the first
  * capacity samples. */
+/* Adaptive node cap (Sec. IV-A, Remark 1): moves the context to a larger
+ * caller-owned arena (kp_required_bytes with the new t_e; 256-byte
+ * aligned) and raises t_e, keeping the tree, the region and sub-region
+ * tables, the loop state and the staged obstacles (a device-to-device copy
+ * at HBM bandwidth; the tree's SoA rows move to the new stride).  The old
+ * arena is no longer used when the call returns.  t_e may not shrink.
+ * Typical use: kp_plan ends with KP_NO_SOLUTION and kp_get_info reports a
+ * full tree (state 2); grow by a constant factor and call kp_resume. */
+kp_status kp_grow(kp_ctx *ctx, void *dev_arena, size_t arena_bytes, int32_t t_e);
+/* Continues the loop (Algorithm 1) from the context's current tree until a
+ * goal node is appended, the tree is full (Eq. 6 gives lambda = 0) or the
+ * budget is spent, then fills traj as kp_plan does.  KP_ERR_STATE without
+ * a tree (kp_reset / kp_plan first). */
+kp_status kp_resume(kp_ctx *ctx, const kp_budget *budget, kp_traj *traj);
 kp_status kp_set_sample_log(kp_ctx *ctx, const kp_sample_log *log);
 
 /* Upper bound, in nanoseconds, of every device-side wait (grid barrier,

@@ -970,6 +970,119 @@ kp_status kp_import_tree(kp_ctx* ctx, const kp_tree_view* v) {
   return KP_OK;
 }
 
+kp_status kp_grow(kp_ctx* ctx, void* dev_arena, size_t arena_bytes, int32_t t_e) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (!dev_arena || ((uintptr_t)dev_arena & 255u)) return fail(ctx, KP_ERR_ARG, "bad arena");
+  if (ctx->plan_pending) return fail(ctx, KP_ERR_STATE, "kp_plan_result not called");
+  if (t_e < ctx->dims.t_e || t_e > (1 << 28)) return fail(ctx, KP_ERR_ARG, "bad node cap");
+  Dims nd = ctx->dims;
+  nd.t_e = t_e;
+  const Layout nl = make_layout(nd);
+  if (arena_bytes < nl.total) return fail(ctx, KP_ERR_OOM, "arena too small for the new node cap");
+  char* src = ctx->arena;
+  char* dst = static_cast<char*>(dev_arena);
+  const Layout& ol = ctx->lay;
+  const Dims& od = ctx->dims;
+  // the loop state, to know how many nodes to carry over
+  s = ensure_pinned(ctx, sizeof(KCtl));
+  if (s != KP_OK) return s;
+  KP_CUDA(cudaMemcpyAsync(ctx->pinned, src + ol.ctl, sizeof(KCtl), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  KCtl h;
+  std::memcpy(&h, ctx->pinned, sizeof(KCtl));
+  const size_t n = ctx->have_tree ? (size_t)h.n_nodes : 0;
+  auto d2d = [&](size_t dst_off, size_t src_off, size_t bytes) -> kp_status {
+    if (bytes)
+      KP_CUDA(cudaMemcpyAsync(dst + dst_off, src + src_off, bytes, cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+    return KP_OK;
+  };
+  // control region (loop state, barrier words; a tree that was full can
+  // grow again) and the staged obstacles
+  if (h.state == KP_DEV_FULL) h.state = KP_DEV_RUNNING;
+  std::memcpy(ctx->pinned, &h, sizeof(KCtl));
+  KP_CUDA(cudaMemcpyAsync(dst + nl.ctl, ctx->pinned, sizeof(KCtl), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  if ((s = d2d(nl.boxes, ol.boxes, (size_t)ctx->P.blob_bytes)) != KP_OK) return s;
+  // the tree: SoA rows move to the new stride
+  if (n) {
+    KP_CUDA(cudaMemcpy2DAsync(dst + nl.st, (size_t)nd.t_e * 4, src + ol.st, (size_t)od.t_e * 4,
+                              n * 4, (size_t)od.D, cudaMemcpyDeviceToDevice, ctx->stream));
+    KP_CUDA(cudaMemcpy2DAsync(dst + nl.ctrl, (size_t)nd.t_e * 4, src + ol.ctrl,
+                              (size_t)od.t_e * 4, n * 4, (size_t)od.N, cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+    if ((s = d2d(nl.parent, ol.parent, n * 4)) != KP_OK) return s;
+    if ((s = d2d(nl.steps, ol.steps, n)) != KP_OK) return s;
+    if ((s = d2d(nl.region, ol.region, n * 4)) != KP_OK) return s;
+    if ((s = d2d(nl.sub, ol.sub, n * 4)) != KP_OK) return s;
+    if ((s = d2d(nl.in_ve, ol.in_ve, n)) != KP_OK) return s;
+  }
+  // decomposition tables (sizes do not depend on the node cap)
+  if ((s = d2d(nl.n_valid, ol.n_valid, (size_t)od.R * 4)) != KP_OK) return s;
+  if ((s = d2d(nl.n_invalid, ol.n_invalid, (size_t)od.R * 4)) != KP_OK) return s;
+  if ((s = d2d(nl.cov, ol.cov, (size_t)od.R * 4)) != KP_OK) return s;
+  if ((s = d2d(nl.avail, ol.avail, (size_t)od.R)) != KP_OK) return s;
+  if ((s = d2d(nl.score, ol.score, (size_t)od.R * 8)) != KP_OK) return s;
+  if ((s = d2d(nl.thr, ol.thr, (size_t)od.R * 8)) != KP_OK) return s;
+  if ((s = d2d(nl.visited, ol.visited, od.n_sub)) != KP_OK) return s;
+  if ((s = d2d(nl.claim, ol.claim, od.n_sub * 4)) != KP_OK) return s;
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  // rebind: pointers from the new layout; what the layout does not give
+  // (staged obstacles, chunking, network, harvest) carries over
+  const KParams old = ctx->P;
+  ctx->prm.t_e = t_e;
+  fill_params(ctx->P, nd, nl, &ctx->sys, &ctx->ws, &ctx->prm, dst);
+  KParams& P = ctx->P;
+  P.n_boxes_pad = old.n_boxes_pad;
+  P.blob_bytes = old.blob_bytes;
+  P.bp_g = old.bp_g;
+  P.bp_start_off = old.bp_start_off;
+  P.bp_ids_off = old.bp_ids_off;
+  for (int a = 0; a < 3; ++a) P.bp_scale[a] = old.bp_scale[a];
+  P.nch = old.nch;
+  P.sd_bytes = old.sd_bytes;
+  P.mlp_W1 = old.mlp_W1;
+  P.mlp_b1 = old.mlp_b1;
+  P.mlp_W2 = old.mlp_W2;
+  P.mlp_b2 = old.mlp_b2;
+  P.mlp_W3 = old.mlp_W3;
+  P.mlp_b3 = old.mlp_b3;
+  P.mix_thr = old.mix_thr;
+  P.features_on = old.features_on;
+  P.hv_feat = old.hv_feat;
+  P.hv_target = old.hv_target;
+  P.hv_count = old.hv_count;
+  P.hv_cap = old.hv_cap;
+  ctx->dims = nd;
+  ctx->lay = nl;
+  ctx->arena = dst;
+  ctx->arena_bytes = arena_bytes;
+  return configure_launch(ctx);
+}
+
+kp_status kp_resume(kp_ctx* ctx, const kp_budget* budget, kp_traj* traj) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (!budget || !traj) return fail(ctx, KP_ERR_ARG, "null argument");
+  if (!ctx->have_tree) return fail(ctx, KP_ERR_STATE, "no tree: call kp_reset or kp_plan first");
+  if (ctx->plan_pending) return fail(ctx, KP_ERR_STATE, "kp_plan_result not called");
+  if (budget->max_iters < 1) return fail(ctx, KP_ERR_ARG, "max_iters must be >= 1");
+  if (traj->capacity < 0) return fail(ctx, KP_ERR_ARG, "negative capacity");
+  const int rows = traj->capacity < KP_TRAJ_ROWS ? traj->capacity : KP_TRAJ_ROWS;
+  s = ensure_pinned(ctx, sizeof(KCtl) + (size_t)rows * 17 * 4);
+  if (s != KP_OK) return s;
+  KParams P = params_now(ctx);
+  const uint64_t max_ns = budget->max_ms > 0.0 ? (uint64_t)(budget->max_ms * 1e6) : 0ull;
+  KP_CUDA(launch_loop(ctx, P, budget->max_iters, max_ns));
+  kp_extract_kernel<<<1, 32, 0, ctx->stream>>>(P);
+  KP_CUDA(cudaGetLastError());
+  ctx->plan_pending = true;
+  ctx->plan_rows = rows;
+  return kp_plan_result(ctx, traj);
+}
+
 kp_status kp_set_sample_log(kp_ctx* ctx, const kp_sample_log* log) {
   kp_status s = check_ctx(ctx);
   if (s != KP_OK) return s;

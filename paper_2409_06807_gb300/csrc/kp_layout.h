@@ -128,7 +128,7 @@ struct KParams {
   uint32_t seed_lo, seed_hi;
   // obstacles: a blob staged whole into shared memory:
   //   [n_boxes_pad][8] floats (lo.xyz, pad, hi.xyz, pad), then the
-  //   broad-phase grid: int32 cell_start[bp_g^3 + 1], uint16 ids[...]
+  //   broad-phase grid: uint16 cell_start[bp_g^3 + 1], uint16 ids[...]
   const float* boxes;
   int32_t n_boxes_pad;
   int32_t blob_bytes;

@@ -115,6 +115,8 @@ SIGNATURES = {
     "kp_get_info": (C.c_int, [_vp, C.POINTER(Info)]),
     "kp_export_tree": (C.c_int, [_vp, C.POINTER(TreeView)]),
     "kp_import_tree": (C.c_int, [_vp, C.POINTER(TreeView)]),
+    "kp_grow": (C.c_int, [_vp, _vp, C.c_size_t, C.c_int32]),
+    "kp_resume": (C.c_int, [_vp, C.POINTER(Budget), C.POINTER(Traj)]),
     "kp_set_sample_log": (C.c_int, [_vp, C.POINTER(SampleLog)]),
     "kp_set_wait_limit": (C.c_int, [_vp, C.c_uint64]),
     "kp_selftest_wait_timeout": (C.c_int, [_vp]),
@@ -302,6 +304,53 @@ class Planner:
         n = t.n_edges
         return st, dict(states=states[:n, : self.d], ctrls=ctrls[:n, : self.n_ctrl],
                         steps=steps[:n])
+
+    def grow(self, t_e):
+        """Raises the node cap to t_e (Remark 1): a new arena, the tree and
+        tables carried over by the device."""
+        import torch
+        L = lib()
+        prm = Params()
+        C.memmove(C.byref(prm), C.byref(self._prm), C.sizeof(Params))
+        prm.t_e = int(t_e)
+        nbytes = L.kp_required_bytes(C.byref(self._sys), C.byref(self._ws), self.box_capacity,
+                                     C.byref(prm))
+        if nbytes == 0:
+            raise KpError(ERR_ARG, "invalid node cap")
+        with torch.cuda.device(self.device):
+            arena = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        self._check(L.kp_grow(self._ctx, C.c_void_p(arena.data_ptr()), int(nbytes), int(t_e)),
+                    "kp_grow")
+        self.arena, self.arena_bytes, self._prm = arena, int(nbytes), prm
+        self.w = self.w.with_(t_e=int(t_e))
+
+    def resume(self, max_iters=1000, max_ms=0.0, capacity=4096):
+        """Continues planning from the current tree."""
+        states = np.zeros((capacity, 12), np.float32)
+        ctrls = np.zeros((capacity, 4), np.float32)
+        steps = np.zeros(capacity, np.int32)
+        t = Traj(capacity, 0, _fptr(states), _fptr(ctrls),
+                 steps.ctypes.data_as(C.POINTER(C.c_int32)))
+        b = Budget(int(max_iters), float(max_ms))
+        st = self._check(lib().kp_resume(self._ctx, C.byref(b), C.byref(t)), "kp_resume")
+        n = t.n_edges
+        return st, dict(states=states[:n, : self.d], ctrls=ctrls[:n, : self.n_ctrl],
+                        steps=steps[:n])
+
+    def plan_adaptive(self, max_iters=1000, growth=2.0, t_e_max=1 << 24, capacity=4096):
+        """Plans with the current node cap and, while the tree fills up
+        without reaching the goal, grows the cap by 'growth' and continues
+        (Remark 1).  Returns (status, trajectory, number of growths)."""
+        st, traj = self.plan(max_iters=max_iters, capacity=capacity)
+        grown = 0
+        while st == NO_SOLUTION and self.info()["state"] == 2 and self.w.t_e < t_e_max:
+            self.grow(min(int(self.w.t_e * growth), t_e_max))
+            grown += 1
+            left = max_iters - self.info()["iteration"]
+            if left < 1:
+                break
+            st, traj = self.resume(max_iters=left, capacity=capacity)
+        return st, traj, grown
 
     def plan_async(self, max_iters=1000, max_ms=0.0, capacity=4096, x_init=None, goal=None):
         """Enqueue a whole query on the stream; collect it with plan_result."""

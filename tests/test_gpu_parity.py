@@ -299,3 +299,60 @@ def test_boxes_on_cell_faces(P):
         boxes=boxes, x_init=np.array([0.03, 0.03, 0.5, 0, 0, 0], np.float32))
     exact, ran = lockstep(P, w, 8)
     assert exact >= min(ran, 3)
+
+
+def test_grow_keeps_tree_and_continues_in_lockstep(P):
+    """Remark 1 (adaptive node cap): the oracle fills a tree at t_e = 2048
+    (Eq. 6 gives lambda = 0); the device context holding it moves to a 4x
+    cap.  The tree, tables and loop state survive the move unchanged, and
+    the next pass matches the oracle continuing its own tree with the new
+    cap."""
+    w = W.c1(1, t_e=2048)
+    src = Oracle(w)
+    src.reset()
+    for _ in range(60):
+        status, _, _ = src.iterate()
+        if status != kpo.RUNNING:
+            break
+    assert status == kpo.FULL
+    t = src.export()
+    t["state"] = t["state"].astype(np.float32)
+    t["ctrl"] = t["ctrl"].astype(np.float32)
+    g = P.Planner(w)
+    g.import_tree(t)
+    st, _ = g.resume(max_iters=5)
+    assert st == P.NO_SOLUTION and g.info()["state"] == 2  # still full
+    g.grow(4 * w.t_e)
+    after = g.export_tree()
+    for key in ("parent", "steps", "region", "sub", "in_ve", "n_valid", "n_invalid", "thr",
+                "visited", "cov", "avail"):
+        assert np.array_equal(after[key], t[key]), key
+    assert np.array_equal(after["state"], t["state"]) and np.array_equal(after["ctrl"], t["ctrl"])
+    w2 = w.with_(t_e=4 * w.t_e)
+    o = Oracle(w2)
+    o.import_(t)
+    g.enable_log(w2.t_e)
+    status, ost, orec = o.iterate(records=True)
+    gs = g.expand_step(1)
+    assert len(gs) == 1 and ost["n_samples"] > 0
+    assert compare_pass(w2, ost, orec, gs[0], g.read_log(ost["n_samples"])) <= 2
+
+
+@pytest.mark.parametrize("seed", [0, 2])
+def test_plan_adaptive_revalidated(P, seed):
+    """A cap too small for the double-integrator query grows by 2x until a
+    goal node is reached; the trajectory re-validates under the oracle."""
+    w = W.c1(seed, t_e=2048)
+    g = P.Planner(w)
+    st, traj, grown = g.plan_adaptive(max_iters=400, growth=2.0, t_e_max=1 << 18)
+    assert st == P.OK and grown >= 1
+    o = Oracle(w)
+    scale = state_scale(w)
+    prev = w.x_init.astype(np.float64)
+    for e in range(len(traj["steps"])):
+        depth, x_end = o.dense_check(prev, traj["ctrls"][e].astype(np.float64),
+                                     int(traj["steps"][e]), 100)
+        assert depth <= 1e-4
+        assert np.max(np.abs(x_end - traj["states"][e]) / scale) <= 1e-4
+        prev = traj["states"][e].astype(np.float64)
+    assert np.linalg.norm(prev[:3] - w.goal_c) <= float(w.goal_r) * (1 + 1e-6)
