@@ -51,6 +51,10 @@ typedef struct {
   int32_t speed_bins;           /* >= 1 speed bins in the region index      */
   double speed_hi;              /* speeds binned over [0, speed_hi]         */
   int32_t sub[3];               /* sub-region cells per region and axis     */
+  int32_t state_grid[12];       /* cells over state dimension d >= 3 in the
+                                   region index (0 or 1: not decomposed);
+                                   an unbounded dimension (an angle) is
+                                   wrapped to [-pi, pi) first            */
   int32_t t_e;                  /* node cap (Sec. IV-A)                      */
   int32_t lambda_max;           /* Eq. 6                                     */
   double delta;                 /* Eq. 3                                     */

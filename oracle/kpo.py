@@ -32,7 +32,7 @@ class Config(C.Structure):
         ("phys", C.c_double * 16),
         ("ws_lo", C.c_double * 3), ("ws_hi", C.c_double * 3),
         ("grid", C.c_int32 * 3), ("speed_bins", C.c_int32),
-        ("speed_hi", C.c_double), ("sub", C.c_int32 * 3),
+        ("speed_hi", C.c_double), ("sub", C.c_int32 * 3), ("state_grid", C.c_int32 * 12),
         ("t_e", C.c_int32), ("lambda_max", C.c_int32),
         ("delta", C.c_double), ("eps", C.c_double),
         ("seed", C.c_uint64),
@@ -146,6 +146,8 @@ def make_config(w) -> Config:
         c.sub[i] = int(w.sub[i])
         c.goal_c[i] = float(w.goal_c[i])
     c.speed_bins = int(w.speed_bins)
+    for i in range(12):
+        c.state_grid[i] = int(w.state_grid[i])
     c.speed_hi = float(np.float32(w.speed_hi))
     c.t_e, c.lambda_max = int(w.t_e), int(w.lambda_max)
     c.delta, c.eps = float(w.delta), float(w.eps)

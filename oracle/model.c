@@ -24,8 +24,10 @@
  * counts as a collision.
  *
  * Binning (Sec. III, decomposition R and sub-regions R_i^k): a uniform grid
- * over the workspace position, optionally with speed bins in the region
- * index; each region holds a uniform sub-grid.
+ * over the workspace position, optionally with speed bins and with cells
+ * over further state dimensions in the region index (a grid over the whole
+ * state space, as in the paper's experiments, Sec. VI); each region holds a
+ * uniform sub-grid over position.
  */
 #include <math.h>
 #include <string.h>
@@ -268,8 +270,35 @@ void kpo_bin(const kpo *o, const double *x, int32_t *region, int32_t *sub,
     m /= (double)o->cfg.speed_bins;
     if (m < worst) worst = m;
   }
+  /* further state dimensions of a state-space grid, slowest in the index:
+   * e = c_3 + n_3 (c_4 + n_4 (...)) over the decomposed dimensions */
+  int e = 0, stride = 1;
+  for (int dd = 3; dd < o->d; ++dd) {
+    const int n = o->cfg.state_grid[dd];
+    if (n <= 1) continue;
+    double t;
+    if (isfinite(o->cfg.x_lo[dd]) && isfinite(o->cfg.x_hi[dd])) {
+      t = (x[dd] - o->cfg.x_lo[dd]) * ((double)n / (o->cfg.x_hi[dd] - o->cfg.x_lo[dd]));
+    } else {
+      const double pi = 3.14159265358979323846;
+      const double y = x[dd] - 2.0 * pi * floor((x[dd] + pi) / (2.0 * pi));
+      t = (y + pi) * ((double)n / (2.0 * pi));
+    }
+    double m;
+    const int c = cell_of(t, n, &m);
+    if (!(isfinite(o->cfg.x_lo[dd]) && isfinite(o->cfg.x_hi[dd]))) {
+      /* -pi and pi are the same face of a wrapped dimension */
+      if (t < m) m = t;
+      if ((double)n - t < m) m = (double)n - t;
+    }
+    m /= (double)n;
+    if (m < worst) worst = m;
+    e += stride * c;
+    stride *= n;
+  }
   int gx = o->cfg.grid[0], gy = o->cfg.grid[1], gz = o->cfg.grid[2];
-  int r = cell[0] + gx * (cell[1] + gy * (cell[2] + gz * sb));
+  const int nsb = o->cfg.speed_bins > 1 ? o->cfg.speed_bins : 1;
+  int r = cell[0] + gx * (cell[1] + gy * (cell[2] + gz * (sb + nsb * e)));
   int k = fine[0] + o->cfg.sub[0] * (fine[1] + o->cfg.sub[1] * fine[2]);
   *region = r;
   *sub = r * o->n_sub_per + k;

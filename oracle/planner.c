@@ -66,6 +66,10 @@ kpo *kpo_create(const kpo_config *cfg, const float *boxes, int32_t n_boxes) {
   int sb = cfg->speed_bins > 1 ? cfg->speed_bins : 1;
   o->cfg.speed_bins = sb;
   o->R = cfg->grid[0] * cfg->grid[1] * cfg->grid[2] * sb;
+  for (int dd = 0; dd < 12; ++dd) {
+    if (dd < 3 || dd >= o->d || o->cfg.state_grid[dd] < 1) o->cfg.state_grid[dd] = 1;
+    o->R *= o->cfg.state_grid[dd];
+  }
   o->n_sub_per = cfg->sub[0] * cfg->sub[1] * cfg->sub[2];
   o->n_sub = o->R * o->n_sub_per;
   o->vol = 1.0;

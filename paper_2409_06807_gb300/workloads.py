@@ -66,6 +66,9 @@ class Workload:
     goal_c: np.ndarray        # (3,) float32
     goal_r: np.float32
     extra: dict = field(default_factory=dict)
+    # cells over state dimension d >= 3 in the region index (0: position
+    # grid only); an unbounded dimension (an angle) is wrapped to [-pi, pi)
+    state_grid: tuple = (0,) * 12
 
     @property
     def d(self) -> int:

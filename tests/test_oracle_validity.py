@@ -177,3 +177,61 @@ def test_speed_bins():
         x[6:9] = (speed, 0, 0)
         r, _, _ = o.bin(x)
         assert r // 4096 == expect
+
+
+def test_state_grid_binning_by_hand():
+    """A grid over the Dubins state space (Sec. VI: grid dimension equal to
+    the state dimension): 2^3 position cells x 4 heading cells over
+    [-pi, pi) (the heading is wrapped) x 2 pitch cells over [-pi/6, pi/6] x
+    2 speed cells over [0.05, 0.2].  Cell centres land in the cell built by
+    hand from the mixed radix (position fastest, then heading, pitch,
+    speed); region count 8 * 16."""
+    sg = [0] * 12
+    sg[3], sg[4], sg[5] = 4, 2, 2
+    w = W.tiny(W.DUBINS, n_boxes=0, state_grid=tuple(sg))
+    o = Oracle(w)
+    assert o.R == 8 * 16
+    th = np.pi / 6
+    seen = set()
+    for cpos in range(8):
+        # centre of the first fine cell of position region cpos (2 x 2 x 2
+        # fine cells per region)
+        p = (2 * np.array([cpos % 2, (cpos // 2) % 2, cpos // 4]) + 0.5) / 4
+        for ch in range(4):
+            psi = -np.pi + (ch + 0.5) * (2 * np.pi / 4)
+            for cp in range(2):
+                pitch = -th + (cp + 0.5) * th
+                for cv in range(2):
+                    v = 0.05 + (cv + 0.5) * 0.075
+                    r, s, m = o.bin(np.array([*p, psi, pitch, v]))
+                    expect = cpos + 8 * (ch + 4 * (cp + 2 * cv))
+                    assert r == expect
+                    assert abs(m - 0.125) < 1e-12  # half a fine cell, half a heading cell
+                    seen.add(r)
+    assert seen == set(range(128))
+
+
+def test_state_grid_wraps_and_clamps():
+    sg = [0] * 12
+    sg[3], sg[4], sg[5] = 4, 2, 2
+    o = Oracle(W.tiny(W.DUBINS, n_boxes=0, state_grid=tuple(sg)))
+    base = np.array([0.1, 0.1, 0.1, 0.0, 0.0, 0.1])
+    # heading pi + 0.1 wraps to -pi + 0.1 (cell 0); -pi - 0.1 to pi - 0.1 (cell 3)
+    for psi, cell in ((np.pi + 0.1, 0), (-np.pi - 0.1, 3), (3 * np.pi + 0.2, 0), (0.01, 2)):
+        x = base.copy()
+        x[3] = psi
+        r, _, _ = o.bin(x)
+        assert (r // 8) % 4 == cell, (psi, r)
+    # the wrap point is a face of the heading cells
+    x = base.copy()
+    x[3] = np.pi - 1e-6
+    _, _, m = o.bin(x)
+    assert m < 1e-6
+    # pitch and speed clamp to their end cells outside the box
+    x = base.copy()
+    x[4], x[5] = 1.0, 0.5
+    r, _, _ = o.bin(x)
+    assert (r // 32) % 2 == 1 and r // 64 == 1
+    x[4], x[5] = -1.0, 0.0
+    r, _, _ = o.bin(x)
+    assert (r // 32) % 2 == 0 and r // 64 == 0
