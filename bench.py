@@ -401,6 +401,29 @@ def te_sweep_leg(local, flush, n_layouts=20):
                                  "allocation and the device copy of each growth"}}
 
 
+def decomposition_leg(local, flush, n_layouts=100):
+    """Decomposition choice (Sec. IV-B, Sec. VI): the Dubins forest with the
+    position grid of the benchmark (16^3 regions) against a grid over the
+    whole state (8^3 position cells x 4 heading x 2 pitch x 2 speed cells),
+    same layouts and random stream."""
+    from paper_2409_06807_gb300 import planner as P
+    sg = [0] * 12
+    sg[3], sg[4], sg[5] = 4, 2, 2
+    seeds = list(range(50_000, 50_000 + n_layouts))
+    out = {}
+    for name, kw in (("position_16^3", {}),
+                     ("state_8^3x4x2x2", {"grid": (8, 8, 8), "state_grid": tuple(sg)})):
+        make = lambda s: W.c2(s, **kw)
+        pl = P.Planner(make(seeds[0]), device=f"cuda:{local}")
+        timed_query(pl, make(seeds[0]), flush, MAX_ITERS)  # warm
+        rows = [timed_query(pl, make(s), flush, MAX_ITERS) for s in seeds]
+        pl.close()
+        out[name] = mode_summary(rows, P.OK)
+        out[name]["regions"] = rows[0][2]["n_regions"]
+    out["workload"] = f"Dubins forest (200 boxes), {n_layouts} layouts (seeds {seeds[0]}..{seeds[-1]})"
+    return out
+
+
 def learned_leg(n_layouts, local, flush, peak_tflops):
     """Learned proposal against the plain planner on the Dubins forest: the
     network is trained on pairs harvested from plain runs (layout seeds from
@@ -597,6 +620,8 @@ def run_ours(args, world, rank, local):
     extra = {}
     if args.steady:
         extra["steady_state"] = steady_state_leg(local, peak_ops)
+    if args.decomp_layouts > 0:
+        extra["decomposition"] = decomposition_leg(local, flush, args.decomp_layouts)
     if args.te_layouts > 0:
         extra["t_e_sweep"] = te_sweep_leg(local, flush, args.te_layouts)
     if args.learned_layouts > 0:
@@ -646,6 +671,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--learned-layouts", type=int, default=1000,
                     help="held-out layouts of the learned-vs-plain comparison (0: skip)")
+    ap.add_argument("--decomp-layouts", type=int, default=100,
+                    help="layouts of the decomposition comparison (0: skip)")
     ap.add_argument("--te-layouts", type=int, default=20,
                     help="layouts of the node-cap sweep on the quadrotor (0: skip)")
     ap.add_argument("--serve-queries", type=int, default=512,

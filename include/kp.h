@@ -72,13 +72,21 @@ typedef struct {
 
 /* Workspace W (Sec. II) and the decomposition R (Sec. III): a uniform grid
  * of grid[0]*grid[1]*grid[2] position cells times speed_bins speed bins over
- * [0, speed_hi]; every region holds sub[0]*sub[1]*sub[2] sub-regions. */
+ * [0, speed_hi] times state_grid[d] cells over each further state dimension
+ * d >= 3 with state_grid[d] > 1 (a grid over the whole state space, as in
+ * the paper's experiments, Sec. VI: a bounded dimension binned over
+ * [x_lo, x_hi], an unbounded one, an angle, wrapped to [-pi, pi) first);
+ * every region holds sub[0]*sub[1]*sub[2] sub-regions over position.
+ * Region index: position fastest, then the speed bin, then the further
+ * dimensions in increasing d. */
 typedef struct {
   float lo[3], hi[3];
   int32_t grid[3];
   int32_t speed_bins;         /* >= 1 (1: no speed bins)                    */
   float speed_hi;
   int32_t sub[3];
+  int32_t state_grid[12];     /* 0 or 1: dimension not decomposed; entries
+                                 0..2 and >= the state dimension ignored   */
 } kp_workspace;
 
 /* Obstacle set O (Sec. II): closed axis-aligned boxes, host pointer to

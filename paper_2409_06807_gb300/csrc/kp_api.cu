@@ -200,7 +200,11 @@ const char* check_inputs(const kp_system* sys, const kp_workspace* ws, int32_t n
   if (prm->t_e < 2 || prm->t_e > (1 << 28)) return "t_e out of range";
   if (prm->lambda_max < 1 || prm->lambda_max > 1024) return "lambda_max out of range";
   if (!(prm->delta > 0.0) || !(prm->eps > 0.0) || !(prm->eps < 1.0)) return "bad delta/eps";
-  const long long R = (long long)ws->grid[0] * ws->grid[1] * ws->grid[2] * ws->speed_bins;
+  long long R = (long long)ws->grid[0] * ws->grid[1] * ws->grid[2] * ws->speed_bins;
+  for (int dd = 3; dd < d->D; ++dd) {
+    if (ws->state_grid[dd] < 0 || ws->state_grid[dd] > 4096) return "bad state grid";
+    if (ws->state_grid[dd] > 1) R *= ws->state_grid[dd];
+  }
   const long long nsp = (long long)ws->sub[0] * ws->sub[1] * ws->sub[2];
   if (R > (1 << 24) || R * nsp > (1ll << 30)) return "decomposition too large";
   d->R = (int)R;
@@ -556,6 +560,20 @@ void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* 
     vol *= ((double)ws->hi[a] - (double)ws->lo[a]) / (double)ws->grid[a];
   }
   P.speed_bins = ws->speed_bins;
+  // further state dimensions of the region index (cells per unit of the
+  // dimension; an unbounded one is binned over [-pi, pi) after wrapping)
+  for (int dd = 0; dd < 12; ++dd) {
+    const int n = dd >= 3 && dd < d.D && ws->state_grid[dd] > 1 ? ws->state_grid[dd] : 1;
+    P.state_grid[dd] = n;
+    P.state_scale[dd] = 0.0f;
+    if (n > 1) {
+      const bool bounded = std::isfinite(sys->x_lo[dd]) && std::isfinite(sys->x_hi[dd]);
+      P.state_scale[dd] =
+          bounded ? (float)((double)n / ((double)sys->x_hi[dd] - (double)sys->x_lo[dd]))
+                  : (float)((double)n / (2.0 * 3.14159265358979323846));
+      P.state_wrap[dd] = bounded ? 0 : 1;
+    }
+  }
   P.speed_scale = ws->speed_bins > 1 ? (float)((double)ws->speed_bins / (double)ws->speed_hi) : 0.0f;
   P.n_sub_per = d.n_sub_per;
   P.R = d.R;

@@ -366,7 +366,28 @@ __device__ __forceinline__ void bin_state(const float* x, const KParams& P, int*
   int sb = 0;
   if (P.speed_bins > 1)
     sb = fine_cell(__fmul_rn(System<SYS>::speed(x), P.speed_scale), P.speed_bins);
-  const int r = cell[0] + P.grid[0] * (cell[1] + P.grid[1] * (cell[2] + P.grid[2] * sb));
+  // further state dimensions (a grid over the state space), slowest
+  int e = 0, stride = 1;
+#pragma unroll
+  for (int dd = 3; dd < System<SYS>::D; ++dd) {
+    const int n = P.state_grid[dd];
+    if (n > 1) {
+      float t;
+      if (P.state_wrap[dd]) {
+        const float pi = 3.14159265358979324f;
+        const float turns = floorf(__fmul_rn(__fadd_rn(x[dd], pi), 0.159154943091895336f));
+        const float y = __fsub_rn(x[dd], __fmul_rn(turns, 6.28318530717958648f));
+        t = __fmul_rn(__fadd_rn(y, pi), P.state_scale[dd]);
+      } else {
+        t = __fmul_rn(__fsub_rn(x[dd], P.x_lo[dd]), P.state_scale[dd]);
+      }
+      e += stride * fine_cell(t, n);
+      stride *= n;
+    }
+  }
+  const int nsb = P.speed_bins > 1 ? P.speed_bins : 1;
+  const int r =
+      cell[0] + P.grid[0] * (cell[1] + P.grid[1] * (cell[2] + P.grid[2] * (sb + nsb * e)));
   const int k = fine[0] + P.sub[0] * (fine[1] + P.sub[1] * fine[2]);
   *region = r;
   *sub = r * P.n_sub_per + k;

@@ -114,6 +114,9 @@ struct KParams {
   int32_t grid[3];
   int32_t speed_bins;
   float speed_scale;    // speed_bins / speed_hi
+  int32_t state_grid[12];  // cells over state dimension d (1: not decomposed)
+  float state_scale[12];   // cells per unit of that dimension
+  int32_t state_wrap[12];  // 1: an angle, wrapped to [-pi, pi) before binning
   int32_t n_sub_per;    // n'
   int32_t R;            // regions
   int32_t R_pad;        // next power of two >= R

@@ -37,7 +37,8 @@ class System(C.Structure):
 
 class Workspace(C.Structure):
     _fields_ = [("lo", C.c_float * 3), ("hi", C.c_float * 3), ("grid", C.c_int32 * 3),
-                ("speed_bins", C.c_int32), ("speed_hi", C.c_float), ("sub", C.c_int32 * 3)]
+                ("speed_bins", C.c_int32), ("speed_hi", C.c_float), ("sub", C.c_int32 * 3),
+                ("state_grid", C.c_int32 * 12)]
 
 
 class Obstacles(C.Structure):
@@ -194,6 +195,8 @@ def structs(w):
         ws.grid[a] = int(w.grid[a])
         ws.sub[a] = int(w.sub[a])
     ws.speed_bins = int(w.speed_bins)
+    for i in range(12):
+        ws.state_grid[i] = int(w.state_grid[i])
     ws.speed_hi = float(w.speed_hi)
     p = Params()
     p.t_e, p.lambda_max = int(w.t_e), int(w.lambda_max)

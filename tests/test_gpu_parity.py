@@ -356,3 +356,29 @@ def test_plan_adaptive_revalidated(P, seed):
         assert np.max(np.abs(x_end - traj["states"][e]) / scale) <= 1e-4
         prev = traj["states"][e].astype(np.float64)
     assert np.linalg.norm(prev[:3] - w.goal_c) <= float(w.goal_r) * (1 + 1e-6)
+
+
+def _state_grid(**cells):
+    sg = [0] * 12
+    for d, n in cells.items():
+        sg[int(d[1:])] = n
+    return tuple(sg)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lockstep_tiny_state_grid(P, seed):
+    """Regions over the whole Dubins state (Sec. VI): 2^3 position cells x
+    4 heading cells (wrapped angle) x 2 pitch x 2 speed cells."""
+    w = W.tiny(W.DUBINS, seed=seed, t_e=2000, lambda_max=8,
+               state_grid=_state_grid(d3=4, d4=2, d5=2))
+    exact, ran = lockstep(P, w, 12)
+    assert exact >= min(ran, 3)
+
+
+def test_frontier_c2_state_grid(P):
+    """The Dubins forest with an 8^3 x 4 x 2 x 2 state-space grid (8,192
+    regions, 524,288 sub-regions): one pass over the oracle's 3-pass tree."""
+    w = W.c2(0, grid=(8, 8, 8), state_grid=_state_grid(d3=4, d4=2, d5=2))
+    flips, ost = frontier(P, w, grow=2)
+    assert ost["n_samples"] > 10000
+    assert flips <= 2
