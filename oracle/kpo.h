@@ -51,6 +51,11 @@ typedef struct {
   int32_t speed_bins;           /* >= 1 speed bins in the region index      */
   double speed_hi;              /* speeds binned over [0, speed_hi]         */
   int32_t sub[3];               /* sub-region cells per region and axis     */
+  int32_t fso;                  /* 1: regions are the leaves of a kd-tree
+                                   split on obstacle faces (a free-space-
+                                   obeying decomposition, Sec. IV-B); the
+                                   position grid, speed bins and state grid
+                                   are then unused                        */
   int32_t state_grid[12];       /* cells over state dimension d >= 3 in the
                                    region index (0 or 1: not decomposed);
                                    an unbounded dimension (an angle) is
@@ -183,6 +188,17 @@ void kpo_eq345(int32_t n, const uint32_t *n_valid, const uint32_t *n_invalid,
                const uint32_t *cov, const uint8_t *avail, double vol,
                double delta, double eps, double *score, double *p_accept,
                uint64_t *thr, double *score_sum);
+/* The same with a volume per region (vol_r[i]; the free-space-obeying
+ * decomposition, whose regions differ in size). */
+void kpo_eq345_vol(int32_t n, const uint32_t *n_valid, const uint32_t *n_invalid,
+                   const uint32_t *cov, const uint8_t *avail, const double *vol_r,
+                   double delta, double eps, double *score, double *p_accept,
+                   uint64_t *thr, double *score_sum);
+/* Regions of the free-space-obeying decomposition (capacity). */
+#define KPO_FSO_MAX_LEAVES 16384
+/* Leaf boxes of that decomposition in region order (lo/hi: [cap][3]);
+ * returns the number of leaves (0 when the regions are a grid). */
+int32_t kpo_fso_leaves(const kpo *o, double *lo, double *hi, int32_t cap);
 /* Eq. 6. */
 int32_t kpo_lambda(int32_t t_e, int32_t n_tree, int32_t n_ve,
                    int32_t lambda_max);

@@ -32,7 +32,8 @@ class Config(C.Structure):
         ("phys", C.c_double * 16),
         ("ws_lo", C.c_double * 3), ("ws_hi", C.c_double * 3),
         ("grid", C.c_int32 * 3), ("speed_bins", C.c_int32),
-        ("speed_hi", C.c_double), ("sub", C.c_int32 * 3), ("state_grid", C.c_int32 * 12),
+        ("speed_hi", C.c_double), ("sub", C.c_int32 * 3), ("fso", C.c_int32),
+        ("state_grid", C.c_int32 * 12),
         ("t_e", C.c_int32), ("lambda_max", C.c_int32),
         ("delta", C.c_double), ("eps", C.c_double),
         ("seed", C.c_uint64),
@@ -120,6 +121,11 @@ def lib():
         L.kpo_harvest_count.restype = C.c_int32
         L.kpo_harvest_count.argtypes = [vp]
         L.kpo_box_muller.argtypes = [_u32p, _f64p]
+        L.kpo_fso_leaves.restype = C.c_int32
+        L.kpo_fso_leaves.argtypes = [vp, _f64p, _f64p, C.c_int32]
+        L.kpo_eq345_vol.argtypes = [C.c_int32, _u32p, _u32p, _u32p, _u8p, _f64p,
+                                    C.c_double, C.c_double, _f64p, _f64p, _u64p,
+                                    C.POINTER(C.c_double)]
         L.kpo_dense_check.restype = C.c_double
         L.kpo_dense_check.argtypes = [vp, _f64p, _f64p, C.c_int32, C.c_int32, _f64p]
         _lib = L
@@ -148,6 +154,7 @@ def make_config(w) -> Config:
     c.speed_bins = int(w.speed_bins)
     for i in range(12):
         c.state_grid[i] = int(w.state_grid[i])
+    c.fso = 1 if getattr(w, "fso", False) else 0
     c.speed_hi = float(np.float32(w.speed_hi))
     c.t_e, c.lambda_max = int(w.t_e), int(w.lambda_max)
     c.delta, c.eps = float(w.delta), float(w.eps)
@@ -173,6 +180,22 @@ def eq345(n_valid, n_invalid, cov, avail, vol, delta, eps):
                     np.ascontiguousarray(cov, np.uint32),
                     np.ascontiguousarray(avail, np.uint8), vol, delta, eps,
                     score, p, thr, C.byref(s))
+    return score, p, thr, s.value
+
+
+def eq345_vol(n_valid, n_invalid, cov, avail, vol_r, delta, eps):
+    """Eq. 3-5 with a volume per region."""
+    n = len(n_valid)
+    score = np.zeros(n)
+    p = np.zeros(n)
+    thr = np.zeros(n, np.uint64)
+    s = C.c_double()
+    lib().kpo_eq345_vol(n, np.ascontiguousarray(n_valid, np.uint32),
+                        np.ascontiguousarray(n_invalid, np.uint32),
+                        np.ascontiguousarray(cov, np.uint32),
+                        np.ascontiguousarray(avail, np.uint8),
+                        np.ascontiguousarray(vol_r, np.float64), delta, eps,
+                        score, p, thr, C.byref(s))
     return score, p, thr, s.value
 
 
@@ -388,6 +411,14 @@ class Oracle:
         lib().kpo_bin(self._h, np.asarray(x, np.float64), C.byref(r), C.byref(s),
                       C.byref(m))
         return r.value, s.value, m.value
+
+    def fso_leaves(self):
+        """Leaf boxes (lo, hi), each (n_leaves, 3), of the free-space-obeying
+        decomposition in region order; None for a grid."""
+        lo = np.zeros((16384, 3))
+        hi = np.zeros((16384, 3))
+        n = lib().kpo_fso_leaves(self._h, lo, hi, 16384)
+        return (lo[:n], hi[:n]) if n else None
 
     def features(self, v) -> np.ndarray:
         f = np.zeros(32)

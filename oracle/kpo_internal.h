@@ -14,6 +14,13 @@ struct kpo {
   int n_sub_per;           /* sub-regions per region (n')                 */
   int n_sub;               /* R * n'                                      */
   double vol;              /* workspace volume of one region (Eq. 3)      */
+  /* free-space-obeying decomposition: a kd-tree whose leaves are the
+   * regions; node i: axis (3 = leaf), split, right child (left = i + 1) */
+  int kd_n, kd_cap, n_leaves;
+  int *kd_axis, *kd_right, *kd_leaf;
+  double *kd_split;
+  double *leaf_lo, *leaf_hi; /* [n_leaves][3]                             */
+  double *region_vol;        /* [R] volume of each region, NULL for grids */
   double *boxes;           /* [nb][6]: lo xyz, hi xyz                     */
   int nb;
 
@@ -45,5 +52,9 @@ struct kpo {
   double *hv_feat, *hv_target;
   int hv_cap, hv_count;
 };
+
+/* Builds the kd-tree of the free-space-obeying decomposition from the
+ * obstacles (model.c).  Returns 0, or -1 past KPO_FSO_MAX_LEAVES leaves. */
+int kpo_build_fso(kpo *o);
 
 #endif

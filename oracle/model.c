@@ -30,6 +30,7 @@
  * uniform sub-grid over position.
  */
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "kpo_internal.h"
@@ -247,8 +248,155 @@ static double speed_of(const kpo *o, const double *x) {
   }
 }
 
+/* ------------------------------------------------------------------ */
+/* free-space-obeying decomposition (Sec. IV-B)                         */
+/* ------------------------------------------------------------------ */
+
+/* The regions are the leaves of a kd-tree over the workspace whose
+ * splitting planes are obstacle faces.  A cell is split while some face of
+ * a box that meets the cell's interior lies strictly inside it: on the axis
+ * with the most distinct such face coordinates (the lowest axis on a tie),
+ * at the lower median of them.  A leaf therefore has no obstacle face
+ * crossing it, so it is either inside an obstacle or free of every one.
+ * Nodes are numbered in depth-first pre-order, the left child (the side
+ * below the plane) right after its parent; leaves are numbered in the same
+ * order. */
+
+static int cmp_double(const void *a, const void *b) {
+  const double x = *(const double *)a, y = *(const double *)b;
+  return (x > y) - (x < y);
+}
+
+static int kd_push(kpo *o) {
+  if (o->kd_n == o->kd_cap) {
+    const int cap = o->kd_cap ? 2 * o->kd_cap : 64;
+    o->kd_axis = (int *)realloc(o->kd_axis, sizeof(int) * (size_t)cap);
+    o->kd_right = (int *)realloc(o->kd_right, sizeof(int) * (size_t)cap);
+    o->kd_leaf = (int *)realloc(o->kd_leaf, sizeof(int) * (size_t)cap);
+    o->kd_split = (double *)realloc(o->kd_split, sizeof(double) * (size_t)cap);
+    o->kd_cap = cap;
+  }
+  return o->kd_n++;
+}
+
+static int kd_build(kpo *o, const double lo[3], const double hi[3], double *cand) {
+  const int node = kd_push(o);
+  int best_axis = -1, best_m = 0;
+  double split = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    int m = 0;
+    for (int b = 0; b < o->nb; ++b) {
+      const double *bx = o->boxes + 6 * (size_t)b;
+      int meets = 1;
+      for (int c = 0; c < 3; ++c)
+        if (!(bx[c] < hi[c] && bx[3 + c] > lo[c])) meets = 0;
+      if (!meets) continue;
+      for (int s = 0; s < 2; ++s) {
+        const double f = bx[3 * s + a];
+        if (f > lo[a] && f < hi[a]) cand[m++] = f;
+      }
+    }
+    qsort(cand, (size_t)m, sizeof(double), cmp_double);
+    int u = 0;
+    for (int i = 0; i < m; ++i)
+      if (u == 0 || cand[i] != cand[u - 1]) cand[u++] = cand[i];
+    if (u > best_m) {
+      best_m = u;
+      best_axis = a;
+      split = cand[(u - 1) / 2];
+    }
+  }
+  if (best_axis < 0) {
+    if (o->n_leaves == KPO_FSO_MAX_LEAVES) return -1;
+    const int leaf = o->n_leaves++;
+    o->kd_axis[node] = 3;
+    o->kd_leaf[node] = leaf;
+    o->kd_right[node] = -1;
+    o->kd_split[node] = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      o->leaf_lo[3 * leaf + a] = lo[a];
+      o->leaf_hi[3 * leaf + a] = hi[a];
+    }
+    return 0;
+  }
+  o->kd_axis[node] = best_axis;
+  o->kd_leaf[node] = -1;
+  o->kd_split[node] = split;
+  double clo[3], chi[3];
+  memcpy(clo, lo, sizeof clo);
+  memcpy(chi, hi, sizeof chi);
+  chi[best_axis] = split;
+  if (kd_build(o, clo, chi, cand) != 0) return -1;
+  o->kd_right[node] = o->kd_n;
+  memcpy(chi, hi, sizeof chi);
+  clo[best_axis] = split;
+  return kd_build(o, clo, chi, cand);
+}
+
+int kpo_build_fso(kpo *o) {
+  o->leaf_lo = (double *)calloc(3 * (size_t)KPO_FSO_MAX_LEAVES, sizeof(double));
+  o->leaf_hi = (double *)calloc(3 * (size_t)KPO_FSO_MAX_LEAVES, sizeof(double));
+  double *cand = (double *)malloc(sizeof(double) * (size_t)(2 * o->nb + 1));
+  o->n_leaves = 0;
+  o->kd_n = 0;
+  const int rc = kd_build(o, o->cfg.ws_lo, o->cfg.ws_hi, cand);
+  free(cand);
+  if (rc != 0) return -1;
+  /* Eq. 3's vol: each leaf's own workspace volume */
+  o->region_vol = (double *)calloc((size_t)o->n_leaves, sizeof(double));
+  for (int r = 0; r < o->n_leaves; ++r)
+    o->region_vol[r] = (o->leaf_hi[3 * r] - o->leaf_lo[3 * r]) *
+                       (o->leaf_hi[3 * r + 1] - o->leaf_lo[3 * r + 1]) *
+                       (o->leaf_hi[3 * r + 2] - o->leaf_lo[3 * r + 2]);
+  return 0;
+}
+
+int32_t kpo_fso_leaves(const kpo *o, double *lo, double *hi, int32_t cap) {
+  if (!o->cfg.fso) return 0;
+  for (int r = 0; r < o->n_leaves && r < cap; ++r)
+    for (int a = 0; a < 3; ++a) {
+      lo[3 * r + a] = o->leaf_lo[3 * r + a];
+      hi[3 * r + a] = o->leaf_hi[3 * r + a];
+    }
+  return o->n_leaves;
+}
+
+/* Leaf of position p (descend: below the plane goes left) and the sub-grid
+ * cell inside it; *margin = the nearest face crossed on the way or of the
+ * sub-grid, in units of the workspace extent along its axis. */
+static void bin_fso(const kpo *o, const double *x, int32_t *region, int32_t *sub,
+                    double *margin) {
+  double worst = INFINITY;
+  int node = 0;
+  while (o->kd_axis[node] != 3) {
+    const int a = o->kd_axis[node];
+    const double s = o->kd_split[node];
+    const double m = fabs(x[a] - s) / (o->cfg.ws_hi[a] - o->cfg.ws_lo[a]);
+    if (m < worst || isnan(m)) worst = isnan(m) ? 0.0 : m;
+    node = x[a] < s ? node + 1 : o->kd_right[node];
+  }
+  const int r = o->kd_leaf[node];
+  int fine[3];
+  for (int a = 0; a < 3; ++a) {
+    const int n = o->cfg.sub[a];
+    const double lo = o->leaf_lo[3 * r + a], hi = o->leaf_hi[3 * r + a];
+    double m;
+    fine[a] = cell_of((x[a] - lo) * ((double)n / (hi - lo)), n, &m);
+    m *= (hi - lo) / (double)n / (o->cfg.ws_hi[a] - o->cfg.ws_lo[a]);
+    if (m < worst) worst = m;
+  }
+  const int k = fine[0] + o->cfg.sub[0] * (fine[1] + o->cfg.sub[1] * fine[2]);
+  *region = r;
+  *sub = r * o->n_sub_per + k;
+  if (margin) *margin = worst;
+}
+
 void kpo_bin(const kpo *o, const double *x, int32_t *region, int32_t *sub,
              double *margin) {
+  if (o->cfg.fso) {
+    bin_fso(o, x, region, sub, margin);
+    return;
+  }
   int cell[3], fine[3];
   double worst = INFINITY;
   for (int a = 0; a < 3; ++a) {

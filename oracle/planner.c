@@ -71,13 +71,21 @@ kpo *kpo_create(const kpo_config *cfg, const float *boxes, int32_t n_boxes) {
     o->R *= o->cfg.state_grid[dd];
   }
   o->n_sub_per = cfg->sub[0] * cfg->sub[1] * cfg->sub[2];
-  o->n_sub = o->R * o->n_sub_per;
   o->vol = 1.0;
   for (int a = 0; a < 3; ++a)
     o->vol *= (cfg->ws_hi[a] - cfg->ws_lo[a]) / (double)cfg->grid[a];
   o->nb = n_boxes;
   o->boxes = (double *)xcalloc((size_t)n_boxes * 6, sizeof(double));
   for (int i = 0; i < 6 * n_boxes; ++i) o->boxes[i] = (double)boxes[i];
+  if (cfg->fso) {
+    /* the regions are the kd-tree's leaves, each with its own volume */
+    if (kpo_build_fso(o) != 0) {
+      kpo_destroy(o);
+      return NULL;
+    }
+    o->R = o->n_leaves;
+  }
+  o->n_sub = o->R * o->n_sub_per;
   size_t te = (size_t)cfg->t_e;
   o->x = (double *)xcalloc(te * o->d, sizeof(double));
   o->parent = (int *)xcalloc(te, sizeof(int));
@@ -105,6 +113,8 @@ void kpo_destroy(kpo *o) {
   free(o->region); free(o->sub); free(o->in_ve); free(o->n_valid);
   free(o->n_invalid); free(o->cov); free(o->avail); free(o->visited);
   free(o->score); free(o->p_accept); free(o->thr); free(o->mlp);
+  free(o->kd_axis); free(o->kd_right); free(o->kd_leaf); free(o->kd_split);
+  free(o->leaf_lo); free(o->leaf_hi); free(o->region_vol);
   free(o);
 }
 
@@ -123,9 +133,21 @@ void kpo_eq345(int32_t n, const uint32_t *n_valid, const uint32_t *n_invalid,
                const uint32_t *cov, const uint8_t *avail, double vol,
                double delta, double eps, double *score, double *p_accept,
                uint64_t *thr, double *score_sum) {
+  double *v = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int i = 0; i < n; ++i) v[i] = vol;
+  kpo_eq345_vol(n, n_valid, n_invalid, cov, avail, v, delta, eps, score, p_accept, thr,
+                score_sum);
+  free(v);
+}
+
+void kpo_eq345_vol(int32_t n, const uint32_t *n_valid, const uint32_t *n_invalid,
+                   const uint32_t *cov, const uint8_t *avail, const double *vol_r,
+                   double delta, double eps, double *score, double *p_accept,
+                   uint64_t *thr, double *score_sum) {
   for (int i = 0; i < n; ++i) {
     score[i] = 0.0;
     if (!avail[i]) continue;
+    const double vol = vol_r[i];
     double nv = (double)n_valid[i], ni = (double)n_invalid[i];
     /* Eq. 3: FreeVol = (delta + n_valid) vol / (delta + n_valid + n_invalid) */
     double freevol = ((delta + nv) * vol) / ((delta + nv) + ni);
@@ -198,8 +220,12 @@ static void update_estimates(kpo *o) {
     nv[r] = (uint32_t)o->n_valid[r];
     ni[r] = (uint32_t)o->n_invalid[r];
   }
-  kpo_eq345(o->R, nv, ni, o->cov, o->avail, o->vol, o->cfg.delta, o->cfg.eps,
-            o->score, o->p_accept, o->thr, &o->score_sum);
+  if (o->region_vol)
+    kpo_eq345_vol(o->R, nv, ni, o->cov, o->avail, o->region_vol, o->cfg.delta, o->cfg.eps,
+                  o->score, o->p_accept, o->thr, &o->score_sum);
+  else
+    kpo_eq345(o->R, nv, ni, o->cov, o->avail, o->vol, o->cfg.delta, o->cfg.eps,
+              o->score, o->p_accept, o->thr, &o->score_sum);
   free(nv);
   free(ni);
 }
@@ -236,7 +262,9 @@ void kpo_features(const kpo *o, int32_t v, double *f) {
   f[11] = log1p(nv);
   f[12] = log1p(ni);
   f[13] = (double)o->thr[r] / TWO32;
-  /* face neighbours in the position grid, same speed bin */
+  /* face neighbours in the position grid, same speed bin (none when the
+   * regions are kd-tree leaves) */
+  if (o->cfg.fso) return;
   const int gx = o->cfg.grid[0], gy = o->cfg.grid[1], gz = o->cfg.grid[2];
   const int cx = r % gx, cy = (r / gx) % gy, cz = (r / (gx * gy)) % gz;
   const int sb = r / (gx * gy * gz);

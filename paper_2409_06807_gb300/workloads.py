@@ -69,6 +69,10 @@ class Workload:
     # cells over state dimension d >= 3 in the region index (0: position
     # grid only); an unbounded dimension (an angle) is wrapped to [-pi, pi)
     state_grid: tuple = (0,) * 12
+    # regions are the leaves of a kd-tree split on obstacle faces (a
+    # free-space-obeying decomposition); grid, speed bins and state grid
+    # are then unused, sub is the sub-grid inside each leaf
+    fso: bool = False
 
     @property
     def d(self) -> int:
