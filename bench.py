@@ -289,7 +289,9 @@ def timed_query(pl, w, flush, max_iters, cap=4096):
     """One query through the single-query launch, L2 flushed first; returns
     (status, device ms from the reset to the trajectory, info)."""
     import torch
+    t0 = time.perf_counter()
     pl.set_obstacles(w.boxes)
+    t_set = (time.perf_counter() - t0) * 1e3
     pl.w = w
     flush.zero_()
     torch.cuda.synchronize()
@@ -299,7 +301,9 @@ def timed_query(pl, w, flush, max_iters, cap=4096):
     pl.plan_async(max_iters=max_iters, capacity=cap)
     e1.record(pl.stream)
     st, _ = pl.plan_result()
-    return st, e0.elapsed_time(e1), pl.info()
+    info = pl.info()
+    info["set_obstacles_ms"] = t_set
+    return st, e0.elapsed_time(e1), info
 
 
 def mode_summary(rows, ok_status):
@@ -309,7 +313,8 @@ def mode_summary(rows, ok_status):
     return {"success": sum(r[0] == ok_status for r in rows) / len(rows),
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "mean_ms": float(ms.mean()), "samples_per_s": samples / (ms.sum() / 1e3),
-            "mean_samples": samples / len(rows), "steps_per_sample": steps / max(1, samples)}
+            "mean_samples": samples / len(rows), "steps_per_sample": steps / max(1, samples),
+            "set_obstacles_ms": float(np.mean([r[2]["set_obstacles_ms"] for r in rows]))}
 
 
 def steady_state_leg(local, peak_ops, n_frontier=65536, reps=20):
@@ -404,22 +409,25 @@ def te_sweep_leg(local, flush, n_layouts=20):
 def decomposition_leg(local, flush, n_layouts=100):
     """Decomposition choice (Sec. IV-B, Sec. VI): the Dubins forest with the
     position grid of the benchmark (16^3 regions) against a grid over the
-    whole state (8^3 position cells x 4 heading x 2 pitch x 2 speed cells),
-    same layouts and random stream."""
+    whole state (8^3 position cells x 4 heading x 2 pitch x 2 speed cells)
+    and against a free-space-obeying decomposition (kd-tree leaves split on
+    obstacle faces, built on the host by kp_set_obstacles, whose time is
+    reported apart from the query's), same layouts and random stream."""
     from paper_2409_06807_gb300 import planner as P
     sg = [0] * 12
     sg[3], sg[4], sg[5] = 4, 2, 2
     seeds = list(range(50_000, 50_000 + n_layouts))
     out = {}
     for name, kw in (("position_16^3", {}),
-                     ("state_8^3x4x2x2", {"grid": (8, 8, 8), "state_grid": tuple(sg)})):
+                     ("state_8^3x4x2x2", {"grid": (8, 8, 8), "state_grid": tuple(sg)}),
+                     ("kd_tree_fso", {"fso": True})):
         make = lambda s: W.c2(s, **kw)
         pl = P.Planner(make(seeds[0]), device=f"cuda:{local}")
         timed_query(pl, make(seeds[0]), flush, MAX_ITERS)  # warm
         rows = [timed_query(pl, make(s), flush, MAX_ITERS) for s in seeds]
         pl.close()
         out[name] = mode_summary(rows, P.OK)
-        out[name]["regions"] = rows[0][2]["n_regions"]
+        out[name]["regions"] = float(np.mean([r[2]["n_regions"] for r in rows]))
     out["workload"] = f"Dubins forest (200 boxes), {n_layouts} layouts (seeds {seeds[0]}..{seeds[-1]})"
     return out
 

@@ -78,7 +78,19 @@ typedef struct {
  * [x_lo, x_hi], an unbounded one, an angle, wrapped to [-pi, pi) first);
  * every region holds sub[0]*sub[1]*sub[2] sub-regions over position.
  * Region index: position fastest, then the speed bin, then the further
- * dimensions in increasing d. */
+ * dimensions in increasing d.
+ * fso = 1 replaces the grid by a free-space-obeying decomposition (Sec.
+ * IV-B): the regions are the leaves of a kd-tree over W whose planes are
+ * obstacle faces.  A cell is split while a face of a box meeting its
+ * interior lies strictly inside it: on the axis with the most distinct such
+ * coordinates (the lowest axis on a tie), at the lower median of them; so
+ * every leaf lies inside an obstacle or meets none.  Leaves are numbered
+ * depth first, the side below each plane first (a point on a plane goes
+ * above it); each holds a sub[0]*sub[1]*sub[2] sub-grid over its own box,
+ * and Eq. 3 takes its own volume.  grid, speed_bins and state_grid are then
+ * ignored.  The tree is rebuilt by kp_set_obstacles; at most 16,384 leaves
+ * and depth 64 (KP_ERR_ARG beyond).  Not available in kp_plan_static or
+ * the server. */
 typedef struct {
   float lo[3], hi[3];
   int32_t grid[3];
@@ -87,6 +99,7 @@ typedef struct {
   int32_t sub[3];
   int32_t state_grid[12];     /* 0 or 1: dimension not decomposed; entries
                                  0..2 and >= the state dimension ignored   */
+  int32_t fso;                /* 1: free-space-obeying kd-tree regions      */
 } kp_workspace;
 
 /* Obstacle set O (Sec. II): closed axis-aligned boxes, host pointer to

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -113,13 +114,22 @@ constexpr int kFirstRows = 256;  // trajectory rows read with the header
 struct Dims {
   int sys, D, N, R, R_pad, n_sub_per, t_e, boxes_pad;
   size_t n_sub;
+  // the tables hold R_tab regions: R itself for a grid; for the kd-tree
+  // decomposition the leaf capacity, R being the leaves of the current
+  // obstacle set
+  int fso, R_tab;
+  size_t n_sub_tab;
 };
 
 struct Layout {
   size_t ctl, boxes, st, parent, ctrl, steps, region, sub, in_ve, cs, flags, acc_key, acc_list,
       n_valid, n_invalid, cov, avail, visited, claim, score, thr, ve, blk_a, blk_b, chunk_sum,
-      stats, traj, feat, net_raw, total;
+      stats, traj, feat, net_raw, kd_node, kd_split, leaf_box, region_vol, total;
 };
+
+// Bytes of the kd-tree slices (nodes, splits, leaf boxes, leaf volumes);
+// they are contiguous in the arena from Layout::kd_node on.
+constexpr size_t kKdNodes = 2 * (size_t)KP_FSO_MAX_LEAVES;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -145,14 +155,14 @@ Layout make_layout(const Dims& d) {
   L.flags = take(te);
   L.acc_key = take(te * 4);
   L.acc_list = take(te * 4);
-  L.n_valid = take((size_t)d.R * 4);
-  L.n_invalid = take((size_t)d.R * 4);
-  L.cov = take((size_t)d.R * 4);
-  L.avail = take((size_t)d.R);
-  L.visited = take(d.n_sub);
-  L.claim = take(d.n_sub * 4);
-  L.score = take((size_t)d.R * 8);
-  L.thr = take((size_t)d.R * 8);
+  L.n_valid = take((size_t)d.R_tab * 4);
+  L.n_invalid = take((size_t)d.R_tab * 4);
+  L.cov = take((size_t)d.R_tab * 4);
+  L.avail = take((size_t)d.R_tab);
+  L.visited = take(d.n_sub_tab);
+  L.claim = take(d.n_sub_tab * 4);
+  L.score = take((size_t)d.R_tab * 8);
+  L.thr = take((size_t)d.R_tab * 8);
   L.ve = take(te * 4);
   L.blk_a = take((size_t)KP_MAX_GRID * 4);
   L.blk_b = take((size_t)KP_MAX_GRID * 4);
@@ -161,6 +171,12 @@ Layout make_layout(const Dims& d) {
   L.traj = take((size_t)KP_TRAJ_ROWS * 17 * 4);
   L.feat = take(te * 32 * 2);     // bf16 node features of the V_E positions
   L.net_raw = take(te * 8 * 4);   // network outputs of the V_E positions
+  if (d.fso) {
+    L.kd_node = take(kKdNodes * 4);
+    L.kd_split = take(kKdNodes * 4);
+    L.leaf_box = take((size_t)KP_FSO_MAX_LEAVES * 32);
+    L.region_vol = take((size_t)KP_FSO_MAX_LEAVES * 8);
+  }
   L.total = off;
   return L;
 }
@@ -200,18 +216,23 @@ const char* check_inputs(const kp_system* sys, const kp_workspace* ws, int32_t n
   if (prm->t_e < 2 || prm->t_e > (1 << 28)) return "t_e out of range";
   if (prm->lambda_max < 1 || prm->lambda_max > 1024) return "lambda_max out of range";
   if (!(prm->delta > 0.0) || !(prm->eps > 0.0) || !(prm->eps < 1.0)) return "bad delta/eps";
+  if (ws->fso != 0 && ws->fso != 1) return "fso must be 0 or 1";
   long long R = (long long)ws->grid[0] * ws->grid[1] * ws->grid[2] * ws->speed_bins;
   for (int dd = 3; dd < d->D; ++dd) {
     if (ws->state_grid[dd] < 0 || ws->state_grid[dd] > 4096) return "bad state grid";
     if (ws->state_grid[dd] > 1) R *= ws->state_grid[dd];
   }
   const long long nsp = (long long)ws->sub[0] * ws->sub[1] * ws->sub[2];
+  d->fso = ws->fso;
+  if (d->fso) R = KP_FSO_MAX_LEAVES;  // the leaf count comes with the obstacles
   if (R > (1 << 24) || R * nsp > (1ll << 30)) return "decomposition too large";
-  d->R = (int)R;
+  d->R_tab = (int)R;
+  d->n_sub_tab = (size_t)(R * nsp);
+  d->R = d->fso ? 1 : (int)R;
   d->R_pad = 1;
   while (d->R_pad < d->R) d->R_pad *= 2;
   d->n_sub_per = (int)nsp;
-  d->n_sub = (size_t)(R * nsp);
+  d->n_sub = (size_t)d->R * (size_t)nsp;
   d->t_e = prm->t_e;
   d->boxes_pad = (n_boxes + 7) / 8 * 8;
   return nullptr;
@@ -448,6 +469,102 @@ const char* check_boxes(const float* boxes, int nb) {
   return nullptr;
 }
 
+// Free-space-obeying decomposition (Sec. IV-B) as a kd-tree over the
+// workspace whose planes are obstacle faces.  A cell is split while a face
+// of a box meeting its interior lies strictly inside it: on the axis with
+// the most distinct such coordinates (the lowest on a tie), at the lower
+// median.  Nodes and leaves are numbered depth first, the side below the
+// plane first.  A child sees only the boxes that met its parent.
+struct KdTree {
+  std::vector<int32_t> node;
+  std::vector<float> split;
+  std::vector<float> lo, hi;  // [leaves][3]
+};
+
+bool kd_cell(KdTree& T, const float* fb, const std::vector<int>& ids, const float lo[3],
+             const float hi[3], int depth) {
+  const size_t me = T.node.size();
+  T.node.push_back(0);
+  T.split.push_back(0.0f);
+  std::vector<int> in;
+  for (int b : ids) {
+    const float* bx = fb + (size_t)b * 8;
+    if (bx[0] < hi[0] && bx[4] > lo[0] && bx[1] < hi[1] && bx[5] > lo[1] && bx[2] < hi[2] &&
+        bx[6] > lo[2])
+      in.push_back(b);
+  }
+  int axis = -1;
+  size_t most = 0;
+  float at = 0.0f;
+  std::vector<float> c;
+  for (int a = 0; a < 3; ++a) {
+    c.clear();
+    for (int b : in)
+      for (int s = 0; s < 2; ++s) {
+        const float f = fb[(size_t)b * 8 + 4 * s + a];
+        if (f > lo[a] && f < hi[a]) c.push_back(f);
+      }
+    std::sort(c.begin(), c.end());
+    c.erase(std::unique(c.begin(), c.end()), c.end());
+    if (c.size() > most) {
+      most = c.size();
+      axis = a;
+      at = c[(c.size() - 1) / 2];
+    }
+  }
+  if (axis < 0) {  // no face crosses the cell: a leaf
+    const size_t leaf = T.lo.size() / 3;
+    if (leaf >= (size_t)KP_FSO_MAX_LEAVES) return false;
+    T.node[me] = (int32_t)((3u << 30) | (uint32_t)leaf);
+    T.lo.insert(T.lo.end(), lo, lo + 3);
+    T.hi.insert(T.hi.end(), hi, hi + 3);
+    return true;
+  }
+  if (depth >= KP_FSO_MAX_DEPTH) return false;
+  T.split[me] = at;
+  float clo[3] = {lo[0], lo[1], lo[2]}, chi[3] = {hi[0], hi[1], hi[2]};
+  chi[axis] = at;
+  if (!kd_cell(T, fb, in, lo, chi, depth + 1)) return false;
+  T.node[me] = (int32_t)(((uint32_t)axis << 30) | (uint32_t)T.node.size());
+  clo[axis] = at;
+  return kd_cell(T, fb, in, clo, hi, depth + 1);
+}
+
+// Builds the tree over the padded blob boxes and writes the arena image of
+// its slices to 'host' (kd_node, kd_split, leaf_box, region_vol at their
+// offsets relative to lay.kd_node).  Returns the leaf count, 0 past the
+// limits.
+int build_kd(unsigned char* host, const float* fb, int nb, const kp_workspace& ws,
+             const Layout& lay) {
+  KdTree T;
+  std::vector<int> all((size_t)nb);
+  for (int b = 0; b < nb; ++b) all[(size_t)b] = b;
+  if (!kd_cell(T, fb, all, ws.lo, ws.hi, 0)) return 0;
+  const int leaves = (int)(T.lo.size() / 3);
+  int32_t* node = reinterpret_cast<int32_t*>(host);
+  float* split = reinterpret_cast<float*>(host + (lay.kd_split - lay.kd_node));
+  float* box = reinterpret_cast<float*>(host + (lay.leaf_box - lay.kd_node));
+  double* vol = reinterpret_cast<double*>(host + (lay.region_vol - lay.kd_node));
+  for (size_t i = 0; i < T.node.size(); ++i) {
+    node[i] = T.node[i];
+    split[i] = T.split[i];
+  }
+  for (int r = 0; r < leaves; ++r) {
+    float* o = box + (size_t)r * 8;
+    for (int a = 0; a < 3; ++a) {
+      const float l = T.lo[(size_t)r * 3 + a], h = T.hi[(size_t)r * 3 + a];
+      o[a] = l;
+      o[4 + a] = (float)((double)ws.sub[a] / ((double)h - (double)l));
+    }
+    o[3] = o[7] = 0.0f;
+    const float* l = &T.lo[(size_t)r * 3];
+    const float* h = &T.hi[(size_t)r * 3];
+    vol[r] = ((double)h[0] - (double)l[0]) * ((double)h[1] - (double)l[1]) *
+             ((double)h[2] - (double)l[2]);
+  }
+  return leaves;
+}
+
 kp_status configure_launch(kp_ctx* ctx);
 
 kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
@@ -455,14 +572,34 @@ kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
   if (nb < 0 || nb > ctx->n_boxes_cap) return fail(ctx, KP_ERR_ARG, "box count above capacity");
   if (nb > 0 && !obs->boxes) return fail(ctx, KP_ERR_ARG, "null boxes");
   if (const char* m = check_boxes(nb > 0 ? obs->boxes : nullptr, nb)) return fail(ctx, KP_ERR_ARG, "%s", m);
-  // build the blob in pinned host memory, then one async copy
-  kp_status ps = ensure_pinned(ctx, (size_t)KP_BLOB_BYTES + sizeof(KCtl));
+  // build the blob (and the kd-tree) in pinned host memory, then async copies
+  const Layout& L = ctx->lay;
+  const size_t kd_bytes = ctx->dims.fso ? L.total - L.kd_node : 0;
+  kp_status ps = ensure_pinned(ctx, (size_t)KP_BLOB_BYTES + kd_bytes + sizeof(KCtl));
   if (ps != KP_OK) return ps;
   KP_CUDA(cudaStreamSynchronize(ctx->stream));  // the staging buffer is free
   unsigned char* host = static_cast<unsigned char*>(ctx->pinned);
   const size_t bytes = build_blob(host, nb > 0 ? obs->boxes : nullptr, nb, ctx->ws, ctx->P);
-  KP_CUDA(cudaMemcpyAsync(ctx->arena + ctx->lay.boxes, host, bytes, cudaMemcpyHostToDevice,
+  KP_CUDA(cudaMemcpyAsync(ctx->arena + L.boxes, host, bytes, cudaMemcpyHostToDevice,
                           ctx->stream));
+  if (ctx->dims.fso) {
+    unsigned char* kd = host + (size_t)KP_BLOB_BYTES;
+    const int leaves = build_kd(kd, reinterpret_cast<const float*>(host), nb, ctx->ws, L);
+    if (leaves == 0) {
+      KP_CUDA(cudaStreamSynchronize(ctx->stream));
+      return fail(ctx, KP_ERR_ARG, "kd-tree decomposition above %d leaves or depth %d",
+                  KP_FSO_MAX_LEAVES, KP_FSO_MAX_DEPTH);
+    }
+    KP_CUDA(cudaMemcpyAsync(ctx->arena + L.kd_node, kd, kd_bytes, cudaMemcpyHostToDevice,
+                            ctx->stream));
+    Dims& d = ctx->dims;
+    d.R = leaves;
+    d.R_pad = 1;
+    while (d.R_pad < d.R) d.R_pad *= 2;
+    d.n_sub = (size_t)d.R * (size_t)d.n_sub_per;
+    ctx->P.R = d.R;
+    ctx->P.R_pad = d.R_pad;
+  }
   KP_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->dims.boxes_pad = ctx->P.n_boxes_pad;
   ctx->have_tree = false;
@@ -583,6 +720,13 @@ void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* 
   P.delta = prm->delta;
   P.eps = prm->eps;
   P.vol = vol;
+  P.fso = d.fso;
+  if (d.fso) {
+    P.kd_node = reinterpret_cast<const int32_t*>(A + lay.kd_node);
+    P.kd_split = reinterpret_cast<const float*>(A + lay.kd_split);
+    P.leaf_box = reinterpret_cast<const float4*>(A + lay.leaf_box);
+    P.region_vol = reinterpret_cast<const double*>(A + lay.region_vol);
+  }
   P.boxes = reinterpret_cast<const float*>(A + lay.boxes);
   P.st = reinterpret_cast<float*>(A + lay.st);
   P.parent = reinterpret_cast<int32_t*>(A + lay.parent);
@@ -1024,6 +1168,7 @@ kp_status kp_grow(kp_ctx* ctx, void* dev_arena, size_t arena_bytes, int32_t t_e)
   KP_CUDA(cudaMemcpyAsync(dst + nl.ctl, ctx->pinned, sizeof(KCtl), cudaMemcpyHostToDevice,
                           ctx->stream));
   if ((s = d2d(nl.boxes, ol.boxes, (size_t)ctx->P.blob_bytes)) != KP_OK) return s;
+  if (od.fso && (s = d2d(nl.kd_node, ol.kd_node, ol.total - ol.kd_node)) != KP_OK) return s;
   // the tree: SoA rows move to the new stride
   if (n) {
     KP_CUDA(cudaMemcpy2DAsync(dst + nl.st, (size_t)nd.t_e * 4, src + ol.st, (size_t)od.t_e * 4,
@@ -1263,6 +1408,7 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   const int nb = obs ? obs->n_boxes : 0;
   Dims d{};
   if (check_inputs(sys, ws, nb, prm, &d)) return KP_ERR_ARG;
+  if (d.fso) return KP_ERR_ARG;  // grid regions only
   if (nb > 0 && !obs->boxes) return KP_ERR_ARG;
   if (check_boxes(nb > 0 ? obs->boxes : nullptr, nb)) return KP_ERR_ARG;
   for (int i = 0; i < d.D; ++i)
@@ -1765,6 +1911,7 @@ kp_status kp_server_submit(kp_server* s, const kp_system* sys, const kp_workspac
   const int nb = obs ? obs->n_boxes : 0;
   Dims d{};
   if (check_inputs(sys, ws, nb, prm, &d)) return KP_ERR_ARG;
+  if (d.fso) return KP_ERR_ARG;  // grid regions only
   if (nb > 0 && (!obs->boxes || check_boxes(obs->boxes, nb))) return KP_ERR_ARG;
   if (budget->max_iters < 1 || !(goal->radius >= 0.0f)) return KP_ERR_ARG;
   for (int i = 0; i < d.D; ++i)

@@ -352,9 +352,39 @@ __device__ __forceinline__ int fine_cell(float t, int n) {
   return t >= 0.0f ? (t < (float)n ? (int)t : n - 1) : 0;
 }
 
+// Region and sub-region under the kd-tree decomposition: descend from the
+// root (below a plane goes left, to node + 1), then the sub-grid cell of the
+// leaf's own box.  The tree is built on the host with depth at most
+// KP_FSO_MAX_DEPTH and every child index above its parent's, so the walk
+// ends; the bound only guards it.
+__device__ __forceinline__ void bin_fso(const float* x, const KParams& P, int* region,
+                                        int* sub) {
+  // codes are read unsigned: the tag sits in the top two bits
+  int node = 0;
+  uint32_t code = (uint32_t)__ldg(P.kd_node);
+  for (int depth = 0; (code >> 30) != 3u && depth < KP_FSO_MAX_DEPTH; ++depth) {
+    const uint32_t a = code >> 30;
+    const float xa = a == 0u ? x[0] : (a == 1u ? x[1] : x[2]);
+    node = xa < __ldg(P.kd_split + node) ? node + 1 : (int)(code & 0x3fffffffu);
+    code = (uint32_t)__ldg(P.kd_node + node);
+  }
+  const int r = (code >> 30) == 3u ? (int)(code & 0x3fffffffu) : 0;
+  const float4 lo = __ldg(P.leaf_box + 2 * r);
+  const float4 sc = __ldg(P.leaf_box + 2 * r + 1);
+  const int fx = fine_cell(__fmul_rn(__fsub_rn(x[0], lo.x), sc.x), P.sub[0]);
+  const int fy = fine_cell(__fmul_rn(__fsub_rn(x[1], lo.y), sc.y), P.sub[1]);
+  const int fz = fine_cell(__fmul_rn(__fsub_rn(x[2], lo.z), sc.z), P.sub[2]);
+  *region = r;
+  *sub = r * P.n_sub_per + fx + P.sub[0] * (fy + P.sub[1] * fz);
+}
+
 template <int SYS>
 __device__ __forceinline__ void bin_state(const float* x, const KParams& P, int* region,
                                           int* sub) {
+  if (P.fso) {
+    bin_fso(x, P, region, sub);
+    return;
+  }
   int cell[3], fine[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {

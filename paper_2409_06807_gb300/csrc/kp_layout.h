@@ -34,6 +34,8 @@ constexpr int KP_BP_MAX_G = 16;        // finest broad-phase grid per axis
 constexpr int KP_BP_MAX_IDS = 32768;   // broad-phase (cell, box) entries
 constexpr int KP_BLOB_BYTES = 4096 * 32 + (KP_BP_MAX_G * KP_BP_MAX_G * KP_BP_MAX_G + 4) * 4 +
                               KP_BP_MAX_IDS * 2;  // arena room for the obstacle blob
+constexpr int KP_FSO_MAX_LEAVES = 16384; // regions of a kd-tree decomposition
+constexpr int KP_FSO_MAX_DEPTH = 64;     // its deepest leaf
 
 // Device control block (one per context, in the arena).
 struct KCtl {
@@ -117,6 +119,16 @@ struct KParams {
   int32_t state_grid[12];  // cells over state dimension d (1: not decomposed)
   float state_scale[12];   // cells per unit of that dimension
   int32_t state_wrap[12];  // 1: an angle, wrapped to [-pi, pi) before binning
+  // free-space-obeying decomposition (fso = 1): a kd-tree over position;
+  // node i: (axis << 30) | right child for a split at kd_split[i] (the left
+  // child is i + 1; a point below the plane goes left), (3 << 30) | leaf
+  // for a leaf; leaf r: leaf_box[2r] = lo.xyz, leaf_box[2r+1] = sub-grid
+  // cells per unit length; region_vol[r] = its volume (Eq. 3)
+  int32_t fso;
+  const int32_t* kd_node;
+  const float* kd_split;
+  const float4* leaf_box;
+  const double* region_vol;
   int32_t n_sub_per;    // n'
   int32_t R;            // regions
   int32_t R_pad;        // next power of two >= R

@@ -196,7 +196,8 @@ __device__ __forceinline__ int write_ve(const KParams& P, const Team& T, int n, 
 // unbounded one wrapped to [-pi, pi) and divided by pi; goal minus
 // position; Cov / n'; FreeVol / vol; log(1 + n_valid); log(1 + n_invalid);
 // P_accept of the node's region and of its six face neighbours in the
-// position grid (0 outside); zeros from feature 20 on.
+// position grid (0 outside, and 0 under the kd-tree decomposition); zeros
+// from feature 20 on.
 __device__ __forceinline__ float state_feature(const KParams& P, int i, float x) {
   if (P.feat_scale[i] > 0.0f) return (x - P.x_lo[i]) * P.feat_scale[i] - 1.0f;
   const float y = x - 6.28318530717958648f * floorf((x + 3.14159265358979324f) *
@@ -242,7 +243,8 @@ __device__ __forceinline__ void node_feature_pair(const KParams& P, int v, int q
       f2[0] = log1pf(ni);
       f2[1] = (float)P.thr[r] * 2.3283064365386963e-10f;
       break;
-    default:  // q = 7, 8, 9: neighbours 2(q-7) and 2(q-7)+1
+    default:  // q = 7, 8, 9: neighbours 2(q-7) and 2(q-7)+1 (none for kd-tree regions)
+      if (P.fso) break;
       f2[0] = neighbour_accept(P, r, 2 * (q - 7));
       f2[1] = neighbour_accept(P, r, 2 * (q - 7) + 1);
   }
@@ -637,7 +639,8 @@ __device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, in
     if (r < P.R && P.avail[r]) {
       const double nv = (double)P.n_valid[r], ni = (double)P.n_invalid[r];
       const double dn = __dadd_rn(P.delta, nv);
-      const double fv = __ddiv_rn(__dmul_rn(dn, P.vol), __dadd_rn(dn, ni));
+      const double vol = P.region_vol ? P.region_vol[r] : P.vol;
+      const double fv = __ddiv_rn(__dmul_rn(dn, vol), __dadd_rn(dn, ni));
       const double f2 = __dmul_rn(fv, fv);
       const double f4 = __dmul_rn(f2, f2);
       const double na = __dadd_rn(nv, ni);

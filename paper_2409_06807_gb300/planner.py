@@ -38,7 +38,7 @@ class System(C.Structure):
 class Workspace(C.Structure):
     _fields_ = [("lo", C.c_float * 3), ("hi", C.c_float * 3), ("grid", C.c_int32 * 3),
                 ("speed_bins", C.c_int32), ("speed_hi", C.c_float), ("sub", C.c_int32 * 3),
-                ("state_grid", C.c_int32 * 12)]
+                ("state_grid", C.c_int32 * 12), ("fso", C.c_int32)]
 
 
 class Obstacles(C.Structure):
@@ -197,6 +197,7 @@ def structs(w):
     ws.speed_bins = int(w.speed_bins)
     for i in range(12):
         ws.state_grid[i] = int(w.state_grid[i])
+    ws.fso = 1 if getattr(w, "fso", False) else 0
     ws.speed_hi = float(w.speed_hi)
     p = Params()
     p.t_e, p.lambda_max = int(w.t_e), int(w.lambda_max)
@@ -272,6 +273,9 @@ class Planner:
         boxes = np.ascontiguousarray(np.asarray(boxes, np.float32).reshape(-1, 6))
         obs = Obstacles(_fptr(boxes) if len(boxes) else None, len(boxes))
         self._check(lib().kp_set_obstacles(self._ctx, C.byref(obs)), "kp_set_obstacles")
+        # a kd-tree decomposition has as many regions as the new set gives
+        info = self.info()
+        self.n_regions, self.n_sub = info["n_regions"], info["n_subregions"]
 
     def reset(self, x_init=None, goal=None, seed=None):
         w = self.w

@@ -382,3 +382,107 @@ def test_frontier_c2_state_grid(P):
     flips, ost = frontier(P, w, grow=2)
     assert ost["n_samples"] > 10000
     assert flips <= 2
+
+
+# ---------------------------------------------------------------------------
+# free-space-obeying decomposition (kd-tree over obstacle faces, Sec. IV-B)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("system", [W.DI, W.DUBINS, W.QUAD])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_lockstep_tiny_fso(P, system, seed):
+    """Regions are the leaves of the kd-tree the host builds from the
+    obstacles; each pass matches the oracle's own tree and leaf volumes."""
+    w = W.tiny(system, seed=seed, t_e=2000, lambda_max=8, n_boxes=4, fso=True)
+    g = P.Planner(w)
+    assert g.n_regions == Oracle(w).R > 1
+    exact, ran = lockstep(P, w, 12)
+    assert exact >= min(ran, 3)
+
+
+def test_lockstep_c1_fso(P):
+    """Double integrator, 16 random boxes: kd-tree regions, passes of up to
+    tens of thousands of samples."""
+    w = W.c1(1).with_(fso=True)
+    exact, ran = lockstep(P, w, 10)
+    assert exact >= 2
+
+
+def test_frontier_c2_fso(P):
+    """The 200-trunk Dubins forest with kd-tree regions (about 1,240
+    leaves): one pass over the oracle's 3-pass tree."""
+    w = W.c2(0).with_(fso=True)
+    flips, ost = frontier(P, w, grow=2)
+    assert ost["n_samples"] > 10000
+    assert flips <= 2
+
+
+def test_frontier_c3_fso(P):
+    """The 1,200-box quadrotor building with kd-tree regions (about 2,000
+    leaves): one pass over the oracle's 1-pass tree."""
+    w = W.c3(0).with_(fso=True)
+    flips, ost = frontier(P, w, grow=1)
+    assert ost["n_samples"] > 10000
+    assert flips <= 2
+
+
+def test_fso_obstacle_swap_rebuilds(P):
+    """kp_set_obstacles rebuilds the tree: the region count follows the new
+    set (as the oracle builds it), planning re-validates, and an empty set
+    is one region (the whole workspace: no guidance, so a short budget need
+    not solve)."""
+    w = W.c1(0).with_(fso=True)
+    empty = w.with_(boxes=np.zeros((0, 6), np.float32))
+    g = P.Planner(empty, box_capacity=64)
+    assert g.n_regions == 1
+    st, _ = g.plan(max_iters=20)
+    assert st in (P.OK, P.NO_SOLUTION)
+    _tree_invariants(empty, g.export_tree())
+    g.set_obstacles(w.boxes)
+    g.w = w
+    assert g.n_regions == Oracle(w).R
+    st, traj = g.plan(max_iters=200)
+    assert st == P.OK
+    _revalidate(w, traj, w.x_init)
+    _tree_invariants(w, g.export_tree(), sample_edges=200)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_plan_c2_fso_revalidated(P, seed):
+    """Full-size forest query with kd-tree regions: trajectory re-validated
+    by the oracle, and the tree's regions are the oracle's leaves."""
+    w = W.c2(seed).with_(fso=True)
+    g = P.Planner(w)
+    st, traj = g.plan(max_iters=200)
+    assert st == P.OK
+    _revalidate(w, traj, w.x_init)
+    _tree_invariants(w, g.export_tree(), sample_edges=300)
+
+
+def test_grow_fso_keeps_leaves(P):
+    """Remark 1 with kd-tree regions: after the move to a larger arena the
+    next pass still bins into the same leaves as the oracle."""
+    w = W.c1(1, t_e=1024).with_(fso=True)
+    src = Oracle(w)
+    src.reset()
+    for _ in range(60):
+        status, _, _ = src.iterate()
+        if status != kpo.RUNNING:
+            break
+    assert status == kpo.FULL
+    t = src.export()
+    t["state"] = t["state"].astype(np.float32)
+    t["ctrl"] = t["ctrl"].astype(np.float32)
+    g = P.Planner(w)
+    g.import_tree(t)
+    g.grow(4 * w.t_e)
+    w2 = w.with_(t_e=4 * w.t_e)
+    o = Oracle(w2)
+    o.import_(t)
+    g.enable_log(w2.t_e)
+    status, ost, orec = o.iterate(records=True)
+    gs = g.expand_step(1)
+    assert len(gs) == 1 and ost["n_samples"] > 0
+    assert compare_pass(w2, ost, orec, gs[0], g.read_log(ost["n_samples"])) <= 2
+    compare_trees(w2, g.export_tree(), o.export())
+

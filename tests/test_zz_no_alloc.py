@@ -71,3 +71,10 @@ def test_static_plan_refuses_oversized_problem(P):
     w = W.c2(0)  # t_e = 2^20: its arena is far above the static maximum
     st, _ = static_plan(P, w)
     assert st == P.ERR_OOM
+
+
+def test_static_plan_takes_grid_regions_only(P):
+    """The kd-tree decomposition needs the context path (its tree is built
+    with the obstacles); the no-allocation entry point refuses it."""
+    st, _ = static_plan(P, W.c1(0).with_(fso=True))
+    assert st == P.ERR_ARG
