@@ -122,7 +122,7 @@ struct Dims {
 };
 
 struct Layout {
-  size_t ctl, boxes, st, parent, ctrl, steps, region, sub, in_ve, cs, flags, acc_key, acc_list,
+  size_t ctl, boxes, st, parent, ctrl, steps, region, sub, in_ve, cs, flags, acc_key,
       n_valid, n_invalid, cov, avail, visited, claim, score, thr, ve, blk_a, blk_b, chunk_sum,
       stats, traj, feat, net_raw, kd_node, kd_split, leaf_box, region_vol, total;
 };
@@ -154,7 +154,6 @@ Layout make_layout(const Dims& d) {
   L.cs = take(te * 4);
   L.flags = take(te);
   L.acc_key = take(te * 4);
-  L.acc_list = take(te * 4);
   L.n_valid = take((size_t)d.R_tab * 4);
   L.n_invalid = take((size_t)d.R_tab * 4);
   L.cov = take((size_t)d.R_tab * 4);
@@ -567,6 +566,16 @@ int build_kd(unsigned char* host, const float* fb, int nb, const kp_workspace& w
 
 kp_status configure_launch(kp_ctx* ctx);
 
+// Region chunks of the Score sums (Eq. 5): a power of two, at most one per
+// block, chunks of at least 32 regions (one per lane of the warp that
+// scores them), at most 1024 chunks.  Any power of two gives the same
+// pairwise tree.
+int region_chunks(int blocks, int R_pad) {
+  int nch = 1;
+  while (nch * 2 <= blocks && nch * 2 * 32 <= R_pad && nch * 2 <= 1024) nch *= 2;
+  return nch;
+}
+
 kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
   const int nb = obs ? obs->n_boxes : 0;
   if (nb < 0 || nb > ctx->n_boxes_cap) return fail(ctx, KP_ERR_ARG, "box count above capacity");
@@ -631,8 +640,7 @@ kp_status configure_launch(kp_ctx* ctx) {
   if (s != KP_OK) return s;
   // region chunks: a power of two <= the smaller grid, <= R_pad, <= 1024
   const int gmin = ctx->grid[0] < ctx->grid[1] ? ctx->grid[0] : ctx->grid[1];
-  int nch = 1;
-  while (nch * 2 <= gmin && nch * 2 <= d.R_pad && nch * 2 <= 1024) nch *= 2;
+  const int nch = region_chunks(gmin, d.R_pad);
   ctx->P.nch = nch;
   // ... then with the scratch this chunking needs (smaller shared memory
   // never lowers the grid, so nch stays at most the grid)
@@ -737,7 +745,6 @@ void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* 
   P.in_ve = reinterpret_cast<uint8_t*>(A + lay.in_ve);
   P.cs = reinterpret_cast<int32_t*>(A + lay.cs);
   P.acc_key = reinterpret_cast<uint32_t*>(A + lay.acc_key);
-  P.acc_list = reinterpret_cast<uint32_t*>(A + lay.acc_list);
   P.flags = reinterpret_cast<uint8_t*>(A + lay.flags);
   P.n_valid = reinterpret_cast<uint32_t*>(A + lay.n_valid);
   P.n_invalid = reinterpret_cast<uint32_t*>(A + lay.n_invalid);
@@ -1475,9 +1482,8 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   }
   int grid = bps * num_sms;
   if (grid > KP_MAX_GRID) grid = KP_MAX_GRID;
-  int nch = 1;
-  while (nch * 2 <= grid && nch * 2 <= d.R_pad && nch * 2 <= 1024) nch *= 2;
-  P.nch = nch;
+  P.nch = region_chunks(grid, d.R_pad);
+  if (d.R_pad / P.nch > sd) return KP_ERR_ARG;  // a chunk's scores exceed the scratch
 
   cudaError_t e = cudaSuccess;
   auto ok = [&](cudaError_t r) {
@@ -1699,8 +1705,7 @@ bool try_admit(kp_server* s, PendingQuery& q) {
   P.seed_lo = (uint32_t)(q.prm.seed & 0xffffffffu);
   P.seed_hi = (uint32_t)(q.prm.seed >> 32);
   P.wait_ns = 2000000000ull;
-  int nch = 1;
-  while (nch * 2 <= s->team_blocks && nch * 2 <= d.R_pad && nch * 2 <= 1024) nch *= 2;
+  const int nch = region_chunks(s->team_blocks, d.R_pad);
   P.nch = nch;
   P.sd_bytes = KS_SD_DOUBLES * 8;
   const size_t blob_bytes = build_blob(s->blob.data(), q.boxes.empty() ? nullptr : q.boxes.data(),

@@ -53,7 +53,7 @@ struct KCtl {
   int32_t n_edges;     // trajectory extraction: edges on the chain
   int32_t work_next;   // next sample key handed out in the expand phase
   uint32_t s_done;     // region chunks whose Score partial sum is written
-  int32_t mat_next;    // next accepted sample handed out for materialising
+  uint32_t sum_gen;    // generation of the published Eq. 5 sum (one per pass)
   double score_sum;    // sum of Eq. 5 over R_avail, this pass
   // work counters since the last reset (samples, integrator steps run,
   // segment hulls tested against the obstacle set)
@@ -86,9 +86,10 @@ struct KLog {
 struct KStats {
   int32_t iteration, n_ve, lambda, n_samples, n_valid, n_accepted, n_nodes, goal_node;
   // device time of the pass as seen by block 0 (ns): work then barrier wait
-  // of each phase: [0,1] Propagate, [2] accept + Score, [3] 0, [4] wait,
-  // [5] append + P_accept, [6] 0, [7] wait, [8] node sets, [9] wait,
-  // [10] V_E list and Eq. 6, [11] previous pass's final wait
+  // of each phase: [0,1] Propagate, [2] accept + Score + P_accept, [3]
+  // features and network, [4] wait, [5] 0, [6] wait after [3], [7] 0,
+  // [8] node sets and new nodes, [9] wait, [10] V_E list and Eq. 6, [11]
+  // previous pass's final wait
   int32_t phase_ns[12];
 };
 
@@ -164,11 +165,8 @@ struct KParams {
   int32_t* cs;        // sub-region of a contender (claim check)
   uint8_t* flags;     // KP_F_* of the sample
   // accepted samples: each accept warp compacts its keys (winner flag in
-  // bit 31) at the start of its own key range in acc_key; the append
-  // copies them to acc_list in key order, i.e. acc_list[i] becomes node
-  // t_old + i
+  // bit 31) at the start of its own key range, in key order
   uint32_t* acc_key;
-  uint32_t* acc_list;
   // decomposition tables
   uint32_t* n_valid;
   uint32_t* n_invalid;

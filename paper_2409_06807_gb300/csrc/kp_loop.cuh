@@ -33,13 +33,20 @@
 
 namespace kp {
 
+constexpr int KP_WARPS = KP_BLOCK / 32;
+
 struct LoopShared {
   ScanSmem scan;
   unsigned long long red[64];
   uint64_t mbar;
   int flag;
-  int bcast[2];
+  int bcast[3];
   int32_t phase_ns[12];  // per-pass phase timers (block 0, thread 0)
+  // accepted samples of this block, from the accept phase to the node-set
+  // phase: warp w compacted acc_n[w] keys at acc_key[acc_a[w]...], which
+  // are the block's accepted samples acc_off[w] .. acc_off[w] + acc_n[w] - 1
+  int acc_a[KP_WARPS], acc_n[KP_WARPS], acc_off[KP_WARPS];
+  int acc_tot;
 };
 
 // Stage the obstacle blob (boxes and broad-phase grid) into shared memory
@@ -539,19 +546,19 @@ __device__ __forceinline__ void warp_range(int c0, int c1, int* a, int* b) {
 // takes keys t0 + 32q + l: every load is coalesced), with the loads of a
 // tile's flags, contenders' sub-regions and their claims issued together,
 // and compacts its accepted keys (claim winners marked in bit 31) in key
-// order at the start of its range in acc_key.  Phase S (warp 0) runs
+// order at the start of its range in acc_key.  Phases S and T (warp 0) run
 // alongside.  Publishes the block's accepted count, adds the valid count to
-// the pass, and returns the warp's accepted count and its offset among the
-// block's accepted samples (kept in registers across the grid barrier).
+// the pass, and leaves where each warp's accepted keys are, and their
+// offsets among the block's, in shared memory for the node-set phase.
 constexpr int KP_ACC_KPL = 8;
 
-__device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, int nch, double* sd);
+__device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, int nch, double* sd,
+                                             uint32_t sum_gen);
 
 template <bool LOG>
 __device__ __forceinline__ void phase_accept(const KParams& P, const Team& T, int S, int nch,
-                                             double* sd, LoopShared& sh, int* warp_off,
-                                             int* warp_n) {
-  if (threadIdx.x < 32) phase_scores(P, T, nch, sd);
+                                             double* sd, LoopShared& sh, uint32_t sum_gen) {
+  if (threadIdx.x < 32) phase_scores(P, T, nch, sd, sum_gen);
   const uint32_t FULL = 0xffffffffu;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt = (1u << lane) - 1u;
@@ -598,8 +605,12 @@ __device__ __forceinline__ void phase_accept(const KParams& P, const Team& T, in
     off += q < w ? cq : 0;
     block_acc += cq;
   }
-  *warp_off = off;
-  *warp_n = n_acc;
+  if (lane == 0) {
+    sh.acc_a[w] = a;
+    sh.acc_n[w] = n_acc;
+    sh.acc_off[w] = off;
+  }
+  if (threadIdx.x == 0) sh.acc_tot = block_acc;
   unsigned long long bv, dummy;
   block_sum2((unsigned long long)n_valid, 0, sh.red, &bv, &dummy);
   if (threadIdx.x == 0) {
@@ -621,14 +632,21 @@ __device__ __forceinline__ void warp_pairwise(double* buf, int n) {
   __syncwarp();
 }
 
+__device__ __forceinline__ void phase_thresholds(const KParams& P, const Team& T, int nch);
+
 // Phase S (warp 0): Eq. 3-4 for this block's region chunk and its pairwise
 // partial sum; the last chunk to finish reduces the partial sums into the
-// sum of Eq. 5 (same pairwise tree whichever block it is).  Every operation
-// is an explicitly rounded IEEE double operation in the order
+// sum of Eq. 5 (same pairwise tree whichever block it is) and publishes it
+// with generation 'sum_gen'.  Every operation is an explicitly rounded IEEE
+// double operation in the order
 // FreeVol = ((delta + nv) vol) / ((delta + nv) + ni),
 // f4 = (FreeVol FreeVol)(FreeVol FreeVol),
 // Score = f4 / ((1 + Cov)(1 + (nv + ni)(nv + ni))).
-__device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, int nch, double* sd) {
+// Then phase T: every chunk waits (bounded) for the sum and writes its
+// thresholds.  Nothing in the accept phase reads thr, and the node-set
+// draws that do come after the grid barrier.
+__device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, int nch, double* sd,
+                                             uint32_t sum_gen) {
   if (T.b >= nch) return;
   const int lane = (int)(threadIdx.x & 31u);
   const int ch = P.R_pad / nch;
@@ -666,9 +684,29 @@ __device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, in
     if (lane == 0) {
       P.ctl->score_sum = sd[0];
       P.ctl->s_done = 0;  // for the next pass
+      __threadfence();
+      st_release(&P.ctl->sum_gen, sum_gen);
     }
   }
   __syncwarp();
+  int ok = 1;
+  if (lane == 0) {
+    const uint64_t t0 = global_ns();
+    uint32_t spins = 0;
+    while (ld_acquire(&P.ctl->sum_gen) != sum_gen) {
+      if ((++spins & 63u) == 0) {
+        if (*((volatile int*)&P.ctl->err) != 0) { ok = 0; break; }
+        if (global_ns() - t0 > P.wait_ns) {
+          raise_error(P.ctl, KP_DEV_ERR_TIMEOUT, 24);
+          ok = 0;
+          break;
+        }
+      }
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  if (ok) phase_thresholds(P, T, nch);
 }
 
 // Phase T (warp 0): P_accept and the integer threshold of this block's
@@ -696,50 +734,29 @@ __device__ __forceinline__ void phase_thresholds(const KParams& P, const Team& T
   }
 }
 
-// Phase P (warps 1..): each warp copies its compacted accepted keys to
-// their place in key order, acc_list[block offset + warp offset + i]
-// (acc_list[i] becomes node t_old + i).  Phase T (warp 0) runs alongside.
-__device__ __forceinline__ void phase_append(const KParams& P, const Team& T, int S, int nch,
-                                             int warp_off, int warp_n, int* total_out) {
-  unsigned long long off, total;
-  warp_prefix(T, P.blk_a, &off, &total);
-  *total_out = (int)total;
-  if (threadIdx.x < 32) {
-    if (T.b == 0 && threadIdx.x == 0) P.ctl->mat_next = 0;
-    phase_thresholds(P, T, nch);
-    return;
-  }
-  int k0, k1, a, b;
-  chunk_of(T, S, &k0, &k1);
-  warp_range(k0, k1, &a, &b);
-  const int base = (int)off + warp_off;
-  for (int i = (int)(threadIdx.x & 31u); i < warp_n; i += 32) P.acc_list[base + i] = P.acc_key[a + i];
-}
-
-// Materialises the new nodes t_old .. t_old + n_new - 1: every accepted
-// sample is re-derived from its key (the same draw and the same integrator
-// steps as in the expand phase, so the same numbers) and written to the
-// tree with its parent, control, duration, region and sub-region; visited
-// and the goal test (closed ball on position; the smallest new goal node
-// wins) follow.  Warps take batches of 32 from a grid-wide counter, so long
-// and short samples spread over the whole team.  With the sample log on,
-// the re-derived state is compared with the logged one.
+// Materialises this block's accepted samples as the nodes id0 .. id0 +
+// acc_tot - 1 (id0 = t_old + the accepted samples of the blocks before it:
+// node ids follow the sample keys).  Every accepted sample is re-derived
+// from its key (the same draw and the same integrator steps as in the
+// expand phase, so the same numbers) and written to the tree with its
+// parent, control, duration, region and sub-region; visited and the goal
+// test (closed ball on position; the smallest new goal node wins) follow.
+// Thread j of the block takes the block's samples j, j + blockDim.x, ...;
+// consecutive threads write consecutive nodes.  With the sample log on, the
+// re-derived state is compared with the logged one.
 template <int SYS, bool LOG>
-__device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int t_old, int n_new,
-                                            int lam) {
+__device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int id0, int lam,
+                                            const LoopShared& sh) {
   using Sys = System<SYS>;
   constexpr int D = Sys::D, N = Sys::N;
-  const uint32_t lane = threadIdx.x & 31u;
-  for (;;) {
-    int base = 0;
-    if (lane == 0) base = atomicAdd(&P.ctl->mat_next, 32);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= n_new) break;
-    const int i = base + (int)lane;
-    if (i >= n_new) continue;
-    const uint32_t e = P.acc_list[i];
+  for (int j = (int)threadIdx.x; j < sh.acc_tot; j += (int)blockDim.x) {
+    int w = 0;
+#pragma unroll
+    for (int q = 0; q < KP_WARPS; ++q)
+      if (j >= sh.acc_off[q] && j < sh.acc_off[q] + sh.acc_n[q]) w = q;
+    const uint32_t e = P.acc_key[sh.acc_a[w] + (j - sh.acc_off[w])];
     const int key = (int)(e & 0x7fffffffu);
-    const int id = t_old + i;
+    const int id = id0 + j;
     float x[D], u[N];
     int k;
     uint32_t wacc, wr[4];
@@ -788,12 +805,18 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int t
 
 // Phase N: Algorithm 4 node sets, one draw per old node (counter: it, v, 0,
 // purpose 2) against the threshold of its region; new nodes are in V_E.
-// Returns this thread's offset among the block's V_E members.
-// The new nodes (ids from t_old) are materialised here as well; they are
-// counted as V_E members without reading their sets.
+// Returns this thread's offset among the block's V_E members and, in
+// *n_new, the number of accepted samples of the pass (the new nodes).
+// The new nodes (ids from t_old, in key order) are materialised here as
+// well, each block its own accepted samples; they are counted as V_E
+// members without reading their sets.
 template <int SYS, bool LOG>
 __device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, uint32_t it,
-                                              int t_old, int t_new, int lam, LoopShared& sh) {
+                                              int t_old, int lam, LoopShared& sh, int* n_new) {
+  unsigned long long acc_before, acc_total;
+  block_prefix(T, P.blk_a, sh, &acc_before, &acc_total);
+  *n_new = (int)acc_total;
+  const int t_new = t_old + (int)acc_total;
   int v0, v1, r0, r1;
   chunk_of(T, t_new, &v0, &v1);
   thread_run(v0, v1, &r0, &r1);
@@ -810,7 +833,7 @@ __device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, u
   int tot;
   const int off = block_exclusive_scan(c, sh.scan, &tot);
   if (threadIdx.x == 0) P.blk_b[T.b] = (uint32_t)tot;
-  materialise<SYS, LOG>(P, it, t_old, t_new - t_old, lam);
+  materialise<SYS, LOG>(P, it, t_old + (int)acc_before, lam, sh);
   return off;
 }
 
@@ -832,13 +855,17 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     ctl->s_done = 0;
   }
   // the loop state, read once per block
+  // (the generation of the published Eq. 5 sum, too: nothing writes it
+  // before the accept phase, so every block reads the same value)
   if (threadIdx.x == 0) {
     sh.bcast[0] = ctl->n_nodes;
     sh.bcast[1] = ctl->iteration;
+    sh.bcast[2] = (int)*((volatile uint32_t*)&ctl->sum_gen);
   }
   __syncthreads();
   int n_tree = sh.bcast[0];
   uint32_t it = (uint32_t)sh.bcast[1];
+  const uint32_t sum_gen0 = (uint32_t)sh.bcast[2];
   const int nch = P.nch;
 
   // V_E list from the stored node sets
@@ -883,19 +910,15 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     stamp(0);
     if (!team_sync(T, ctl, P.wait_ns, 20)) return false;
     stamp(1);
-    int warp_off, warp_n;
-    phase_accept<LOG>(P, T, S, nch, sd, sh, &warp_off, &warp_n);
+    phase_accept<LOG>(P, T, S, nch, sd, sh, sum_gen0 + (uint32_t)run + 1u);
     stamp(2);
     if (!team_sync(T, ctl, P.wait_ns, 21)) return false;
     stamp(4);
-    int n_acc;
-    phase_append(P, T, S, nch, warp_off, warp_n, &n_acc);
-    stamp(5);
-    if (!team_sync(T, ctl, P.wait_ns, 22)) return false;
-    stamp(7);
+    if (timer) phase_ns[5] = phase_ns[7] = 0;
     const int t_old = n_tree;
+    int n_acc;
+    ve_off = phase_nodesets<SYS, LOG>(P, T, it, t_old, lam, sh, &n_acc);
     n_tree = t_old + n_acc;
-    ve_off = phase_nodesets<SYS, LOG>(P, T, it, t_old, n_tree, lam, sh);
     stamp(8);
     if (!team_sync(T, ctl, P.wait_ns, 23)) return false;
     stamp(9);
