@@ -122,7 +122,7 @@ struct Dims {
 };
 
 struct Layout {
-  size_t ctl, boxes, st, parent, ctrl, steps, region, sub, in_ve, cs, flags, acc_key,
+  size_t ctl, boxes, st, parent, ctrl, steps, region, sub, in_ve, cs, xs, flags, acc_key,
       n_valid, n_invalid, cov, avail, visited, claim, score, thr, ve, blk_a, blk_b, chunk_sum,
       stats, traj, feat, net_raw, kd_node, kd_split, leaf_box, region_vol, total;
 };
@@ -152,6 +152,7 @@ Layout make_layout(const Dims& d) {
   L.sub = take(te * 4);
   L.in_ve = take(te);
   L.cs = take(te * 4);
+  L.xs = take(te * d.D * 4);
   L.flags = take(te);
   L.acc_key = take(te * 4);
   L.n_valid = take((size_t)d.R_tab * 4);
@@ -744,6 +745,7 @@ void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* 
   P.node_sub = reinterpret_cast<int32_t*>(A + lay.sub);
   P.in_ve = reinterpret_cast<uint8_t*>(A + lay.in_ve);
   P.cs = reinterpret_cast<int32_t*>(A + lay.cs);
+  P.xs = reinterpret_cast<float*>(A + lay.xs);
   P.acc_key = reinterpret_cast<uint32_t*>(A + lay.acc_key);
   P.flags = reinterpret_cast<uint8_t*>(A + lay.flags);
   P.n_valid = reinterpret_cast<uint32_t*>(A + lay.n_valid);

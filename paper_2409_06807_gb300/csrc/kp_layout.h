@@ -163,6 +163,7 @@ struct KParams {
   uint8_t* in_ve;
   // per-sample scratch, indexed by sample key (< t_e)
   int32_t* cs;        // sub-region of a contender (claim check)
+  float* xs;          // [D][t_e] end state of a sample that may be accepted
   uint8_t* flags;     // KP_F_* of the sample
   // accepted samples: each accept warp compacts its keys (winner flag in
   // bit 31) at the start of its own key range, in key order

@@ -311,23 +311,21 @@ __device__ __forceinline__ void box_muller4(uint4 w, float* z) {
 }
 
 // The draw of sample key (V_E position p = key / lam, j = key - p lam) in
-// pass it (Algorithm 2: random control in U, random duration): loads the
-// parent's state into x and returns the parent's node id.  Counter (it,
-// node, j, purpose): purpose 0 the control words (kept in wr), purpose 1
-// (duration, accept word, selector); with a network attached and the
-// selector below the mix threshold, the control and duration come from the
-// node's Gaussian with normals from purpose 3.  The expand phase and the
-// append (which re-derives accepted samples from their keys) both draw
-// through this function, so both see the same numbers.
+// pass it (Algorithm 2: random control in U, random duration): returns the
+// parent's node id.  Counter (it, node, j, purpose): purpose 0 the control
+// words (kept in wr), purpose 1 (duration, accept word, selector); with a
+// network attached and the selector below the mix threshold, the control
+// and duration come from the node's Gaussian with normals from purpose 3.
+// The expand phase and the node-set phase (which appends accepted samples
+// by their keys) both draw through this function, so both see the same
+// numbers.
 template <int SYS>
-__device__ __forceinline__ int draw_sample(const KParams& P, uint32_t it, int key, int lam, float* x,
-                                           float* u, int* k, uint32_t* wacc, uint32_t* wr) {
-  constexpr int D = System<SYS>::D, N = System<SYS>::N;
+__device__ __forceinline__ int draw_controls(const KParams& P, uint32_t it, int key, int lam,
+                                             float* u, int* k, uint32_t* wacc, uint32_t* wr) {
+  constexpr int N = System<SYS>::N;
   const int p = key / lam;
   const int j = key - p * lam;
   const int v = P.ve[p];
-#pragma unroll
-  for (int d = 0; d < D; ++d) x[d] = P.st[(size_t)d * P.t_e + v];
   const uint4 w0 = philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 0u), P.seed_lo, P.seed_hi);
   const uint4 w1 = philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 1u), P.seed_lo, P.seed_hi);
   wr[0] = w0.x; wr[1] = w0.y; wr[2] = w0.z; wr[3] = w0.w;
@@ -350,6 +348,18 @@ __device__ __forceinline__ int draw_sample(const KParams& P, uint32_t it, int ke
     *k = kk < P.k_min + (int)P.k_span - 1 ? kk : P.k_min + (int)P.k_span - 1;
   }
   *wacc = w1.y;
+  return v;
+}
+
+// The draw of sample 'key' and its parent's state (the start of the
+// segment).
+template <int SYS>
+__device__ __forceinline__ int draw_sample(const KParams& P, uint32_t it, int key, int lam, float* x,
+                                           float* u, int* k, uint32_t* wacc, uint32_t* wr) {
+  constexpr int D = System<SYS>::D;
+  const int v = draw_controls<SYS>(P, it, key, lam, u, k, wacc, wr);
+#pragma unroll
+  for (int d = 0; d < D; ++d) x[d] = P.st[(size_t)d * P.t_e + v];
   return v;
 }
 
@@ -426,10 +436,14 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
             f |= KP_F_BERN;
             P.avail[r] = 1;
           }
-          // an accepted sample is re-derived from its key when it is
-          // appended; only a contender's sub-region is kept for the claim
-          // check
+          // a sample that may be accepted (a contender, or past its draw)
+          // keeps its end state for the append, and a contender its
+          // sub-region for the claim check
           if (cont) P.cs[key] = s;
+          if (cont || bern) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) P.xs[(size_t)d * P.t_e + key] = x[d];
+          }
         } else {
           atomicAdd(&P.n_invalid[r], 1u);
         }
@@ -736,14 +750,15 @@ __device__ __forceinline__ void phase_thresholds(const KParams& P, const Team& T
 
 // Materialises this block's accepted samples as the nodes id0 .. id0 +
 // acc_tot - 1 (id0 = t_old + the accepted samples of the blocks before it:
-// node ids follow the sample keys).  Every accepted sample is re-derived
-// from its key (the same draw and the same integrator steps as in the
-// expand phase, so the same numbers) and written to the tree with its
-// parent, control, duration, region and sub-region; visited and the goal
-// test (closed ball on position; the smallest new goal node wins) follow.
-// Thread j of the block takes the block's samples j, j + blockDim.x, ...;
-// consecutive threads write consecutive nodes.  With the sample log on, the
-// re-derived state is compared with the logged one.
+// node ids follow the sample keys).  Every accepted sample takes the end
+// state the expand phase kept for it, its parent, control and duration
+// from its key (the same draw), and its region and sub-region; visited and
+// the goal test (closed ball on position; the smallest new goal node wins)
+// follow.  Thread j of the block takes the block's samples j, j +
+// blockDim.x, ...; consecutive threads write consecutive nodes.  With the
+// sample log on, the sample is also re-derived from its key (the same
+// integrator steps, explicitly rounded, so the same numbers) and must match
+// the kept and the logged state bit for bit.
 template <int SYS, bool LOG>
 __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int id0, int lam,
                                             const LoopShared& sh) {
@@ -760,8 +775,9 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int i
     float x[D], u[N];
     int k;
     uint32_t wacc, wr[4];
-    const int v = draw_sample<SYS>(P, it, key, lam, x, u, &k, &wacc, wr);
-    for (int st = 0; st < k; ++st) Sys::step(x, u, P.dt, P);
+    const int v = draw_controls<SYS>(P, it, key, lam, u, &k, &wacc, wr);
+#pragma unroll
+    for (int d = 0; d < D; ++d) x[d] = P.xs[(size_t)d * P.t_e + key];
     int r, s;
     bin_state<SYS>(x, P, &r, &s);
 #pragma unroll
@@ -794,10 +810,15 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int i
     }
     if (LOG && key < P.log.capacity) {
       if (goal) P.log.flags[key] |= (uint8_t)KP_F_GOAL;
+      float y[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) y[d] = P.st[(size_t)d * P.t_e + v];
+      for (int st = 0; st < k; ++st) Sys::step(y, u, P.dt, P);
       bool same = P.log.region[key] == r && P.log.sub[key] == s;
 #pragma unroll
       for (int d = 0; d < D; ++d)
-        same = same && __float_as_uint(P.log.state[12 * (size_t)key + d]) == __float_as_uint(x[d]);
+        same = same && __float_as_uint(P.log.state[12 * (size_t)key + d]) == __float_as_uint(x[d]) &&
+               __float_as_uint(y[d]) == __float_as_uint(x[d]);
       if (!same) raise_error(P.ctl, KP_DEV_ERR_REPLAY, 40);
     }
   }
