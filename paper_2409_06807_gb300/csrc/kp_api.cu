@@ -143,7 +143,9 @@ Layout make_layout(const Dims& d) {
   };
   const size_t te = (size_t)d.t_e;
   L.ctl = take(sizeof(KCtl));
-  L.boxes = take((size_t)KP_BLOB_BYTES);  // room for any obstacle set and its grid
+  // room for any obstacle set and its grid (and a compact copy of a kd-tree
+  // after it, staged with it when shared memory allows)
+  L.boxes = take((size_t)KP_BLOB_BYTES + (d.fso ? kKdNodes * 8 : 0));
   L.st = take(te * d.D * 4);
   L.parent = take(te * 4);
   L.ctrl = take(te * d.N * 4);
@@ -266,6 +268,8 @@ struct kp_ctx {
   uint64_t wait_ns;
   int grid[2];
   size_t smem;
+  int blob_base;  // blob bytes without the kd-tree copy
+  int blob_kd;    // blob bytes with it (0: no tree)
   std::string err;
   void* pinned;
   size_t pinned_bytes;
@@ -535,12 +539,13 @@ bool kd_cell(KdTree& T, const float* fb, const std::vector<int>& ids, const floa
 // offsets relative to lay.kd_node).  Returns the leaf count, 0 past the
 // limits.
 int build_kd(unsigned char* host, const float* fb, int nb, const kp_workspace& ws,
-             const Layout& lay) {
+             const Layout& lay, int* n_nodes) {
   KdTree T;
   std::vector<int> all((size_t)nb);
   for (int b = 0; b < nb; ++b) all[(size_t)b] = b;
   if (!kd_cell(T, fb, all, ws.lo, ws.hi, 0)) return 0;
   const int leaves = (int)(T.lo.size() / 3);
+  *n_nodes = (int)T.node.size();
   int32_t* node = reinterpret_cast<int32_t*>(host);
   float* split = reinterpret_cast<float*>(host + (lay.kd_split - lay.kd_node));
   float* box = reinterpret_cast<float*>(host + (lay.leaf_box - lay.kd_node));
@@ -585,16 +590,20 @@ kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
   // build the blob (and the kd-tree) in pinned host memory, then async copies
   const Layout& L = ctx->lay;
   const size_t kd_bytes = ctx->dims.fso ? L.total - L.kd_node : 0;
-  kp_status ps = ensure_pinned(ctx, (size_t)KP_BLOB_BYTES + kd_bytes + sizeof(KCtl));
+  kp_status ps = ensure_pinned(ctx, (size_t)KP_BLOB_BYTES + (ctx->dims.fso ? kKdNodes * 8 : 0) +
+                                        kd_bytes + sizeof(KCtl));
   if (ps != KP_OK) return ps;
   KP_CUDA(cudaStreamSynchronize(ctx->stream));  // the staging buffer is free
   unsigned char* host = static_cast<unsigned char*>(ctx->pinned);
   const size_t bytes = build_blob(host, nb > 0 ? obs->boxes : nullptr, nb, ctx->ws, ctx->P);
   KP_CUDA(cudaMemcpyAsync(ctx->arena + L.boxes, host, bytes, cudaMemcpyHostToDevice,
                           ctx->stream));
+  ctx->blob_base = (int)bytes;
+  ctx->blob_kd = 0;
   if (ctx->dims.fso) {
-    unsigned char* kd = host + (size_t)KP_BLOB_BYTES;
-    const int leaves = build_kd(kd, reinterpret_cast<const float*>(host), nb, ctx->ws, L);
+    unsigned char* kd = host + (size_t)KP_BLOB_BYTES + kKdNodes * 8;
+    int n_nodes = 0;
+    const int leaves = build_kd(kd, reinterpret_cast<const float*>(host), nb, ctx->ws, L, &n_nodes);
     if (leaves == 0) {
       KP_CUDA(cudaStreamSynchronize(ctx->stream));
       return fail(ctx, KP_ERR_ARG, "kd-tree decomposition above %d leaves or depth %d",
@@ -602,6 +611,15 @@ kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
     }
     KP_CUDA(cudaMemcpyAsync(ctx->arena + L.kd_node, kd, kd_bytes, cudaMemcpyHostToDevice,
                             ctx->stream));
+    // the compact copy (codes, then splits) right after the blob
+    const size_t at = round16(bytes);
+    std::memset(host + bytes, 0, at - bytes);
+    std::memcpy(host + at, kd, (size_t)n_nodes * 4);
+    std::memcpy(host + at + (size_t)n_nodes * 4, kd + (L.kd_split - L.kd_node), (size_t)n_nodes * 4);
+    ctx->blob_kd = (int)round16(at + (size_t)n_nodes * 8);
+    ctx->P.kd_n = n_nodes;
+    KP_CUDA(cudaMemcpyAsync(ctx->arena + L.boxes + bytes, host + bytes, ctx->blob_kd - bytes,
+                            cudaMemcpyHostToDevice, ctx->stream));
     Dims& d = ctx->dims;
     d.R = leaves;
     d.R_pad = 1;
@@ -618,6 +636,8 @@ kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
 
 kp_status configure_launch(kp_ctx* ctx) {
   const Dims& d = ctx->dims;
+  ctx->P.blob_bytes = ctx->blob_base;
+  ctx->P.kd_smem_off = -1;
   // shared memory: boxes + the double scratch of the region-score sums (a
   // chunk's scores, then the chunk sums) + the network tile (learned form)
   auto grids = [&](int sd) -> kp_status {
@@ -646,7 +666,22 @@ kp_status configure_launch(kp_ctx* ctx) {
   // ... then with the scratch this chunking needs (smaller shared memory
   // never lowers the grid, so nch stays at most the grid)
   const int need = d.R_pad / nch > nch ? d.R_pad / nch : nch;
-  return grids(need);
+  s = grids(need);
+  if (s != KP_OK || ctx->blob_kd == 0) return s;
+  // the kd-tree goes into shared memory with the blob when that keeps the
+  // resident blocks (it is read at every binning)
+  const size_t smem_kd = ctx->smem + (size_t)(ctx->blob_kd - ctx->blob_base);
+  for (int log = 0; log < 2; ++log) {
+    int bps = 0;
+    KP_CUDA(occupancy(d.sys, log != 0, smem_kd, &bps));
+    int g = bps * ctx->num_sms;
+    if (g > KP_MAX_GRID) g = KP_MAX_GRID;
+    if (g < ctx->grid[log]) return KP_OK;
+  }
+  ctx->P.blob_bytes = ctx->blob_kd;
+  ctx->P.kd_smem_off = (int)round16((size_t)ctx->blob_base);
+  ctx->smem = smem_kd;
+  return KP_OK;
 }
 
 kp_status clear_tables(kp_ctx* ctx) {
@@ -730,6 +765,7 @@ void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* 
   P.eps = prm->eps;
   P.vol = vol;
   P.fso = d.fso;
+  P.kd_smem_off = -1;
   if (d.fso) {
     P.kd_node = reinterpret_cast<const int32_t*>(A + lay.kd_node);
     P.kd_split = reinterpret_cast<const float*>(A + lay.kd_split);
@@ -1176,7 +1212,8 @@ kp_status kp_grow(kp_ctx* ctx, void* dev_arena, size_t arena_bytes, int32_t t_e)
   std::memcpy(ctx->pinned, &h, sizeof(KCtl));
   KP_CUDA(cudaMemcpyAsync(dst + nl.ctl, ctx->pinned, sizeof(KCtl), cudaMemcpyHostToDevice,
                           ctx->stream));
-  if ((s = d2d(nl.boxes, ol.boxes, (size_t)ctx->P.blob_bytes)) != KP_OK) return s;
+  const int blob_all = ctx->blob_kd > ctx->blob_base ? ctx->blob_kd : ctx->blob_base;
+  if ((s = d2d(nl.boxes, ol.boxes, (size_t)blob_all)) != KP_OK) return s;
   if (od.fso && (s = d2d(nl.kd_node, ol.kd_node, ol.total - ol.kd_node)) != KP_OK) return s;
   // the tree: SoA rows move to the new stride
   if (n) {
@@ -1209,6 +1246,8 @@ kp_status kp_grow(kp_ctx* ctx, void* dev_arena, size_t arena_bytes, int32_t t_e)
   KParams& P = ctx->P;
   P.n_boxes_pad = old.n_boxes_pad;
   P.blob_bytes = old.blob_bytes;
+  P.kd_n = old.kd_n;
+  P.kd_smem_off = old.kd_smem_off;
   P.bp_g = old.bp_g;
   P.bp_start_off = old.bp_start_off;
   P.bp_ids_off = old.bp_ids_off;

@@ -354,19 +354,25 @@ __device__ __forceinline__ int fine_cell(float t, int n) {
 
 // Region and sub-region under the kd-tree decomposition: descend from the
 // root (below a plane goes left, to node + 1), then the sub-grid cell of the
-// leaf's own box.  The tree is built on the host with depth at most
-// KP_FSO_MAX_DEPTH and every child index above its parent's, so the walk
-// ends; the bound only guards it.
-__device__ __forceinline__ void bin_fso(const float* x, const KParams& P, int* region,
-                                        int* sub) {
+// leaf's own box.  The tree is read from the staged blob in shared memory
+// when it was staged (sblob given and kd_smem_off >= 0), else from global
+// memory.  It is built on the host with depth at most KP_FSO_MAX_DEPTH and
+// every child index above its parent's, so the walk ends; the bound only
+// guards it.
+__device__ __forceinline__ void bin_fso(const float* x, const KParams& P, int* region, int* sub,
+                                        const unsigned char* sblob) {
+  const bool staged = sblob != nullptr && P.kd_smem_off >= 0;
+  const int32_t* codes =
+      staged ? reinterpret_cast<const int32_t*>(sblob + P.kd_smem_off) : P.kd_node;
+  const float* splits = staged ? reinterpret_cast<const float*>(codes + P.kd_n) : P.kd_split;
   // codes are read unsigned: the tag sits in the top two bits
   int node = 0;
-  uint32_t code = (uint32_t)__ldg(P.kd_node);
+  uint32_t code = (uint32_t)codes[0];
   for (int depth = 0; (code >> 30) != 3u && depth < KP_FSO_MAX_DEPTH; ++depth) {
     const uint32_t a = code >> 30;
     const float xa = a == 0u ? x[0] : (a == 1u ? x[1] : x[2]);
-    node = xa < __ldg(P.kd_split + node) ? node + 1 : (int)(code & 0x3fffffffu);
-    code = (uint32_t)__ldg(P.kd_node + node);
+    node = xa < splits[node] ? node + 1 : (int)(code & 0x3fffffffu);
+    code = (uint32_t)codes[node];
   }
   const int r = (code >> 30) == 3u ? (int)(code & 0x3fffffffu) : 0;
   const float4 lo = __ldg(P.leaf_box + 2 * r);
@@ -379,10 +385,10 @@ __device__ __forceinline__ void bin_fso(const float* x, const KParams& P, int* r
 }
 
 template <int SYS>
-__device__ __forceinline__ void bin_state(const float* x, const KParams& P, int* region,
-                                          int* sub) {
+__device__ __forceinline__ void bin_state(const float* x, const KParams& P, int* region, int* sub,
+                                          const unsigned char* sblob = nullptr) {
   if (P.fso) {
-    bin_fso(x, P, region, sub);
+    bin_fso(x, P, region, sub, sblob);
     return;
   }
   int cell[3], fine[3];

@@ -126,6 +126,9 @@ struct KParams {
   // for a leaf; leaf r: leaf_box[2r] = lo.xyz, leaf_box[2r+1] = sub-grid
   // cells per unit length; region_vol[r] = its volume (Eq. 3)
   int32_t fso;
+  int32_t kd_n;         // tree nodes
+  int32_t kd_smem_off;  // byte offset in the staged blob of a copy of the
+                        // codes (kd_n) then the splits (kd_n); -1: global
   const int32_t* kd_node;
   const float* kd_split;
   const float4* leaf_box;

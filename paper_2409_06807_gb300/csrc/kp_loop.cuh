@@ -415,7 +415,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
       // ---- finalise the lanes that finished -------------------------------
       if (key >= 0 && done) {
         int r, s;
-        bin_state<SYS>(x, P, &r, &s);
+        bin_state<SYS>(x, P, &r, &s, sblob);
         const bool valid = fail == 0;
         uint32_t f = 0;
         if (valid) {
@@ -761,7 +761,7 @@ __device__ __forceinline__ void phase_thresholds(const KParams& P, const Team& T
 // the kept and the logged state bit for bit.
 template <int SYS, bool LOG>
 __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int id0, int lam,
-                                            const LoopShared& sh) {
+                                            const LoopShared& sh, const unsigned char* sblob) {
   using Sys = System<SYS>;
   constexpr int D = Sys::D, N = Sys::N;
   for (int j = (int)threadIdx.x; j < sh.acc_tot; j += (int)blockDim.x) {
@@ -779,7 +779,7 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int i
 #pragma unroll
     for (int d = 0; d < D; ++d) x[d] = P.xs[(size_t)d * P.t_e + key];
     int r, s;
-    bin_state<SYS>(x, P, &r, &s);
+    bin_state<SYS>(x, P, &r, &s, sblob);
 #pragma unroll
     for (int d = 0; d < D; ++d) P.st[(size_t)d * P.t_e + id] = x[d];
 #pragma unroll
@@ -833,7 +833,8 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int i
 // members without reading their sets.
 template <int SYS, bool LOG>
 __device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, uint32_t it,
-                                              int t_old, int lam, LoopShared& sh, int* n_new) {
+                                              int t_old, int lam, LoopShared& sh, int* n_new,
+                                              const unsigned char* sblob) {
   unsigned long long acc_before, acc_total;
   block_prefix(T, P.blk_a, sh, &acc_before, &acc_total);
   *n_new = (int)acc_total;
@@ -854,7 +855,7 @@ __device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, u
   int tot;
   const int off = block_exclusive_scan(c, sh.scan, &tot);
   if (threadIdx.x == 0) P.blk_b[T.b] = (uint32_t)tot;
-  materialise<SYS, LOG>(P, it, t_old + (int)acc_before, lam, sh);
+  materialise<SYS, LOG>(P, it, t_old + (int)acc_before, lam, sh, sblob);
   return off;
 }
 
@@ -938,7 +939,7 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     if (timer) phase_ns[5] = phase_ns[7] = 0;
     const int t_old = n_tree;
     int n_acc;
-    ve_off = phase_nodesets<SYS, LOG>(P, T, it, t_old, lam, sh, &n_acc);
+    ve_off = phase_nodesets<SYS, LOG>(P, T, it, t_old, lam, sh, &n_acc, smem);
     n_tree = t_old + n_acc;
     stamp(8);
     if (!team_sync(T, ctl, P.wait_ns, 23)) return false;
