@@ -154,7 +154,7 @@ Layout make_layout(const Dims& d) {
   L.sub = take(te * 4);
   L.in_ve = take(te);
   L.cs = take(te * 4);
-  L.xs = take(te * d.D * 4);
+  L.xs = take(te * (size_t)kp_xs_stride(d.D) * 4);
   L.flags = take(te);
   L.acc_key = take(te * 4);
   L.n_valid = take((size_t)d.R_tab * 4);

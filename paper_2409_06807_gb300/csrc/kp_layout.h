@@ -35,6 +35,8 @@ constexpr int KP_BP_MAX_IDS = 32768;   // broad-phase (cell, box) entries
 constexpr int KP_BLOB_BYTES = 4096 * 32 + (KP_BP_MAX_G * KP_BP_MAX_G * KP_BP_MAX_G + 4) * 4 +
                               KP_BP_MAX_IDS * 2;  // arena room for the obstacle blob
 constexpr int KP_FSO_MAX_LEAVES = 16384; // regions of a kd-tree decomposition
+// floats per kept end state (one aligned row of whole 32-byte sectors per key)
+__host__ __device__ constexpr int kp_xs_stride(int D) { return D <= 8 ? 8 : 16; }
 constexpr int KP_FSO_MAX_DEPTH = 64;     // its deepest leaf
 
 // Device control block (one per context, in the arena).
@@ -166,7 +168,7 @@ struct KParams {
   uint8_t* in_ve;
   // per-sample scratch, indexed by sample key (< t_e)
   int32_t* cs;        // sub-region of a contender (claim check)
-  float* xs;          // [D][t_e] end state of a sample that may be accepted
+  float* xs;          // [t_e][kp_xs_stride(D)] end state of a sample that may be accepted
   uint8_t* flags;     // KP_F_* of the sample
   // accepted samples: each accept warp compacts its keys (winner flag in
   // bit 31) at the start of its own key range, in key order

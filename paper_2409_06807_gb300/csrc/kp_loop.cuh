@@ -423,26 +423,34 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
           f = KP_F_VALID;
           const bool cont = P.visited[s] == 0;
           const bool bern = (uint64_t)wacc < P.thr[r];
+          bool may_win = false;
           if (cont) {
             f |= KP_F_CONTENDER;
             // the first claimant of a sub-region knows it is newly reached:
-            // it will get exactly one representative in region r
-            if (atomicMin(&P.claim[s], (uint32_t)key) == 0xffffffffu) {
+            // it will get exactly one representative in region r; a
+            // claimant that finds a smaller key there has already lost
+            const uint32_t prev = atomicMin(&P.claim[s], (uint32_t)key);
+            if (prev == 0xffffffffu) {
               atomicAdd(&P.cov[r], 1u);
               P.avail[r] = 1;
             }
+            may_win = prev > (uint32_t)key;
           }
           if (bern) {
             f |= KP_F_BERN;
             P.avail[r] = 1;
           }
-          // a sample that may be accepted (a contender, or past its draw)
-          // keeps its end state for the append, and a contender its
-          // sub-region for the claim check
+          // a sample that may still be accepted (a contender not yet beaten,
+          // or past its draw) keeps its end state for the append, and a
+          // contender its sub-region for the claim check
           if (cont) P.cs[key] = s;
-          if (cont || bern) {
+          if (may_win || bern) {
+            float4* row = reinterpret_cast<float4*>(P.xs + (size_t)key * kp_xs_stride(D));
 #pragma unroll
-            for (int d = 0; d < D; ++d) P.xs[(size_t)d * P.t_e + key] = x[d];
+            for (int q = 0; q < kp_xs_stride(D) / 4; ++q)
+              row[q] = make_float4(4 * q < D ? x[4 * q] : 0.0f, 4 * q + 1 < D ? x[4 * q + 1] : 0.0f,
+                                   4 * q + 2 < D ? x[4 * q + 2] : 0.0f,
+                                   4 * q + 3 < D ? x[4 * q + 3] : 0.0f);
           }
         } else {
           atomicAdd(&P.n_invalid[r], 1u);
@@ -776,8 +784,17 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int i
     int k;
     uint32_t wacc, wr[4];
     const int v = draw_controls<SYS>(P, it, key, lam, u, &k, &wacc, wr);
+    {
+      const float4* row = reinterpret_cast<const float4*>(P.xs + (size_t)key * kp_xs_stride(D));
 #pragma unroll
-    for (int d = 0; d < D; ++d) x[d] = P.xs[(size_t)d * P.t_e + key];
+      for (int q = 0; q < (D + 3) / 4; ++q) {
+        const float4 c = row[q];
+        if (4 * q < D) x[4 * q] = c.x;
+        if (4 * q + 1 < D) x[4 * q + 1] = c.y;
+        if (4 * q + 2 < D) x[4 * q + 2] = c.z;
+        if (4 * q + 3 < D) x[4 * q + 3] = c.w;
+      }
+    }
     int r, s;
     bin_state<SYS>(x, P, &r, &s, sblob);
 #pragma unroll
