@@ -248,6 +248,31 @@ def cpu_baseline(make, budget_s=15.0):
                       f"(seeds {seeds[0]}..{seeds[-1]}), {n_tot} samples, single thread"}
 
 
+def _oracle_job(job):
+    name, seed, passes = job
+    return oracle_sample(W.BY_NAME[name], seed, passes)
+
+
+def cpu_baseline_all_cores(name, passes=3):
+    """The same oracle on every host core: one process per core (spawned,
+    so no GPU state is inherited), taking seeded layouts one at a time from
+    a list of four per core (layouts are independent problems).  Aggregate
+    samples over the wall time of the pool's work, process start-up
+    excluded."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    seeds = [10_000 + i for i in range(4 * cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_job, [(name, s, 1) for s in seeds[:cores]], chunksize=1)  # start-up
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_job, [(name, s, passes) for s in seeds], chunksize=1)
+        wall = time.perf_counter() - t0
+    n = sum(r[0] for r in res)
+    return {"value": n / wall, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {passes} loop passes of {len(seeds)} seeded layouts (seeds "
+                      f"{seeds[0]}..{seeds[-1]}), one process per core, {n} samples"}
+
+
 def run_reference(args, world, rank):
     """The FP64 oracle timed on this host as the reference arm."""
     if rank != 0:
@@ -428,6 +453,24 @@ def decomposition_leg(local, flush, n_layouts=100):
         pl.close()
         out[name] = mode_summary(rows, P.OK)
         out[name]["regions"] = float(np.mean([r[2]["n_regions"] for r in rows]))
+    out["workload"] = f"Dubins forest (200 boxes), {n_layouts} layouts (seeds {seeds[0]}..{seeds[-1]})"
+    return out
+
+
+def eps_leg(local, flush, n_layouts=50):
+    """Sensitivity to eps of Eq. 5 (the floor of P_accept, Lemma 1): the
+    Dubins forest with eps 1e-3, 1e-2 (the default) and 5e-2, same layouts
+    and random stream."""
+    from paper_2409_06807_gb300 import planner as P
+    seeds = list(range(60_000, 60_000 + n_layouts))
+    out = {}
+    for eps in (1e-3, 1e-2, 5e-2):
+        make = lambda s: W.c2(s, eps=eps)
+        pl = P.Planner(make(seeds[0]), device=f"cuda:{local}")
+        timed_query(pl, make(seeds[0]), flush, MAX_ITERS)  # warm
+        rows = [timed_query(pl, make(s), flush, MAX_ITERS) for s in seeds]
+        pl.close()
+        out[f"eps_{eps:g}"] = mode_summary(rows, P.OK)
     out["workload"] = f"Dubins forest (200 boxes), {n_layouts} layouts (seeds {seeds[0]}..{seeds[-1]})"
     return out
 
@@ -630,6 +673,8 @@ def run_ours(args, world, rank, local):
         extra["steady_state"] = steady_state_leg(local, peak_ops)
     if args.decomp_layouts > 0:
         extra["decomposition"] = decomposition_leg(local, flush, args.decomp_layouts)
+    if args.eps_layouts > 0:
+        extra["eps_sweep"] = eps_leg(local, flush, args.eps_layouts)
     if args.te_layouts > 0:
         extra["t_e_sweep"] = te_sweep_leg(local, flush, args.te_layouts)
     if args.learned_layouts > 0:
@@ -639,6 +684,8 @@ def run_ours(args, world, rank, local):
         extra["serving"] = serving_leg(args.serve_queries, 2000.0, args.serve_pool_gb, local,
                                        flush)
     cpu = cpu_baseline(make) if world == 1 and not args.no_cpu else None
+    if cpu is not None:
+        cpu["all_cores"] = cpu_baseline_all_cores(args.workload)
     pct = np.percentile(step_ms, [50, 99])
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
@@ -681,6 +728,8 @@ def main():
                     help="held-out layouts of the learned-vs-plain comparison (0: skip)")
     ap.add_argument("--decomp-layouts", type=int, default=100,
                     help="layouts of the decomposition comparison (0: skip)")
+    ap.add_argument("--eps-layouts", type=int, default=50,
+                    help="layouts of the eps sensitivity sweep (0: skip)")
     ap.add_argument("--te-layouts", type=int, default=20,
                     help="layouts of the node-cap sweep on the quadrotor (0: skip)")
     ap.add_argument("--serve-queries", type=int, default=512,

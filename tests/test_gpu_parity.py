@@ -486,3 +486,57 @@ def test_grow_fso_keeps_leaves(P):
     assert compare_pass(w2, ost, orec, gs[0], g.read_log(ost["n_samples"])) <= 2
     compare_trees(w2, g.export_tree(), o.export())
 
+
+
+# ---------------------------------------------------------------------------
+# whole queries, statistically: device vs oracle over 100 seeds
+# ---------------------------------------------------------------------------
+
+def _oracle_full_run(seed):
+    """(solved, passes, |T|) of the oracle's whole C1 query (run in a spawned
+    worker: module-level so that it pickles by name)."""
+    o = Oracle(W.c1(seed))
+    o.reset()
+    status, passes = o.run(200)
+    return status == kpo.SOLVED, passes, o.n_nodes
+
+
+def _ks(a, b):
+    """Two-sample Kolmogorov-Smirnov statistic."""
+    a, b = np.sort(np.asarray(a, float)), np.sort(np.asarray(b, float))
+    grid = np.concatenate([a, b])
+    fa = np.searchsorted(a, grid, side="right") / len(a)
+    fb = np.searchsorted(b, grid, side="right") / len(b)
+    return float(np.max(np.abs(fa - fb)))
+
+
+def test_whole_queries_match_oracle_statistically(P):
+    """Whole queries cannot match exactly (FP32 against FP64 decisions near
+    a face eventually split the trees), so C1 queries on 100 seeds are
+    compared in law: success rate, passes to solve and tree size at the
+    solution.  The two-sample KS statistic must stay below its 0.1 %
+    critical value (1.95 sqrt(2/100) = 0.276), and most seeds must run the
+    same number of passes (lock-step passes match exactly until a split)."""
+    import multiprocessing as mp
+    import os
+    seeds = list(range(100, 200))
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        orc = pool.map(_oracle_full_run, seeds, chunksize=1)
+    dev = []
+    for s in seeds:
+        w = W.c1(s)
+        g = P.Planner(w)
+        st, _ = g.plan(max_iters=200)
+        info = g.info()
+        dev.append((st == P.OK, info["iteration"], info["n_nodes"]))
+        g.close()
+    o_ok = np.array([r[0] for r in orc])
+    d_ok = np.array([r[0] for r in dev])
+    assert abs(o_ok.mean() - d_ok.mean()) <= 0.05
+    o_it, d_it = [r[1] for r in orc], [r[1] for r in dev]
+    o_n, d_n = [r[2] for r in orc], [r[2] for r in dev]
+    assert _ks(o_it, d_it) <= 0.276, (_ks(o_it, d_it), np.mean(o_it), np.mean(d_it))
+    assert _ks(o_n, d_n) <= 0.276, (_ks(o_n, d_n), np.mean(o_n), np.mean(d_n))
+    assert abs(np.mean(o_n) / np.mean(d_n) - 1.0) <= 0.1
+    same = np.mean(np.array(o_it) == np.array(d_it))
+    assert same >= 0.5, same
