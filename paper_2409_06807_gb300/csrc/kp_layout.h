@@ -55,7 +55,7 @@ struct KCtl {
   int32_t n_edges;     // trajectory extraction: edges on the chain
   int32_t work_next;   // next sample key handed out in the expand phase
   uint32_t s_done;     // region chunks whose Score partial sum is written
-  uint32_t sum_gen;    // generation of the published Eq. 5 sum (one per pass)
+  uint32_t t_done;     // region chunks whose thresholds are written, this pass
   double score_sum;    // sum of Eq. 5 over R_avail, this pass
   // work counters since the last reset (samples, integrator steps run,
   // segment hulls tested against the obstacle set)

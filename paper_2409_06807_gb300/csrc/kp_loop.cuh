@@ -40,7 +40,7 @@ struct LoopShared {
   unsigned long long red[64];
   uint64_t mbar;
   int flag;
-  int bcast[3];
+  int bcast[2];
   int32_t phase_ns[12];  // per-pass phase timers (block 0, thread 0)
   // accepted samples of this block, from the accept phase to the node-set
   // phase: warp w compacted acc_n[w] keys at acc_key[acc_a[w]...], which
@@ -568,19 +568,18 @@ __device__ __forceinline__ void warp_range(int c0, int c1, int* a, int* b) {
 // takes keys t0 + 32q + l: every load is coalesced), with the loads of a
 // tile's flags, contenders' sub-regions and their claims issued together,
 // and compacts its accepted keys (claim winners marked in bit 31) in key
-// order at the start of its range in acc_key.  Phases S and T (warp 0) run
+// order at the start of its range in acc_key.  Phase S (warp 0) runs
 // alongside.  Publishes the block's accepted count, adds the valid count to
 // the pass, and leaves where each warp's accepted keys are, and their
 // offsets among the block's, in shared memory for the node-set phase.
 constexpr int KP_ACC_KPL = 8;
 
-__device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, int nch, double* sd,
-                                             uint32_t sum_gen);
+__device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, int nch, double* sd);
 
 template <bool LOG>
 __device__ __forceinline__ void phase_accept(const KParams& P, const Team& T, int S, int nch,
-                                             double* sd, LoopShared& sh, uint32_t sum_gen) {
-  if (threadIdx.x < 32) phase_scores(P, T, nch, sd, sum_gen);
+                                             double* sd, LoopShared& sh) {
+  if (threadIdx.x < 32) phase_scores(P, T, nch, sd);
   const uint32_t FULL = 0xffffffffu;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt = (1u << lane) - 1u;
@@ -654,21 +653,15 @@ __device__ __forceinline__ void warp_pairwise(double* buf, int n) {
   __syncwarp();
 }
 
-__device__ __forceinline__ void phase_thresholds(const KParams& P, const Team& T, int nch);
-
 // Phase S (warp 0): Eq. 3-4 for this block's region chunk and its pairwise
 // partial sum; the last chunk to finish reduces the partial sums into the
-// sum of Eq. 5 (same pairwise tree whichever block it is) and publishes it
-// with generation 'sum_gen'.  Every operation is an explicitly rounded IEEE
-// double operation in the order
+// sum of Eq. 5 (same pairwise tree whichever block it is), before the grid
+// barrier that ends the phase.  Every operation is an explicitly rounded
+// IEEE double operation in the order
 // FreeVol = ((delta + nv) vol) / ((delta + nv) + ni),
 // f4 = (FreeVol FreeVol)(FreeVol FreeVol),
 // Score = f4 / ((1 + Cov)(1 + (nv + ni)(nv + ni))).
-// Then phase T: every chunk waits (bounded) for the sum and writes its
-// thresholds.  Nothing in the accept phase reads thr, and the node-set
-// draws that do come after the grid barrier.
-__device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, int nch, double* sd,
-                                             uint32_t sum_gen) {
+__device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, int nch, double* sd) {
   if (T.b >= nch) return;
   const int lane = (int)(threadIdx.x & 31u);
   const int ch = P.R_pad / nch;
@@ -706,33 +699,14 @@ __device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, in
     if (lane == 0) {
       P.ctl->score_sum = sd[0];
       P.ctl->s_done = 0;  // for the next pass
-      __threadfence();
-      st_release(&P.ctl->sum_gen, sum_gen);
     }
   }
   __syncwarp();
-  int ok = 1;
-  if (lane == 0) {
-    const uint64_t t0 = global_ns();
-    uint32_t spins = 0;
-    while (ld_acquire(&P.ctl->sum_gen) != sum_gen) {
-      if ((++spins & 63u) == 0) {
-        if (*((volatile int*)&P.ctl->err) != 0) { ok = 0; break; }
-        if (global_ns() - t0 > P.wait_ns) {
-          raise_error(P.ctl, KP_DEV_ERR_TIMEOUT, 24);
-          ok = 0;
-          break;
-        }
-      }
-    }
-  }
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  __syncwarp();
-  if (ok) phase_thresholds(P, T, nch);
 }
 
-// Phase T (warp 0): P_accept and the integer threshold of this block's
-// region chunk (Eq. 5), from the sum the last chunk published.
+// Phase T (warp 0 of the node-set phase): P_accept and the integer
+// threshold of this block's region chunk (Eq. 5), from the sum the last
+// chunk published in the accept phase.
 __device__ __forceinline__ void phase_thresholds(const KParams& P, const Team& T, int nch) {
   if (T.b >= nch) return;
   const double sum = __ldcg(&P.ctl->score_sum);
@@ -845,17 +819,43 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int i
 // purpose 2) against the threshold of its region; new nodes are in V_E.
 // Returns this thread's offset among the block's V_E members and, in
 // *n_new, the number of accepted samples of the pass (the new nodes).
-// The new nodes (ids from t_old, in key order) are materialised here as
-// well, each block its own accepted samples; they are counted as V_E
-// members without reading their sets.
+// Order inside the phase: warp 0 of every region-chunk block first writes
+// its chunk's thresholds (phase T) and counts itself done; every block then
+// appends its own accepted samples (ids from t_old, in key order), which
+// needs no threshold; then it waits (bounded) until every chunk is done and
+// makes the node-set draws.  New nodes are counted as V_E members without
+// reading their sets.
 template <int SYS, bool LOG>
 __device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, uint32_t it,
                                               int t_old, int lam, LoopShared& sh, int* n_new,
                                               const unsigned char* sblob) {
+  const int nch = P.nch;
+  if (threadIdx.x < 32 && T.b < nch) {
+    phase_thresholds(P, T, nch);
+    __threadfence();
+    __syncwarp();
+    if (threadIdx.x == 0) atomicAdd(&P.ctl->t_done, 1u);
+  }
   unsigned long long acc_before, acc_total;
   block_prefix(T, P.blk_a, sh, &acc_before, &acc_total);
   *n_new = (int)acc_total;
   const int t_new = t_old + (int)acc_total;
+  materialise<SYS, LOG>(P, it, t_old + (int)acc_before, lam, sh, sblob);
+  if (threadIdx.x == 0) {
+    const uint64_t t0 = global_ns();
+    uint32_t spins = 0;
+    while (ld_acquire(&P.ctl->t_done) < (uint32_t)nch) {
+      if ((++spins & 63u) == 0) {
+        if (*((volatile int*)&P.ctl->err) != 0) break;
+        if (global_ns() - t0 > P.wait_ns) {
+          raise_error(P.ctl, KP_DEV_ERR_TIMEOUT, 25);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
   int v0, v1, r0, r1;
   chunk_of(T, t_new, &v0, &v1);
   thread_run(v0, v1, &r0, &r1);
@@ -872,7 +872,6 @@ __device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, u
   int tot;
   const int off = block_exclusive_scan(c, sh.scan, &tot);
   if (threadIdx.x == 0) P.blk_b[T.b] = (uint32_t)tot;
-  materialise<SYS, LOG>(P, it, t_old + (int)acc_before, lam, sh, sblob);
   return off;
 }
 
@@ -892,19 +891,16 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     ctl->n_run = 0;
     ctl->work_next = 0;
     ctl->s_done = 0;
+    ctl->t_done = 0;
   }
   // the loop state, read once per block
-  // (the generation of the published Eq. 5 sum, too: nothing writes it
-  // before the accept phase, so every block reads the same value)
   if (threadIdx.x == 0) {
     sh.bcast[0] = ctl->n_nodes;
     sh.bcast[1] = ctl->iteration;
-    sh.bcast[2] = (int)*((volatile uint32_t*)&ctl->sum_gen);
   }
   __syncthreads();
   int n_tree = sh.bcast[0];
   uint32_t it = (uint32_t)sh.bcast[1];
-  const uint32_t sum_gen0 = (uint32_t)sh.bcast[2];
   const int nch = P.nch;
 
   // V_E list from the stored node sets
@@ -949,7 +945,7 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     stamp(0);
     if (!team_sync(T, ctl, P.wait_ns, 20)) return false;
     stamp(1);
-    phase_accept<LOG>(P, T, S, nch, sd, sh, sum_gen0 + (uint32_t)run + 1u);
+    phase_accept<LOG>(P, T, S, nch, sd, sh);
     stamp(2);
     if (!team_sync(T, ctl, P.wait_ns, 21)) return false;
     stamp(4);
@@ -985,6 +981,7 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
         P.stats[run - 1] = s;
       }
       ctl->it_valid = 0;
+      ctl->t_done = 0;  // every block is past its threshold wait
       ctl->tot_samples += (unsigned long long)S;
       const bool out_of_time = max_ns > 0 && global_ns() - t_start >= max_ns;
       ctl->state = solved ? KP_DEV_SOLVED : (full ? KP_DEV_FULL : KP_DEV_RUNNING);
