@@ -54,7 +54,6 @@ struct KCtl {
   uint32_t it_valid;   // valid samples of the current pass
   int32_t n_edges;     // trajectory extraction: edges on the chain
   int32_t work_next;   // next sample key handed out in the expand phase
-  uint32_t s_done;     // region chunks whose Score partial sum is written
   uint32_t t_done;     // region chunks whose thresholds are written, this pass
   double score_sum;    // sum of Eq. 5 over R_avail, this pass
   // work counters since the last reset (samples, integrator steps run,

@@ -654,10 +654,9 @@ __device__ __forceinline__ void warp_pairwise(double* buf, int n) {
 }
 
 // Phase S (warp 0): Eq. 3-4 for this block's region chunk and its pairwise
-// partial sum; the last chunk to finish reduces the partial sums into the
-// sum of Eq. 5 (same pairwise tree whichever block it is), before the grid
-// barrier that ends the phase.  Every operation is an explicitly rounded
-// IEEE double operation in the order
+// partial sum (published before the grid barrier that ends the phase).
+// Every operation is an explicitly rounded IEEE double operation in the
+// order
 // FreeVol = ((delta + nv) vol) / ((delta + nv) + ni),
 // f4 = (FreeVol FreeVol)(FreeVol FreeVol),
 // Score = f4 / ((1 + Cov)(1 + (nv + ni)(nv + ni))).
@@ -685,31 +684,22 @@ __device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, in
     sd[i] = sc;
   }
   warp_pairwise(sd, ch);
-  int last = 0;
-  if (lane == 0) {
-    P.chunk_sum[T.b] = sd[0];
-    __threadfence();
-    last = atomicAdd(&P.ctl->s_done, 1u) == (uint32_t)(nch - 1);
-  }
-  last = __shfl_sync(0xffffffffu, last, 0);
-  if (last) {
-    __threadfence();
-    for (int i = lane; i < nch; i += 32) sd[i] = __ldcg(P.chunk_sum + i);
-    warp_pairwise(sd, nch);
-    if (lane == 0) {
-      P.ctl->score_sum = sd[0];
-      P.ctl->s_done = 0;  // for the next pass
-    }
-  }
+  if (lane == 0) P.chunk_sum[T.b] = sd[0];
   __syncwarp();
 }
 
-// Phase T (warp 0 of the node-set phase): P_accept and the integer
-// threshold of this block's region chunk (Eq. 5), from the sum the last
-// chunk published in the accept phase.
-__device__ __forceinline__ void phase_thresholds(const KParams& P, const Team& T, int nch) {
+// Phase T (warp 0 of the node-set phase): the sum of Eq. 5 from the chunks'
+// partial sums (every chunk's warp reduces them itself, in the same
+// pairwise tree, so all get the same value), then P_accept and the integer
+// threshold of this block's region chunk.
+__device__ __forceinline__ void phase_thresholds(const KParams& P, const Team& T, int nch,
+                                                 double* sd) {
   if (T.b >= nch) return;
-  const double sum = __ldcg(&P.ctl->score_sum);
+  const int lane = (int)(threadIdx.x & 31u);
+  for (int i = lane; i < nch; i += 32) sd[i] = __ldcg(P.chunk_sum + i);
+  warp_pairwise(sd, nch);
+  const double sum = sd[0];
+  if (T.b == 0 && lane == 0) P.ctl->score_sum = sum;
   const int ch = P.R_pad / nch;
   const int r0 = T.b * ch;
   for (int i = (int)(threadIdx.x & 31u); i < ch; i += 32) {
@@ -828,10 +818,10 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int i
 template <int SYS, bool LOG>
 __device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, uint32_t it,
                                               int t_old, int lam, LoopShared& sh, int* n_new,
-                                              const unsigned char* sblob) {
+                                              const unsigned char* sblob, double* sd) {
   const int nch = P.nch;
   if (threadIdx.x < 32 && T.b < nch) {
-    phase_thresholds(P, T, nch);
+    phase_thresholds(P, T, nch, sd);
     __threadfence();
     __syncwarp();
     if (threadIdx.x == 0) atomicAdd(&P.ctl->t_done, 1u);
@@ -890,7 +880,6 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     ctl->stop = 0;
     ctl->n_run = 0;
     ctl->work_next = 0;
-    ctl->s_done = 0;
     ctl->t_done = 0;
   }
   // the loop state, read once per block
@@ -952,7 +941,7 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     if (timer) phase_ns[5] = phase_ns[7] = 0;
     const int t_old = n_tree;
     int n_acc;
-    ve_off = phase_nodesets<SYS, LOG>(P, T, it, t_old, lam, sh, &n_acc, smem);
+    ve_off = phase_nodesets<SYS, LOG>(P, T, it, t_old, lam, sh, &n_acc, smem, sd);
     n_tree = t_old + n_acc;
     stamp(8);
     if (!team_sync(T, ctl, P.wait_ns, 23)) return false;
@@ -1050,7 +1039,6 @@ __device__ void init_root(const KParams& P, const RootState& root) {
   ctl->tot_hull = 0;
   ctl->tot_box_tests = 0;
   ctl->work_next = 0;
-  ctl->s_done = 0;
   if (!ok) {
     ctl->state = KP_DEV_BAD_ROOT;
     ctl->n_nodes = 0;
