@@ -94,13 +94,15 @@ def test_training_lowers_the_loss(M):
     assert last < first - 1.0, (first, hist, last)
 
 
-def test_harvest_matches_oracle(M):
+@pytest.mark.parametrize("fso", [False, True])
+def test_harvest_matches_oracle(M, fso):
     """Lock-step plain passes with the harvest on: the device collects the
     same pairs as the oracle (features within BF16 rounding, targets within
-    float32 rounding), compared as sorted sets."""
+    float32 rounding), compared as sorted sets; with kd-tree regions the
+    grid-neighbour features are zero on both sides."""
     import torch
     _, P = M
-    w = W.c1(2)
+    w = W.c1(2).with_(fso=fso)
     g = P.Planner(w)
     o = Oracle(w)
     g.reset()
@@ -119,6 +121,8 @@ def test_harvest_matches_oracle(M):
     ko = np.lexsort(np.round(ot, 4).T[::-1])
     np.testing.assert_allclose(gt[kg], ot[ko], atol=1e-5)
     np.testing.assert_allclose(gf[kg], of[ko], atol=2e-2, rtol=1e-2)
+    if fso:
+        assert np.all(gf[:, 14:20] == 0.0) and np.any(gf[:, 13] > 0.0)
 
 
 def test_learned_pass_matches_oracle(M):
