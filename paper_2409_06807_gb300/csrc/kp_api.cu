@@ -587,7 +587,8 @@ kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
   if (nb < 0 || nb > ctx->n_boxes_cap) return fail(ctx, KP_ERR_ARG, "box count above capacity");
   if (nb > 0 && !obs->boxes) return fail(ctx, KP_ERR_ARG, "null boxes");
   if (const char* m = check_boxes(nb > 0 ? obs->boxes : nullptr, nb)) return fail(ctx, KP_ERR_ARG, "%s", m);
-  // build the blob (and the kd-tree) in pinned host memory, then async copies
+  // build the blob (and the kd-tree) in pinned host memory first; nothing
+  // of the context changes unless both succeed
   const Layout& L = ctx->lay;
   const size_t kd_bytes = ctx->dims.fso ? L.total - L.kd_node : 0;
   kp_status ps = ensure_pinned(ctx, (size_t)KP_BLOB_BYTES + (ctx->dims.fso ? kKdNodes * 8 : 0) +
@@ -595,31 +596,34 @@ kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
   if (ps != KP_OK) return ps;
   KP_CUDA(cudaStreamSynchronize(ctx->stream));  // the staging buffer is free
   unsigned char* host = static_cast<unsigned char*>(ctx->pinned);
-  const size_t bytes = build_blob(host, nb > 0 ? obs->boxes : nullptr, nb, ctx->ws, ctx->P);
-  KP_CUDA(cudaMemcpyAsync(ctx->arena + L.boxes, host, bytes, cudaMemcpyHostToDevice,
-                          ctx->stream));
-  ctx->blob_base = (int)bytes;
-  ctx->blob_kd = 0;
+  KParams Pn = ctx->P;
+  const size_t bytes = build_blob(host, nb > 0 ? obs->boxes : nullptr, nb, ctx->ws, Pn);
+  unsigned char* kd = host + (size_t)KP_BLOB_BYTES + kKdNodes * 8;
+  int leaves = 0, n_nodes = 0, blob_kd = 0;
   if (ctx->dims.fso) {
-    unsigned char* kd = host + (size_t)KP_BLOB_BYTES + kKdNodes * 8;
-    int n_nodes = 0;
-    const int leaves = build_kd(kd, reinterpret_cast<const float*>(host), nb, ctx->ws, L, &n_nodes);
-    if (leaves == 0) {
-      KP_CUDA(cudaStreamSynchronize(ctx->stream));
+    leaves = build_kd(kd, reinterpret_cast<const float*>(host), nb, ctx->ws, L, &n_nodes);
+    if (leaves == 0)
       return fail(ctx, KP_ERR_ARG, "kd-tree decomposition above %d leaves or depth %d",
                   KP_FSO_MAX_LEAVES, KP_FSO_MAX_DEPTH);
-    }
-    KP_CUDA(cudaMemcpyAsync(ctx->arena + L.kd_node, kd, kd_bytes, cudaMemcpyHostToDevice,
-                            ctx->stream));
     // the compact copy (codes, then splits) right after the blob
     const size_t at = round16(bytes);
     std::memset(host + bytes, 0, at - bytes);
     std::memcpy(host + at, kd, (size_t)n_nodes * 4);
     std::memcpy(host + at + (size_t)n_nodes * 4, kd + (L.kd_split - L.kd_node), (size_t)n_nodes * 4);
-    ctx->blob_kd = (int)round16(at + (size_t)n_nodes * 8);
+    blob_kd = (int)round16(at + (size_t)n_nodes * 8);
+  }
+  // commit
+  KP_CUDA(cudaMemcpyAsync(ctx->arena + L.boxes, host, blob_kd > 0 ? (size_t)blob_kd : bytes,
+                          cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->dims.fso)
+    KP_CUDA(cudaMemcpyAsync(ctx->arena + L.kd_node, kd, kd_bytes, cudaMemcpyHostToDevice,
+                            ctx->stream));
+  KP_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->P = Pn;
+  ctx->blob_base = (int)bytes;
+  ctx->blob_kd = blob_kd;
+  if (ctx->dims.fso) {
     ctx->P.kd_n = n_nodes;
-    KP_CUDA(cudaMemcpyAsync(ctx->arena + L.boxes + bytes, host + bytes, ctx->blob_kd - bytes,
-                            cudaMemcpyHostToDevice, ctx->stream));
     Dims& d = ctx->dims;
     d.R = leaves;
     d.R_pad = 1;
@@ -628,7 +632,6 @@ kp_status upload_boxes(kp_ctx* ctx, const kp_obstacles* obs) {
     ctx->P.R = d.R;
     ctx->P.R_pad = d.R_pad;
   }
-  KP_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->dims.boxes_pad = ctx->P.n_boxes_pad;
   ctx->have_tree = false;
   return configure_launch(ctx);

@@ -540,3 +540,27 @@ def test_whole_queries_match_oracle_statistically(P):
     assert abs(np.mean(o_n) / np.mean(d_n) - 1.0) <= 0.1
     same = np.mean(np.array(o_it) == np.array(d_it))
     assert same >= 0.5, same
+
+
+def test_fso_leaf_capacity_refused_and_context_unchanged(P):
+    """An obstacle set whose kd-tree passes 16,384 leaves is refused with
+    KP_ERR_ARG, at creation and on replacement; a refused replacement
+    leaves the context as it was (same regions, plans as before)."""
+    rng_boxes = lambda n: W.random_boxes(5, n, side=(0.01, 0.03),
+                                         keep_clear=[((0.1, 0.1, 0.1), 0.02),
+                                                     ((0.9, 0.9, 0.9), 0.06)])
+    w = W.c1(0).with_(fso=True)
+    with pytest.raises(P.KpError) as e:
+        P.Planner(w.with_(boxes=rng_boxes(2000)))
+    assert e.value.status == P.ERR_ARG
+    g = P.Planner(w, box_capacity=2000)
+    regions = g.n_regions
+    assert regions == Oracle(w).R
+    with pytest.raises(P.KpError) as e:
+        g.set_obstacles(rng_boxes(2000))
+    assert e.value.status == P.ERR_ARG
+    assert g.info()["n_regions"] == regions
+    st, traj = g.plan(max_iters=200)
+    assert st == P.OK
+    _revalidate(w, traj, w.x_init)
+    _tree_invariants(w, g.export_tree(), sample_edges=100)

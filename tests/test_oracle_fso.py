@@ -178,3 +178,21 @@ def test_learned_features_have_no_grid_neighbours():
         f = o.features(v)
         assert np.all(f[14:20] == 0.0)
         assert f[13] > 0.0
+
+
+def _many_small_boxes(n):
+    return W.random_boxes(5, n, side=(0.01, 0.03),
+                          keep_clear=[((0.1, 0.1, 0.1), 0.02), ((0.9, 0.9, 0.9), 0.06)])
+
+
+def test_leaf_capacity():
+    """1,000 small random boxes give a tree within the 16,384-leaf capacity
+    (it still tiles W); 2,000 exceed it and the oracle refuses the set."""
+    import pytest
+    w = W.c1(0).with_(boxes=_many_small_boxes(1000), fso=True)
+    o = Oracle(w)
+    lo, hi = o.fso_leaves()
+    assert 1000 < o.R <= 16384
+    assert math.isclose(math.fsum(np.prod(hi - lo, axis=1)), 1.0, rel_tol=1e-12)
+    with pytest.raises(ValueError):
+        Oracle(w.with_(boxes=_many_small_boxes(2000)))
