@@ -203,8 +203,8 @@ __device__ __forceinline__ void sincos_reduced(float x, float* s, float* c) {
 // Every product and sum is written with an explicitly rounded operation
 // (__fmul_rn, __fadd_rn, __fmaf_rn), which the compiler neither fuses nor
 // splits: the integrators give the same bits wherever they are inlined, so
-// a sample re-derived from its key when it is appended equals the sample
-// the expand phase checked and binned.
+// a sample re-derived from its key (the sample log's replay check of every
+// appended sample) equals the sample the expand phase checked and binned.
 // ---------------------------------------------------------------------------
 
 template <int SYS>

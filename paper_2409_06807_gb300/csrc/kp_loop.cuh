@@ -2,24 +2,26 @@
 // the small reset / import / trajectory kernels.  Instantiated once per
 // system by kp_sys_*.cu.
 //
-// One pass of the loop body (Algorithm 1) runs as five grid phases separated
+// One pass of the loop body (Algorithm 1) runs as four grid phases separated
 // by bounded grid barriers, with no host involvement:
 //   E  Propagate (Algorithm 2): lanes carry one sample (V_E position, j)
 //      each and are refilled from a grid-wide key counter; draw u and k,
 //      integrate k steps in FP32 registers, check each step against the
 //      state box and the obstacle boxes staged in shared memory, bin the
 //      end (or first invalid) state, count n_valid / n_invalid, claim newly
-//      reached sub-regions (smallest sample key wins).
+//      reached sub-regions (smallest sample key wins), keep the end state
+//      of a sample that may still be accepted.
 //   A  accept decisions (representative or P_accept draw), accepted keys
 //      compacted per warp in key order; alongside, on warp 0:
 //   S  Score per region (Eq. 3-4, FP64, rounded exactly as written) and
-//      pairwise partial sums per aligned region chunk (Eq. 5's sum).
-//   P  accepted keys copied to their place in key order; alongside:
-//   T  P_accept and the integer accept threshold per region (Eq. 5).
-//   N  one selection draw per old node against its region's new threshold
-//      (Algorithm 4, V_E <-> V_O), per-block V_E counts, and the new nodes
-//      (Algorithm 4, to T and V_E) re-derived from their keys with the goal
-//      test.
+//      the pairwise partial sum of each aligned region chunk (Eq. 5's sum).
+//   N  first, on warp 0 of each region-chunk block, T: the sum of Eq. 5
+//      from the partial sums and P_accept with its integer accept threshold
+//      per region; each block appends its own accepted samples (Algorithm
+//      4, to T and V_E) at their key-order node ids, from the kept end
+//      states, with the goal test; then one selection draw per old node
+//      against its region's new threshold (Algorithm 4, V_E <-> V_O) and
+//      per-block V_E counts.
 //   L  V_E list in ascending node id, lambda for the next pass (Eq. 6),
 //      stop decision.
 // With a network attached (learned proposal) a phase F before E evaluates
