@@ -397,8 +397,18 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
   bool done = false;
   float x[D], u[N];
   uint32_t wacc = 0, wr[4] = {0, 0, 0, 0};
-  // warp state (uniform): the current batch of keys
-  int pool_next = 0, pool_end = 0;
+  // warp state (uniform): the current batch of keys.  The first batch of
+  // every warp is fixed by the warp's index (keys [gw b0, (gw + 1) b0), the
+  // size the live sizing below gives at the start of a pass), so no warp
+  // queues on the counter to start; later batches come from the counter,
+  // offset past the statically handed-out keys.
+  const int n_warps = T.nb * (int)(blockDim.x >> 5);
+  const int gw = T.b * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+  int b0 = S / (2 * n_warps);
+  b0 = b0 < 32 ? 32 : (b0 > KP_KEY_BATCH ? KP_KEY_BATCH : b0);
+  const int static_end = n_warps * b0 < S ? n_warps * b0 : S;
+  int pool_next = gw * b0 < S ? gw * b0 : S;
+  int pool_end = pool_next + b0 < S ? pool_next + b0 : S;
   bool exhausted = S <= 0;
   // bound on the phase's device time, checked warp-uniformly
   const uint64_t t_phase = global_ns();
@@ -483,13 +493,12 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
           // that last took keys long ago must not size it from a stale
           // position and leave with a large batch just before the end)
           const int n_idle_now = __popc(m_idle);
-          int base = 0;
-          if (lane == 0) {
-            // (a warp's first batch of the pass is sized from the start)
-            const int cur = pool_end == 0 ? 0 : *((volatile int*)&P.ctl->work_next);
-            int want = (S - cur) / (2 * T.nb * (int)(blockDim.x >> 5));
+          int base = S;
+          if (lane == 0 && static_end < S) {
+            const int cur = static_end + *((volatile int*)&P.ctl->work_next);
+            int want = (S - cur) / (2 * n_warps);
             want = want < n_idle_now ? n_idle_now : (want > KP_KEY_BATCH ? KP_KEY_BATCH : want);
-            base = atomicAdd(&P.ctl->work_next, want);
+            base = static_end + atomicAdd(&P.ctl->work_next, want);
             base = base < S ? base : S;
             pool_end = base + want < S ? base + want : S;
           }
