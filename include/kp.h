@@ -160,11 +160,11 @@ typedef struct {
   int32_t phase_ns[12]; /* device time of the pass's phases (ns) as seen by
                            one block, each phase's work then its barrier
                            wait: [0] Propagate, [1] wait, [2] accept flags
-                           with Score (Eq. 3-4) and then P_accept (Eq. 5)
-                           alongside, [3] node features and the network
-                           (learned form or harvest, else 0), [4] wait,
-                           [5] 0, [6] wait after [3], [7] 0, [8] node-set
-                           draws and the new nodes appended to T, [9]
+                           with Score (Eq. 3-4) alongside, [3] node
+                           features and the network (learned form or
+                           harvest, else 0), [4] wait, [5] 0, [6] wait
+                           after [3], [7] 0, [8] P_accept (Eq. 5), the new
+                           nodes appended to T and the node-set draws, [9]
                            wait, [10] V_E list and Eq. 6, [11] the previous
                            pass's final wait */
 } kp_iter_stats;

@@ -87,9 +87,9 @@ struct KLog {
 struct KStats {
   int32_t iteration, n_ve, lambda, n_samples, n_valid, n_accepted, n_nodes, goal_node;
   // device time of the pass as seen by block 0 (ns): work then barrier wait
-  // of each phase: [0,1] Propagate, [2] accept + Score + P_accept, [3]
-  // features and network, [4] wait, [5] 0, [6] wait after [3], [7] 0,
-  // [8] node sets and new nodes, [9] wait, [10] V_E list and Eq. 6, [11]
+  // of each phase: [0,1] Propagate, [2] accept + Score, [3] features and
+  // network, [4] wait, [5] 0, [6] wait after [3], [7] 0, [8] P_accept,
+  // new nodes and node sets, [9] wait, [10] V_E list and Eq. 6, [11]
   // previous pass's final wait
   int32_t phase_ns[12];
 };
