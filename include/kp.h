@@ -475,6 +475,18 @@ kp_status kp_server_stats_get(kp_server *srv, kp_server_stats *out);
 /* Asks the teams to leave after their current query and waits for them. */
 void kp_server_destroy(kp_server *srv);
 
+/* Lane-issue peak of the current device, measured: a project kernel in
+ * which every thread runs eight independent FP32 fused multiply-add chains
+ * (one lane operation each, enough independent work per warp that issue,
+ * not latency, bounds the SM) on a full-occupancy grid, timed with CUDA
+ * events on 'cuda_stream' (NULL = the legacy default stream), best of five
+ * launches after a warm-up.  Writes lane operations per second to
+ * *lane_ops_per_s.  This is the measured counterpart of the ALU roofline's
+ * denominator (SMs x 128 FP32 lanes x clock).  Allocates no device memory;
+ * synchronises the stream.  KP_ERR_ARG for a NULL output, KP_ERR_CUDA when
+ * a CUDA call fails. */
+kp_status kp_measure_lane_peak(void *cuda_stream, double *lane_ops_per_s);
+
 /* Last error message of the context (never NULL). */
 const char *kp_last_error(const kp_ctx *ctx);
 

@@ -1451,6 +1451,72 @@ __global__ void kp_static_blob_kernel(unsigned char* blob, const float* raw, int
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// measured lane-issue peak (denominator of the ALU roofline)
+// ---------------------------------------------------------------------------
+
+namespace {
+
+static __device__ float g_kp_peak_sink[KP_MAX_GRID];
+
+// Eight independent FMA chains per thread; 'iters' rounds of eight FMAs.
+__global__ void __launch_bounds__(256) kp_lane_peak_kernel(int iters) {
+  float a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = 1.0f + 1.0e-3f * (float)(threadIdx.x + 7 * j);
+  const float m = 0.99990f, c = 1.0e-4f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = __fmaf_rn(a[j], m, c);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j];
+  if (s == 1234.5f) g_kp_peak_sink[blockIdx.x % KP_MAX_GRID] = s;  // keeps the chains
+}
+
+}  // namespace
+
+extern "C" kp_status kp_measure_lane_peak(void* cuda_stream, double* lane_ops_per_s) {
+  if (!lane_ops_per_s) return KP_ERR_ARG;
+  *lane_ops_per_s = 0.0;
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, n_sm = 0, bps = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kp_lane_peak_kernel, 256, 0) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return KP_ERR_CUDA;
+  }
+  const int grid = n_sm * (bps > 0 ? bps : 1);
+  const int iters = 8192;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 0.0f;
+  for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+    e = cudaEventRecord(e0, stream);
+    if (e == cudaSuccess) {
+      kp_lane_peak_kernel<<<grid, 256, 0, stream>>>(iters);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0 && (best == 0.0f || ms < best)) best = ms;  // rep 0 warms up
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess || best <= 0.0f) {
+    cudaGetLastError();
+    return KP_ERR_CUDA;
+  }
+  *lane_ops_per_s = (double)grid * 256.0 * (double)iters * 8.0 / ((double)best * 1e-3);
+  return KP_OK;
+}
+
 extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws,
                                     const kp_obstacles* obs, const kp_params* prm,
                                     const float* x_init, const kp_goal* goal,

@@ -124,6 +124,7 @@ SIGNATURES = {
     "kp_plan_static": (C.c_int, [C.POINTER(System), C.POINTER(Workspace), C.POINTER(Obstacles),
                                  C.POINTER(Params), C.POINTER(C.c_float), C.POINTER(Goal),
                                  C.POINTER(Budget), C.POINTER(Traj), _vp]),
+    "kp_measure_lane_peak": (C.c_int, [_vp, C.POINTER(C.c_double)]),
     "kp_mlp_num_params": (C.c_int32, []),
     "kp_mlp_required_bytes": (C.c_size_t, [C.c_int32]),
     "kp_mlp_create": (C.c_int, [_vp, C.c_size_t, C.c_int32, C.POINTER(C.c_float), _vp,
@@ -204,6 +205,17 @@ def structs(w):
     p.delta, p.eps = float(w.delta), float(w.eps)
     p.seed = int(w.seed) & 0xFFFFFFFFFFFFFFFF
     return s, ws, p
+
+
+def measure_lane_peak(stream=None):
+    """Measured lane-issue peak of the current device (lane operations per
+    second) from the library's FMA microbenchmark (kp_measure_lane_peak)."""
+    out = C.c_double()
+    st = lib().kp_measure_lane_peak(C.c_void_p(stream.cuda_stream if stream is not None else 0),
+                                    C.byref(out))
+    if st != OK:
+        raise KpError(st, "kp_measure_lane_peak failed")
+    return out.value
 
 
 def goal_struct(w):

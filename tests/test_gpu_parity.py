@@ -564,3 +564,15 @@ def test_fso_leaf_capacity_refused_and_context_unchanged(P):
     assert st == P.OK
     _revalidate(w, traj, w.x_init)
     _tree_invariants(w, g.export_tree(), sample_edges=100)
+
+
+def test_measured_lane_peak_near_the_derived_one(P):
+    """The FMA microbenchmark (the measured ALU denominator) lands near SMs x
+    128 lanes x the maximum SM clock (2,070 MHz on this part): above 40 %
+    of it (clocks may sit below the maximum) and not above it by more than
+    the timing noise."""
+    import torch
+    v = P.measure_lane_peak()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    derived = n_sm * 128 * 2070e6
+    assert 0.4 * derived <= v <= 1.05 * derived, (v, derived)
