@@ -244,7 +244,7 @@ kp_status kp_create(const kp_system *sys, const kp_workspace *ws,
  * to empty. */
 kp_status kp_set_obstacles(kp_ctx *ctx, const kp_obstacles *obs);
 
-/* Algorithm 1, lines 1-3: tree = {x_init}, V_E = {x_init}, counters zero,
+/* Algorithm 1, initialisation: tree = {x_init}, V_E = {x_init}, counters zero,
  * P_accept = 1 everywhere; the Philox key becomes 'seed'.  x_init is a
  * host array of the state dimension.  KP_ERR_ARG if x_init is not valid
  * (Problem 1 requires x_init in X_valid).  If x_init already lies in the

@@ -100,7 +100,7 @@ int32_t kpo_control_dim(const kpo *o);
 int32_t kpo_num_regions(const kpo *o);
 int32_t kpo_num_subregions(const kpo *o);
 
-/* Algorithm 1, lines 1-3.  Returns KPO_ERR when x_init is not valid. */
+/* Algorithm 1, initialisation.  Returns KPO_ERR when x_init is not valid. */
 int32_t kpo_reset(kpo *o, const float *x_init);
 /* One pass of the Algorithm 1 loop body.  Returns the planner status. */
 int32_t kpo_iterate(kpo *o, kpo_records *rec, kpo_iter_stats *st);

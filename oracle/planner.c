@@ -163,7 +163,7 @@ void kpo_eq345_vol(int32_t n, const uint32_t *n_valid, const uint32_t *n_invalid
   for (int i = 0; i < n; ++i) {
     double p;
     if (!avail[i]) {
-      p = 1.0; /* Algorithm 1, line 3: regions without a node keep 1 */
+      p = 1.0; /* Algorithm 1 starts every region at 1; regions without a node keep it */
     } else if (sum > 0.0) {
       /* Eq. 5: P_accept = min{1, Score / sum over R_avail + eps} */
       p = score[i] / sum + eps;
@@ -310,7 +310,7 @@ int32_t kpo_set_harvest(kpo *o, double *feat, double *target, int32_t capacity) 
 int32_t kpo_harvest_count(const kpo *o) { return o->hv_count; }
 
 /* ------------------------------------------------------------------ */
-/* Algorithm 1, lines 1-3                                               */
+/* Algorithm 1, initialisation                                         */
 /* ------------------------------------------------------------------ */
 
 int32_t kpo_reset(kpo *o, const float *x_init) {
@@ -505,7 +505,7 @@ int32_t kpo_iterate(kpo *o, kpo_records *rec, kpo_iter_stats *st) {
     if ((f & 1) && ((f & 8) || (f & 4))) fl[key] |= 16;
   }
 
-  /* ----- Algorithm 4, lines 4-6: V_U -> T and V_E; goal test ----- */
+  /* ----- Algorithm 4, new nodes: V_U -> T and V_E; goal test ----- */
   /* (appended before UpdateEstimates, reading R7) */
   for (int key = 0; key < S; ++key) {
     if (!(fl[key] & 16)) continue;
@@ -542,7 +542,7 @@ int32_t kpo_iterate(kpo *o, kpo_records *rec, kpo_iter_stats *st) {
   refresh_region_sets(o);
   update_estimates(o);
 
-  /* ----- Algorithm 4, lines 1-3 and 7-9: one draw per old node ----- */
+  /* ----- Algorithm 4, old nodes: one draw per old node ----- */
   for (int v = 0; v < n_old; ++v) {
     uint32_t w[4];
     draw(o, it, (uint32_t)v, 0, 2, w);

@@ -1027,7 +1027,7 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParam
 
 // Root of a query (thread 0): x_init checked (state box, no obstacle box
 // contains it) and binned; tree, decomposition and control block set to
-// Algorithm 1, lines 1-3.  Thresholds and cleared tables are the caller's.
+// Algorithm 1, initialisation.  Thresholds and cleared tables are the caller's.
 template <int SYS>
 __device__ void init_root(const KParams& P, const RootState& root) {
   using Sys = System<SYS>;
@@ -1077,7 +1077,7 @@ __device__ void init_root(const KParams& P, const RootState& root) {
   ctl->state = in_goal ? KP_DEV_SOLVED : KP_DEV_RUNNING;
 }
 
-// Algorithm 1, lines 1-3 on the device (after the host cleared the tables):
+// Algorithm 1, initialisation, on the device (after the host cleared the tables):
 // every thread sets P_accept = 1 (threshold 2^32) for its regions, block 0
 // thread 0 writes the root.
 template <int SYS>
