@@ -137,3 +137,113 @@ def test_quadrotor_rk4_order(kpo):
         errs.append(np.linalg.norm(x - ref))
     for a, b in zip(errs, errs[1:]):
         assert 12.0 < a / b < 20.0
+
+
+def _rx(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[1, 0, 0], [0, c, -s], [0, s, c]])
+
+
+def _ry(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, 0, s], [0, 1, 0], [-s, 0, c]])
+
+
+def _rz(a):
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, -s, 0], [s, c, 0], [0, 0, 1]])
+
+
+def _attitude(phi, theta, psi):
+    """Body-to-world rotation of ZYX Euler angles: yaw, then pitch, then roll."""
+    return _rz(psi) @ _ry(theta) @ _rx(phi)
+
+
+def _hat(w):
+    return np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+
+
+def _rotation_exp(w, t):
+    """exp(t [w]x) by Rodrigues' formula."""
+    n = np.linalg.norm(w)
+    K = _hat(np.asarray(w) / n)
+    a = n * t
+    return np.eye(3) + math.sin(a) * K + (1 - math.cos(a)) * K @ K
+
+
+def test_quadrotor_tilted_thrust_follows_the_rotation_matrix(kpo):
+    """Equal rotor thrusts and no body rates: no torque, so the attitude holds
+    and the acceleration is the constant R(phi, theta, psi) e3 F / m - g e3,
+    with R built from elementary rotations; positions are then exact
+    parabolas under RK4."""
+    w = W.c3(0)
+    rng = np.random.default_rng(3)
+    for _ in range(12):
+        phi, theta, psi = rng.uniform(-0.6, 0.6), rng.uniform(-0.6, 0.6), rng.uniform(-3, 3)
+        F = rng.uniform(0.2, 1.8)
+        x0 = np.zeros(12)
+        x0[:3] = rng.uniform(0.3, 0.7, 3)
+        x0[3:6] = (phi, theta, psi)
+        x0[6:9] = rng.uniform(-0.2, 0.2, 3)
+        a = _attitude(phi, theta, psi) @ np.array([0.0, 0.0, F]) - np.array([0.0, 0.0, 1.0])
+        k = 30
+        t = k * float(np.float32(w.dt))
+        traj = kpo.propagate(w, x0, [F / 4] * 4, k)
+        np.testing.assert_allclose(traj[-1, 6:9], x0[6:9] + a * t, atol=1e-12)
+        np.testing.assert_allclose(traj[-1, :3], x0[:3] + x0[6:9] * t + a * t * t / 2, atol=1e-12)
+        np.testing.assert_allclose(traj[-1, 3:6], x0[3:6], atol=1e-14)
+        np.testing.assert_allclose(traj[-1, 9:], 0.0, atol=1e-14)
+
+
+def test_quadrotor_body_rates_turn_the_attitude(kpo):
+    """Constant body rates (torque free: (p, q, 0), or (0, 0, r), with
+    Ixx = Iyy) turn the attitude as R(t) = R(0) exp(t [omega]x); the Euler
+    angles integrated by the oracle must give that rotation."""
+    w = W.c3(0)
+    assert W.QUAD_PHYS["Ixx"] == W.QUAD_PHYS["Iyy"]
+    rng = np.random.default_rng(4)
+    for omega in ([0.6, -0.4, 0.0], [0.0, 0.0, 0.9], [-0.3, 0.5, 0.0]):
+        for _ in range(3):
+            eta0 = (rng.uniform(-0.4, 0.4), rng.uniform(-0.4, 0.4), rng.uniform(-2, 2))
+            x = np.zeros(12)
+            x[:3] = 0.5
+            x[3:6] = eta0
+            x[9:] = omega
+            n, t = 500, 0.5
+            for _ in range(n):
+                x = kpo.step(w, x, [0.25] * 4, t / n)
+            np.testing.assert_allclose(x[9:], omega, atol=1e-12)
+            want = _attitude(*eta0) @ _rotation_exp(omega, t)
+            np.testing.assert_allclose(_attitude(*x[3:6]), want, atol=1e-10)
+
+
+def test_quadrotor_rotor_torques_and_gyroscopic_coupling(kpo):
+    """Roll torque l (T2 - T4) and pitch torque l (T3 - T1) from rest give
+    p = 2 l d t / Ixx and q = 2 l e t / Iyy; torque free, a symmetric body
+    (Ixx = Iyy = I1, Izz = I3) precesses its (p, q) at
+    Omega = (I3 - I1) r / I1 (Euler's equations)."""
+    w = W.c3(0)
+    # the constants as the workload stores them (float32)
+    P = {k: float(np.float32(v)) for k, v in W.QUAD_PHYS.items()}
+    T0, d = 0.25, 0.03
+    k = 20
+    t = k * float(np.float32(w.dt))
+    x0 = np.zeros(12)
+    x0[:3] = 0.5
+    roll = kpo.propagate(w, x0, [T0, T0 + d, T0, T0 - d], k)[-1]
+    assert abs(roll[9] - 2 * P["l"] * d * t / P["Ixx"]) < 1e-12
+    assert abs(roll[10]) < 1e-14 and abs(roll[11]) < 1e-14
+    pitch = kpo.propagate(w, x0, [T0 - d, T0, T0 + d, T0], k)[-1]
+    assert abs(pitch[10] - 2 * P["l"] * d * t / P["Iyy"]) < 1e-12
+    assert abs(pitch[9]) < 1e-14 and abs(pitch[11]) < 1e-14
+    # torque-free precession
+    p0, q0, r0 = 0.4, -0.3, 0.8
+    x = x0.copy()
+    x[9:] = (p0, q0, r0)
+    n, T = 400, 2.0
+    for _ in range(n):
+        x = kpo.step(w, x, [T0] * 4, T / n)
+    Om = (P["Izz"] - P["Ixx"]) * r0 / P["Ixx"]
+    want = (p0 * math.cos(Om * T) - q0 * math.sin(Om * T),
+            p0 * math.sin(Om * T) + q0 * math.cos(Om * T), r0)
+    np.testing.assert_allclose(x[9:], want, atol=1e-10)
