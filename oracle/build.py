@@ -21,15 +21,21 @@ def _stale() -> bool:
     return any(os.path.getmtime(os.path.join(HERE, s)) > t for s in deps)
 
 
+def compile_oracle(src_dir: str, out: str) -> str:
+    """Compile the oracle sources found in src_dir into the library 'out'."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-Wall", "-Wextra", "-Wno-unused-parameter",
+           "-o", tmp] + [os.path.join(src_dir, s) for s in SOURCES] + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build_oracle(force: bool = False) -> str:
     """Compile the oracle shared library if needed; returns its path."""
     if force or _stale():
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", "-Wall", "-Wextra", "-Wno-unused-parameter",
-               "-o", tmp] + [os.path.join(HERE, s) for s in SOURCES] + ["-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
+        compile_oracle(HERE, LIB)
     return LIB
 
 

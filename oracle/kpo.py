@@ -8,6 +8,7 @@ with the attributes of ``paper_2409_06807_gb300.workloads.Workload``).
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -69,7 +70,9 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build_oracle())
+        # KPO_LIB names another build of these sources (the mutation check
+        # of the tests loads copies with a planted mistake this way)
+        L = C.CDLL(os.environ.get("KPO_LIB") or build_oracle())
         vp = C.c_void_p
         L.kpo_create.restype = vp
         L.kpo_create.argtypes = [C.POINTER(Config), _f32p, C.c_int32]

@@ -59,6 +59,24 @@ def test_state_bounds():
     assert not ok  # NaN is never valid
 
 
+def test_state_box_is_closed_on_both_sides():
+    """The state box is a closed set: a state exactly on a bound (the float32
+    value the planner holds) is valid, the next double outwards is not."""
+    w = W.tiny(W.DI, n_boxes=0)
+    o = Oracle(w)
+    base = _state((0.5, 0.5, 0.5))
+    for i in range(6):
+        for bound, out in ((float(w.x_lo[i]), -1.0), (float(w.x_hi[i]), 1.0)):
+            on = base.copy()
+            on[i] = bound
+            ok, _ = o.step_valid(base, on)
+            assert ok, (i, bound)
+            off = on.copy()
+            off[i] = np.nextafter(bound, bound + out)
+            ok, _ = o.step_valid(base, off)
+            assert not ok, (i, bound)
+
+
 def test_axis_aligned_segments_match_dense_sampling():
     """For a segment along one axis the hull is the segment itself, so the
     check must agree with dense point sampling (brute force)."""
