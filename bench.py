@@ -703,7 +703,7 @@ def run_ours(args, world, rank, local):
         "work": {"samples_per_step": samples / len(rows),
                  "steps_per_sample": sum(r[3]["n_steps"] for r in rows) / max(1, samples),
                  "box_tests_per_hull": box_tests_per_hull,
-                 "broad_phase_cells": rows[-1][3]["bp_cells"]},
+                 "broad_phase_grid": rows[-1][3]["bp_grid"]},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
                      "frac": achieved / peak_ops, "traffic": traffic,
                      "peak_source": f"{n_sm} SMs x 128 lanes x {pk.get('sm_max_mhz')} MHz "

@@ -181,7 +181,8 @@ typedef struct {
   int64_t n_steps;     /* integrator steps run (each one checked)          */
   int64_t n_hull_checks; /* step hulls tested against the obstacle set     */
   int64_t n_box_tests;   /* hull-vs-box tests made (after the broad phase)   */
-  int32_t bp_cells;      /* broad-phase grid cells per axis                  */
+  int32_t bp_cells;      /* broad-phase grid cells in all (1: every box)     */
+  int32_t bp_grid[3];    /* broad-phase grid cells along x, y, z             */
 } kp_info;
 
 /* Host-side copy of the tree and decomposition (tests, checkpoints).

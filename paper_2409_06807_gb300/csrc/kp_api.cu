@@ -389,10 +389,40 @@ int host_bp_cell(float v, float lo, float scale, int g) {
   return t >= 0.0f ? (t < (float)g ? (int)t : g - 1) : 0;
 }
 
+// Cell ranges of every padded box on the grid g (cells per axis), with the
+// grid's scale; returns the (cell, box) entry count.
+long long bp_ranges(const float* fb, int nb, const kp_workspace& ws, const int g[3],
+                    float scale[3], std::vector<int>& lo3, std::vector<int>& hi3) {
+  for (int a = 0; a < 3; ++a) scale[a] = (float)((double)g[a] / ((double)ws.hi[a] - (double)ws.lo[a]));
+  lo3.resize((size_t)nb * 3);
+  hi3.resize((size_t)nb * 3);
+  long long entries = 0;
+  for (int b = 0; b < nb; ++b) {
+    long long cells = 1;
+    for (int a = 0; a < 3; ++a) {
+      lo3[(size_t)b * 3 + a] = host_bp_cell(fb[b * 8 + a], ws.lo[a], scale[a], g[a]);
+      hi3[(size_t)b * 3 + a] = host_bp_cell(fb[b * 8 + 4 + a], ws.lo[a], scale[a], g[a]);
+      cells *= hi3[(size_t)b * 3 + a] - lo3[(size_t)b * 3 + a] + 1;
+    }
+    entries += cells;
+  }
+  return entries;
+}
+
 // Writes the obstacle blob (padded boxes, then the broad-phase grid: cell
 // start offsets and box ids of every cell a box overlaps) into 'blob' and
-// sets the blob fields of P.  The grid is the finest of 16^3, 8^3, 4^3,
-// 2^3, 1 cells whose entry count fits KP_BP_MAX_IDS (1 cell = every box).
+// sets the blob fields of P.
+//
+// The grid has 4096 cells in one of seven shapes: 16 x 16 x 16, 64 x 64 x 1
+// (and its two rotations), 32 x 32 x 4 (and its two rotations).  The shape
+// taken is the one with the smallest sum over cells of the squared box
+// count, among those whose entries fit KP_BP_MAX_IDS and the byte budget:
+// the lanes of a warp test the boxes of their own cells and wait for the
+// longest list, so crowded cells cost more than their share.  Obstacles
+// that span the workspace along an axis (trees of a forest) make that axis
+// useless to the grid and the flat shapes win; boxes of every orientation
+// keep the cube.  If no shape fits, the finest of 8^3, 4^3, 2^3 and 1 cell
+// (every box) that fits is used.
 size_t build_blob(unsigned char* blob, const float* boxes, int nb, const kp_workspace& ws,
                   KParams& P, size_t max_bytes = KP_BLOB_BYTES) {
   const int pad = (nb + 7) / 8 * 8;
@@ -410,55 +440,78 @@ size_t build_blob(unsigned char* blob, const float* boxes, int nb, const kp_work
       o[3] = o[7] = 0.0f;
     }
   }
-  int g = nb > 0 ? KP_BP_MAX_G : 1;
+  auto blob_size = [&](const int g[3], long long entries) {
+    return (size_t)pad * 32 + round16((size_t)(g[0] * g[1] * g[2] + 1) * 2) +
+           round16((size_t)entries * 2);
+  };
+  auto fits = [&](const int g[3], long long entries) {
+    return entries <= KP_BP_MAX_IDS && blob_size(g, entries) <= max_bytes;
+  };
+  static const int kShapes[7][3] = {{16, 16, 16}, {64, 64, 1}, {64, 1, 64}, {1, 64, 64},
+                                    {32, 32, 4},  {32, 4, 32}, {4, 32, 32}};
+  static_assert(KP_BP_MAX_G * KP_BP_MAX_G * KP_BP_MAX_G == 4096, "grid shapes hold 4096 cells");
+  int g[3] = {1, 1, 1};
   float scale[3];
-  for (;; g /= 2) {
-    long long entries = 0;
-    for (int a = 0; a < 3; ++a)
-      scale[a] = (float)((double)g / ((double)ws.hi[a] - (double)ws.lo[a]));
-    for (int b = 0; b < nb; ++b) {
-      long long cells = 1;
-      for (int a = 0; a < 3; ++a)
-        cells *= host_bp_cell(fb[b * 8 + 4 + a], ws.lo[a], scale[a], g) -
-                 host_bp_cell(fb[b * 8 + a], ws.lo[a], scale[a], g) + 1;
-      entries += cells;
+  std::vector<int> lo3, hi3;
+  if (nb > 0) {
+    long long best = -1;
+    std::vector<int> count(4096);
+    for (const auto& s : kShapes) {
+      const long long entries = bp_ranges(fb, nb, ws, s, scale, lo3, hi3);
+      if (!fits(s, entries)) continue;
+      std::fill(count.begin(), count.end(), 0);
+      for (int b = 0; b < nb; ++b)
+        for (int z = lo3[(size_t)b * 3 + 2]; z <= hi3[(size_t)b * 3 + 2]; ++z)
+          for (int y = lo3[(size_t)b * 3 + 1]; y <= hi3[(size_t)b * 3 + 1]; ++y)
+            for (int x = lo3[(size_t)b * 3]; x <= hi3[(size_t)b * 3]; ++x)
+              count[(size_t)x + (size_t)s[0] * ((size_t)y + (size_t)s[1] * z)] += 1;
+      long long sq = 0;
+      for (int c : count) sq += (long long)c * c;
+      if (best < 0 || sq < best) {
+        best = sq;
+        for (int a = 0; a < 3; ++a) g[a] = s[a];
+      }
     }
-    const size_t bytes = (size_t)pad * 32 + round16((size_t)(g * g * g + 1) * 2) +
-                         round16((size_t)entries * 2);
-    if ((entries <= KP_BP_MAX_IDS && bytes <= max_bytes) || g == 1) break;
+    if (best < 0)
+      for (int gi = KP_BP_MAX_G / 2; gi >= 1; gi /= 2) {
+        const int s[3] = {gi, gi, gi};
+        if (fits(s, bp_ranges(fb, nb, ws, s, scale, lo3, hi3)) || gi == 1) {
+          for (int a = 0; a < 3; ++a) g[a] = gi;
+          break;
+        }
+      }
   }
-  const int C = g * g * g;
+  bp_ranges(fb, nb, ws, g, scale, lo3, hi3);
+  const int C = g[0] * g[1] * g[2];
   const size_t start_off = (size_t)pad * 32;
   const size_t ids_off = start_off + round16((size_t)(C + 1) * 2);
   // cell starts fit in 16 bits: at most KP_BP_MAX_IDS (< 65536) ids, or the
   // box count for the single-cell grid
   uint16_t* start16 = reinterpret_cast<uint16_t*>(blob + start_off);
   uint16_t* ids = reinterpret_cast<uint16_t*>(blob + ids_off);
-  std::vector<int> lo3((size_t)nb * 3), hi3((size_t)nb * 3);
+  auto cell = [&](int x, int y, int z) { return x + g[0] * (y + g[1] * z); };
   std::vector<int> start((size_t)C + 1, 0);
-  for (int b = 0; b < nb; ++b) {
-    for (int a = 0; a < 3; ++a) {
-      lo3[b * 3 + a] = host_bp_cell(fb[b * 8 + a], ws.lo[a], scale[a], g);
-      hi3[b * 3 + a] = host_bp_cell(fb[b * 8 + 4 + a], ws.lo[a], scale[a], g);
-    }
-    for (int z = lo3[b * 3 + 2]; z <= hi3[b * 3 + 2]; ++z)
-      for (int y = lo3[b * 3 + 1]; y <= hi3[b * 3 + 1]; ++y)
-        for (int x = lo3[b * 3]; x <= hi3[b * 3]; ++x) start[x + g * (y + g * z) + 1] += 1;
-  }
+  for (int b = 0; b < nb; ++b)
+    for (int z = lo3[(size_t)b * 3 + 2]; z <= hi3[(size_t)b * 3 + 2]; ++z)
+      for (int y = lo3[(size_t)b * 3 + 1]; y <= hi3[(size_t)b * 3 + 1]; ++y)
+        for (int x = lo3[(size_t)b * 3]; x <= hi3[(size_t)b * 3]; ++x) start[cell(x, y, z) + 1] += 1;
   for (int c = 0; c < C; ++c) start[c + 1] += start[c];
   for (int c = 0; c <= C; ++c) start16[c] = (uint16_t)start[c];
   std::vector<int> cursor(start.begin(), start.begin() + C);
   for (int b = 0; b < nb; ++b)
-    for (int z = lo3[b * 3 + 2]; z <= hi3[b * 3 + 2]; ++z)
-      for (int y = lo3[b * 3 + 1]; y <= hi3[b * 3 + 1]; ++y)
-        for (int x = lo3[b * 3]; x <= hi3[b * 3]; ++x) ids[cursor[x + g * (y + g * z)]++] = (uint16_t)b;
+    for (int z = lo3[(size_t)b * 3 + 2]; z <= hi3[(size_t)b * 3 + 2]; ++z)
+      for (int y = lo3[(size_t)b * 3 + 1]; y <= hi3[(size_t)b * 3 + 1]; ++y)
+        for (int x = lo3[(size_t)b * 3]; x <= hi3[(size_t)b * 3]; ++x)
+          ids[cursor[cell(x, y, z)]++] = (uint16_t)b;
   const size_t bytes = ids_off + round16((size_t)start[C] * 2);
   P.n_boxes_pad = pad;
   P.blob_bytes = (int32_t)bytes;
-  P.bp_g = g;
+  for (int a = 0; a < 3; ++a) {
+    P.bp_g[a] = g[a];
+    P.bp_scale[a] = scale[a];
+  }
   P.bp_start_off = (int32_t)start_off;
   P.bp_ids_off = (int32_t)ids_off;
-  for (int a = 0; a < 3; ++a) P.bp_scale[a] = scale[a];
   return bytes;
 }
 
@@ -1057,7 +1110,8 @@ kp_status kp_get_info(kp_ctx* ctx, kp_info* out) {
   out->n_steps = ctx->have_tree ? (int64_t)h.tot_steps : 0;
   out->n_hull_checks = ctx->have_tree ? (int64_t)h.tot_hull : 0;
   out->n_box_tests = ctx->have_tree ? (int64_t)h.tot_box_tests : 0;
-  out->bp_cells = ctx->P.bp_g;
+  out->bp_cells = ctx->P.bp_g[0] * ctx->P.bp_g[1] * ctx->P.bp_g[2];
+  for (int a = 0; a < 3; ++a) out->bp_grid[a] = ctx->P.bp_g[a];
   out->n_boxes = ctx->P.n_boxes_pad;
   out->grid_blocks = ctx->grid[ctx->log_on ? 1 : 0];
   return KP_OK;
@@ -1251,7 +1305,7 @@ kp_status kp_grow(kp_ctx* ctx, void* dev_arena, size_t arena_bytes, int32_t t_e)
   P.blob_bytes = old.blob_bytes;
   P.kd_n = old.kd_n;
   P.kd_smem_off = old.kd_smem_off;
-  P.bp_g = old.bp_g;
+  for (int a = 0; a < 3; ++a) P.bp_g[a] = old.bp_g[a];
   P.bp_start_off = old.bp_start_off;
   P.bp_ids_off = old.bp_ids_off;
   for (int a = 0; a < 3; ++a) P.bp_scale[a] = old.bp_scale[a];
@@ -1564,7 +1618,7 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   fill_params(P, d, lay, sys, ws, prm, A);
   const int pad = (nb + 7) / 8 * 8;
   P.n_boxes_pad = pad;
-  P.bp_g = 1;
+  P.bp_g[0] = P.bp_g[1] = P.bp_g[2] = 1;
   P.bp_start_off = pad * 32;
   P.bp_ids_off = P.bp_start_off + 16;
   P.blob_bytes = P.bp_ids_off + (int32_t)round16((size_t)nb * 2);

@@ -495,16 +495,16 @@ __device__ __forceinline__ bool hull_hits_grid(const KParams& P, const float4* _
                                                const uint16_t* __restrict__ sids, float lx,
                                                float ly, float lz, float hx, float hy, float hz,
                                                uint32_t* tests) {
-  const int g = P.bp_g;
-  const int x0 = bp_cell(lx, P.ws_lo[0], P.bp_scale[0], g), x1 = bp_cell(hx, P.ws_lo[0], P.bp_scale[0], g);
-  const int y0 = bp_cell(ly, P.ws_lo[1], P.bp_scale[1], g), y1 = bp_cell(hy, P.ws_lo[1], P.bp_scale[1], g);
-  const int z0 = bp_cell(lz, P.ws_lo[2], P.bp_scale[2], g), z1 = bp_cell(hz, P.ws_lo[2], P.bp_scale[2], g);
+  const int gx = P.bp_g[0], gy = P.bp_g[1], gz = P.bp_g[2];
+  const int x0 = bp_cell(lx, P.ws_lo[0], P.bp_scale[0], gx), x1 = bp_cell(hx, P.ws_lo[0], P.bp_scale[0], gx);
+  const int y0 = bp_cell(ly, P.ws_lo[1], P.bp_scale[1], gy), y1 = bp_cell(hy, P.ws_lo[1], P.bp_scale[1], gy);
+  const int z0 = bp_cell(lz, P.ws_lo[2], P.bp_scale[2], gz), z1 = bp_cell(hz, P.ws_lo[2], P.bp_scale[2], gz);
   uint32_t n = 0;
   bool hit = false;
   for (int cz = z0; cz <= z1 && !hit; ++cz)
     for (int cy = y0; cy <= y1 && !hit; ++cy)
       for (int cx = x0; cx <= x1 && !hit; ++cx) {
-        const int c = cx + g * (cy + g * cz);
+        const int c = cx + gx * (cy + gy * cz);
         const int e = sstart[c + 1];
         for (int q = sstart[c]; q < e; ++q) {
           const int b = sids[q];

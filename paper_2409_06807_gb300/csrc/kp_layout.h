@@ -148,12 +148,12 @@ struct KParams {
   uint32_t seed_lo, seed_hi;
   // obstacles: a blob staged whole into shared memory:
   //   [n_boxes_pad][8] floats (lo.xyz, pad, hi.xyz, pad), then the
-  //   broad-phase grid: uint16 cell_start[bp_g^3 + 1], uint16 ids[...]
+  //   broad-phase grid: uint16 cell_start[bp_g[0] bp_g[1] bp_g[2] + 1], uint16 ids[...]
   const float* boxes;
   int32_t n_boxes_pad;
   int32_t blob_bytes;
   int32_t sd_bytes;      // score scratch after the blob; the network tile follows
-  int32_t bp_g;          // broad-phase cells per axis (1 = every box in one cell)
+  int32_t bp_g[3];       // broad-phase cells along x, y, z (1 1 1: every box in one cell)
   int32_t bp_start_off;  // byte offsets inside the blob
   int32_t bp_ids_off;
   float bp_scale[3];     // cells per unit length, per axis

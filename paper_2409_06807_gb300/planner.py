@@ -78,7 +78,7 @@ class Info(C.Structure):
                                            "n_regions", "n_subregions", "state_dim",
                                            "control_dim", "n_boxes", "grid_blocks")] + \
         [(n, C.c_int64) for n in ("n_samples", "n_steps", "n_hull_checks", "n_box_tests")] + \
-        [("bp_cells", C.c_int32)]
+        [("bp_cells", C.c_int32), ("bp_grid", C.c_int32 * 3)]
 
 
 class TreeView(C.Structure):
@@ -401,7 +401,8 @@ class Planner:
     def info(self):
         i = Info()
         self._check(lib().kp_get_info(self._ctx, C.byref(i)), "kp_get_info")
-        return {f: getattr(i, f) for f, _ in Info._fields_}
+        return {f: (list(getattr(i, f)) if f == "bp_grid" else getattr(i, f))
+                for f, _ in Info._fields_}
 
     # ------------------------------------------------------------------
     def export_tree(self):

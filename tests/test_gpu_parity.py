@@ -282,9 +282,28 @@ def test_broad_phase_coarsens_for_large_boxes(P):
     w = w.with_(boxes=boxes[keep][:400])
     g = P.Planner(w)
     g.reset()
-    assert g.info()["bp_cells"] < 16
+    assert g.info()["bp_cells"] < 4096
     exact, ran = lockstep(P, w, 6)
     assert exact >= min(ran, 2)
+
+
+def test_broad_phase_grid_shape_follows_the_obstacles(P):
+    """Trunks spanning the workspace along one axis give a broad-phase grid
+    flat along that axis; walls of small tiles keep the cube.  With the
+    forest turned so that its trunks run along x or along y, lock-step
+    passes still match the oracle's test of every box."""
+    assert P.Planner(W.c2(0)).info()["bp_grid"] == [64, 64, 1]
+    assert P.Planner(W.c3(0)).info()["bp_grid"] == [16, 16, 16]
+    trunks = W.c2(0).boxes
+    for order, want in (((2, 0, 1), [1, 64, 64]), ((0, 2, 1), [64, 1, 64])):
+        boxes = np.concatenate([trunks[:, list(order)], trunks[:, [3 + a for a in order]]], 1)
+        w = W.tiny(W.DI, seed=0, t_e=4000, lambda_max=16, n_boxes=0)
+        p0 = w.x_init[:3]
+        keep = ~np.all((boxes[:, :3] <= p0 + 0.06) & (boxes[:, 3:] >= p0 - 0.06), axis=1)
+        w = w.with_(boxes=np.ascontiguousarray(boxes[keep]))
+        assert P.Planner(w).info()["bp_grid"] == want
+        exact, ran = lockstep(P, w, 6)
+        assert exact >= min(ran, 2)
 
 
 def test_boxes_on_cell_faces(P):
