@@ -496,9 +496,20 @@ __device__ __forceinline__ bool hull_hits_grid(const KParams& P, const float4* _
                                                float ly, float lz, float hx, float hy, float hz,
                                                uint32_t* tests) {
   const int gx = P.bp_g[0], gy = P.bp_g[1], gz = P.bp_g[2];
-  const int x0 = bp_cell(lx, P.ws_lo[0], P.bp_scale[0], gx), x1 = bp_cell(hx, P.ws_lo[0], P.bp_scale[0], gx);
-  const int y0 = bp_cell(ly, P.ws_lo[1], P.bp_scale[1], gy), y1 = bp_cell(hy, P.ws_lo[1], P.bp_scale[1], gy);
-  const int z0 = bp_cell(lz, P.ws_lo[2], P.bp_scale[2], gz), z1 = bp_cell(hz, P.ws_lo[2], P.bp_scale[2], gz);
+  // an axis of one cell maps every coordinate to cell 0: skip its lookup
+  int x0 = 0, x1 = 0, y0 = 0, y1 = 0, z0 = 0, z1 = 0;
+  if (gx > 1) {
+    x0 = bp_cell(lx, P.ws_lo[0], P.bp_scale[0], gx);
+    x1 = bp_cell(hx, P.ws_lo[0], P.bp_scale[0], gx);
+  }
+  if (gy > 1) {
+    y0 = bp_cell(ly, P.ws_lo[1], P.bp_scale[1], gy);
+    y1 = bp_cell(hy, P.ws_lo[1], P.bp_scale[1], gy);
+  }
+  if (gz > 1) {
+    z0 = bp_cell(lz, P.ws_lo[2], P.bp_scale[2], gz);
+    z1 = bp_cell(hz, P.ws_lo[2], P.bp_scale[2], gz);
+  }
   uint32_t n = 0;
   bool hit = false;
   for (int cz = z0; cz <= z1 && !hit; ++cz)

@@ -390,8 +390,9 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt = (1u << lane) - 1u;
 
-  unsigned long long n_steps = 0, n_hull = 0;
-  uint32_t n_box = 0;
+  // per-thread counts of one pass: a thread runs at most 2^28 / 256 keys of
+  // at most 255 steps each, so 32 bits hold them
+  uint32_t n_steps = 0, n_hull = 0, n_box = 0;
   // lane state: the sample being integrated
   int key = -1, v = 0, k = 0, i = 0, fail = 0;
   bool done = false;
@@ -550,7 +551,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
     }
   }
   unsigned long long bs, bh, bb, dummy;
-  block_sum2(n_steps, n_hull, sh.red, &bs, &bh);
+  block_sum2((unsigned long long)n_steps, (unsigned long long)n_hull, sh.red, &bs, &bh);
   block_sum2((unsigned long long)n_box, 0, sh.red, &bb, &dummy);
   if (threadIdx.x == 0 && bs) {
     atomicAdd(&P.ctl->tot_steps, bs);
