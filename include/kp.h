@@ -241,8 +241,15 @@ kp_status kp_create(const kp_system *sys, const kp_workspace *ws,
                     void *dev_arena, size_t arena_bytes, void *cuda_stream,
                     kp_ctx **out);
 
-/* Replaces the obstacle set (up to KP_MAX_BOXES boxes).  Resets the tree
- * to empty. */
+/* Replaces the obstacle set (up to KP_MAX_BOXES closed boxes, host rows
+ * lo xyz, hi xyz) and resets the tree to empty.  On the host it builds the
+ * broad-phase grid of the step-hull test (Algorithm 2 validity check):
+ * 4096 cells shaped 16x16x16, 64x64x1 or 32x32x4 (or a rotation), the
+ * shape with the smallest sum of squared per-cell box counts, coarser when
+ * the box lists do not fit; under the kd-tree decomposition (Sec. IV-B)
+ * it also rebuilds the tree.  Errors: KP_ERR_ARG (count above capacity,
+ * NaN or lo > hi in a box, kd-tree above its leaf or depth limit; the
+ * context keeps its previous obstacles), KP_ERR_CUDA. */
 kp_status kp_set_obstacles(kp_ctx *ctx, const kp_obstacles *obs);
 
 /* Algorithm 1, initialisation: tree = {x_init}, V_E = {x_init}, counters zero,
