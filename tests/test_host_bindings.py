@@ -1,6 +1,7 @@
-"""Host-side logic of the Python binding that needs no GPU: the network's
-parameter layout (shared by the C ABI and the oracle, each counting it on
-its own) and the serving summary's statistics."""
+"""Host-side logic that needs no GPU: the network's parameter layout
+(shared by the C ABI and the oracle, each counting it on its own), the
+serving summary's statistics, the C ABI's argument validation and the
+arena's size per tree node."""
 import numpy as np
 import pytest
 
@@ -40,3 +41,91 @@ def test_serving_summary():
     assert s["p99_ms"] == pytest.approx(np.percentile(lat, 99))
     assert s["queries_per_s"] == pytest.approx(200.0) and s["samples_per_s"] == pytest.approx(2e5)
     assert s["status"] == {"OK": 75, "NO_SOLUTION": 25}
+
+
+def _required(w, n_boxes=None, edit=None):
+    import ctypes as C
+    from paper_2409_06807_gb300 import planner
+    s, ws, p = planner.structs(w)
+    if edit:
+        edit(s, ws, p)
+    return planner.lib().kp_required_bytes(C.byref(s), C.byref(ws),
+                                           len(w.boxes) if n_boxes is None else n_boxes,
+                                           C.byref(p))
+
+
+def _set(obj, field, value, index=None):
+    if index is None:
+        setattr(obj, field, value)
+    else:
+        getattr(obj, field)[index] = value
+
+
+NAN = float("nan")
+INVALID = {
+    "dt zero": ("s", "dt", 0.0, None), "dt NaN": ("s", "dt", NAN, None),
+    "k_min zero": ("s", "k_min", 0, None), "k_max below k_min": ("s", "k_max", 0, None),
+    "k_max above 255": ("s", "k_max", 256, None),
+    "state bound NaN": ("s", "x_lo", NAN, 4), "state bounds crossed": ("s", "x_lo", 1.0, 4),
+    "control bounds crossed": ("s", "u_lo", 2.0, 0), "control bound infinite": ("s", "u_hi", float("inf"), 1),
+    "workspace empty": ("ws", "hi", 0.0, 0), "grid zero": ("ws", "grid", 0, 1),
+    "grid above 4096": ("ws", "grid", 4097, 2), "sub zero": ("ws", "sub", 0, 0),
+    "speed bins zero": ("ws", "speed_bins", 0, None), "fso two": ("ws", "fso", 2, None),
+    "state grid negative": ("ws", "state_grid", -1, 4),
+    "t_e one": ("p", "t_e", 1, None), "t_e above 2^28": ("p", "t_e", (1 << 28) + 1, None),
+    "lambda zero": ("p", "lambda_max", 0, None), "lambda above 1024": ("p", "lambda_max", 1025, None),
+    "delta zero": ("p", "delta", 0.0, None), "eps zero": ("p", "eps", 0.0, None),
+    "eps one": ("p", "eps", 1.0, None),
+}
+
+
+@pytest.mark.parametrize("case", sorted(INVALID))
+def test_inputs_are_validated_on_the_host(case):
+    """Every documented argument error makes kp_required_bytes return 0 (the
+    same check kp_create applies before touching the device)."""
+    from paper_2409_06807_gb300 import workloads as W
+    which, field, value, index = INVALID[case]
+    w = W.c2(0)
+    assert _required(w) > 0
+
+    def edit(s, ws, p):
+        _set({"s": s, "ws": ws, "p": p}[which], field, value, index)
+    assert _required(w, edit=edit) == 0
+
+
+def test_box_count_and_decomposition_limits():
+    from paper_2409_06807_gb300 import planner
+    from paper_2409_06807_gb300 import workloads as W
+    w = W.c2(0)
+    assert _required(w, n_boxes=-1) == 0
+    assert _required(w, n_boxes=planner.MAX_BOXES) > 0 and _required(w, n_boxes=planner.MAX_BOXES + 1) == 0
+
+    def speed_without_range(s, ws, p):
+        ws.speed_bins, ws.speed_hi = 4, 0.0
+    assert _required(w, edit=speed_without_range) == 0
+
+    def huge(s, ws, p):  # 4096^3 regions
+        ws.grid[0] = ws.grid[1] = ws.grid[2] = 4096
+    assert _required(w, edit=huge) == 0
+
+    def quad_massless(s, ws, p):
+        s.phys[0] = 0.0
+    assert _required(W.c3(0)) > 0 and _required(W.c3(0), edit=quad_massless) == 0
+
+
+def test_arena_grows_by_the_per_node_rows():
+    """Doubling t_e adds the per-node rows of the tree and the per-sample
+    scratch: for the 6D Dubins airplane 191 bytes a node (state 24,
+    control 12, parent, region, sub-region, claim check, accept list and
+    V_E list 4 each, steps, set flag and sample flags 1 each, the kept end
+    state 32, network features 64 and outputs 32), up to 256-byte
+    alignment of each array."""
+    from paper_2409_06807_gb300 import workloads as W
+    a = _required(W.c2(0).with_(t_e=1 << 20))
+    b = _required(W.c2(0).with_(t_e=1 << 21))
+    assert a % 256 == 0 and b % 256 == 0
+    assert abs((b - a) - 191 * (1 << 20)) <= 256 * 32
+    q = _required(W.c3(0).with_(t_e=1 << 20))
+    q2 = _required(W.c3(0).with_(t_e=1 << 21))
+    # 12D: state 48, control 16, kept end state 64
+    assert abs((q2 - q) - (191 + 24 + 4 + 32) * (1 << 20)) <= 256 * 32
