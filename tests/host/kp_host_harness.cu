@@ -1,7 +1,7 @@
-// Host-only harness of the planner library's obstacle-set builders, for
-// CPU tests: the broad-phase grid of the step-hull test (shape choice, cell
-// lists) and the kd-tree of the free-space-obeying decomposition
-// (Sec. IV-B).  It compiles the library's host driver into this unit and
+// Host-only harness of the planner library's host logic, for CPU tests:
+// the broad-phase grid of the step-hull test (shape choice, cell lists),
+// the kd-tree of the free-space-obeying decomposition (Sec. IV-B) and the
+// query server's device-pool allocator.  It compiles the library's host driver into this unit and
 // calls its internal builders directly; no device code runs.  The launch
 // entry points the driver refers to are stubbed: they report "not
 // supported" and are never called here.
@@ -93,5 +93,34 @@ int kpt_kd_leaves(const float* boxes, int nb, const float* lo, const float* hi, 
     }
   return n;
 }
+
+// The query server's device-pool allocator (first fit over a free list of
+// 256-byte granules, coalescing on free), on a host-only server object
+// whose pool is the range [0, bytes).
+void* kpt_pool_new(size_t bytes) {
+  kp_server* s = new kp_server();
+  s->pool_bytes = bytes;
+  s->free_list[0] = bytes & ~(size_t)255;
+  return s;
+}
+int kpt_pool_alloc(void* s, size_t bytes, size_t* off) {
+  return pool_alloc(static_cast<kp_server*>(s), bytes, off) ? 1 : 0;
+}
+void kpt_pool_free(void* s, size_t off, size_t bytes) {
+  pool_free(static_cast<kp_server*>(s), off, bytes);
+}
+// Free blocks in offset order (up to cap); returns their count.
+int kpt_pool_blocks(void* s, size_t* offs, size_t* sizes, int cap) {
+  int n = 0;
+  for (const auto& kv : static_cast<kp_server*>(s)->free_list) {
+    if (n < cap) {
+      offs[n] = kv.first;
+      sizes[n] = kv.second;
+    }
+    ++n;
+  }
+  return n;
+}
+void kpt_pool_delete(void* s) { delete static_cast<kp_server*>(s); }
 
 }  // extern "C"

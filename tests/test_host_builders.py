@@ -1,13 +1,14 @@
-"""The planner library's host-side obstacle builders on CPU (no GPU): the
-broad-phase grid of the step-hull test and the kd-tree of the
-free-space-obeying decomposition (Sec. IV-B).
+"""The planner library's host logic on CPU (no GPU): the broad-phase grid of
+the step-hull test, the kd-tree of the free-space-obeying decomposition
+(Sec. IV-B) and the query server's device-pool allocator.
 
 The library's host driver is compiled into a small harness
-(tests/host/kp_host_harness.cu) whose entry points call the builders
+(tests/host/kp_host_harness.cu) whose entry points call these parts
 directly.  The grid's cell lists must give the verdict of testing every box
 (a box meeting a hull is listed in a cell the hull touches), its shape must
-follow the obstacle set, and the kd-tree's leaves must be the oracle's,
-built by the oracle's own code from the same rule."""
+follow the obstacle set, the kd-tree's leaves must be the oracle's, built
+by the oracle's own code from the same rule, and the allocator must tile
+the pool exactly with first-fit placement."""
 import ctypes as C
 import os
 import shutil
@@ -56,6 +57,15 @@ def H():
                            C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.kpt_kd_leaves.restype = C.c_int
     L.kpt_kd_leaves.argtypes = [f32, C.c_int, f32, f32, f32, C.c_int]
+    u64 = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+    L.kpt_pool_new.restype = C.c_void_p
+    L.kpt_pool_new.argtypes = [C.c_size_t]
+    L.kpt_pool_alloc.restype = C.c_int
+    L.kpt_pool_alloc.argtypes = [C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]
+    L.kpt_pool_free.argtypes = [C.c_void_p, C.c_size_t, C.c_size_t]
+    L.kpt_pool_blocks.restype = C.c_int
+    L.kpt_pool_blocks.argtypes = [C.c_void_p, u64, u64, C.c_int]
+    L.kpt_pool_delete.argtypes = [C.c_void_p]
     return L
 
 
@@ -172,3 +182,53 @@ def test_kd_tree_leaves_are_the_oracles(H, name):
     assert n == len(lo)
     np.testing.assert_array_equal(ours[:, :3], lo.astype(np.float32))
     np.testing.assert_array_equal(ours[:, 3:], hi.astype(np.float32))
+
+
+def _free_blocks(H, s):
+    offs = np.zeros(4096, np.uint64)
+    sizes = np.zeros(4096, np.uint64)
+    n = H.kpt_pool_blocks(s, offs, sizes, 4096)
+    assert n <= 4096
+    return [(int(o), int(z)) for o, z in zip(offs[:n], sizes[:n])]
+
+
+def test_server_pool_allocator(H):
+    """The server admits a query when its arena fits the device pool: first
+    fit over the free list in 256-byte granules, coalescing neighbours on
+    free.  A seeded mix of allocations and frees keeps the free list sorted,
+    aligned and coalesced, free plus allocated tiling the pool exactly, and
+    every allocation at the lowest free block that fits."""
+    total = 64 << 20
+    s = H.kpt_pool_new(total)
+    rng = np.random.default_rng(5)
+    live = {}
+    try:
+        for step in range(3000):
+            before = _free_blocks(H, s)
+            if live and (rng.random() < 0.45 or len(live) > 60):
+                off = int(rng.choice(sorted(live)))
+                H.kpt_pool_free(s, off, live.pop(off))
+            else:
+                want = int(rng.integers(1, 3 << 20))
+                need = (want + 255) // 256 * 256
+                off = C.c_size_t()
+                ok = H.kpt_pool_alloc(s, want, C.byref(off))
+                fits = [o for o, z in before if z >= need]
+                assert bool(ok) == bool(fits)
+                if ok:
+                    assert off.value == fits[0]
+                    live[off.value] = want
+            free = _free_blocks(H, s)
+            assert all(o % 256 == 0 and z % 256 == 0 and z > 0 for o, z in free)
+            assert all(a[0] + a[1] < b[0] for a, b in zip(free, free[1:]))  # sorted, coalesced
+            spans = sorted(free + [(o, (z + 255) // 256 * 256) for o, z in live.items()])
+            pos = 0
+            for o, z in spans:
+                assert o == pos
+                pos += z
+            assert pos == total
+        for off in list(live):
+            H.kpt_pool_free(s, off, live.pop(off))
+        assert _free_blocks(H, s) == [(0, total)]
+    finally:
+        H.kpt_pool_delete(s)
