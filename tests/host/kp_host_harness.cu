@@ -1,10 +1,10 @@
 // Host-only harness of the planner library's host logic, for CPU tests:
 // the broad-phase grid of the step-hull test (shape choice, cell lists),
 // the kd-tree of the free-space-obeying decomposition (Sec. IV-B) and the
-// query server's device-pool allocator.  It compiles the library's host driver into this unit and
-// calls its internal builders directly; no device code runs.  The launch
-// entry points the driver refers to are stubbed: they report "not
-// supported" and are never called here.
+// query server's device-pool allocator.  It compiles the library's host
+// code (kp_api.cu) into this unit and calls those parts directly; no
+// device code runs.  The launch entry points kp_api.cu refers to are
+// stubbed: they report "not supported" and are never called here.
 #include "../../paper_2409_06807_gb300/csrc/kp_api.cu"
 
 namespace kp {
