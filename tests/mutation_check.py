@@ -53,6 +53,19 @@ MUTATIONS = [
      "state box open at its lower bound"),
     ("model.c", "  else if (t >= (double)n)\n    i = n - 1;", "  else if (t > (double)n)\n    i = n - 1;",
      "binning: top clamp off by one"),
+    ("model.c", "    double t = speed_of(o, x) * ((double)o->cfg.speed_bins / o->cfg.speed_hi);",
+     "    double t = speed_of(o, x) * speed_of(o, x) * ((double)o->cfg.speed_bins / o->cfg.speed_hi);",
+     "binning: squared speed in the speed bins"),
+    ("model.c", "      const double y = x[dd] - 2.0 * pi * floor((x[dd] + pi) / (2.0 * pi));\n      t = (y + pi) * ((double)n / (2.0 * pi));",
+     "      const double y = x[dd] - 2.0 * pi * floor(x[dd] / (2.0 * pi));\n      t = y * ((double)n / (2.0 * pi));",
+     "binning: angle wrapped to [0, 2 pi)"),
+    ("model.c", "  int r = cell[0] + gx * (cell[1] + gy * (cell[2] + gz * (sb + nsb * e)));",
+     "  int r = cell[2] + gz * (cell[1] + gy * (cell[0] + gx * (sb + nsb * e)));",
+     "binning: region index with x slowest"),
+    # learned proposal features (reading R13)
+    ("planner.c", "for (int a = 0; a < 3; ++a) f[6 + a] = o->cfg.goal_c[a] - x[a];",
+     "for (int a = 0; a < 3; ++a) f[6 + a] = x[a] - o->cfg.goal_c[a];",
+     "features: goal offset with the wrong sign"),
     # free-space-obeying decomposition (Sec. IV-B, kd-tree over obstacle faces)
     ("model.c", "      split = cand[(u - 1) / 2];", "      split = cand[u / 2];",
      "kd-tree: upper instead of lower median"),
