@@ -120,7 +120,8 @@ def layouts():
     large = np.concatenate([lo, lo + big.uniform(0.3, 0.5, (400, 3)).astype(np.float32)], 1)
     return {"forest": W.c2(0).boxes, "building": W.c3(0).boxes, "random": W.c1(3).boxes,
             "forest along x": turned(W.c2(0).boxes, (2, 0, 1)),
-            "forest along y": turned(W.c2(0).boxes, (0, 2, 1)), "large boxes": large}
+            "forest along y": turned(W.c2(0).boxes, (0, 2, 1)), "large boxes": large,
+            "most boxes": W.random_boxes(9, 4096, side=(0.005, 0.03))}
 
 
 def test_grid_shape_follows_the_obstacles(H):
@@ -136,12 +137,16 @@ def test_grid_shape_follows_the_obstacles(H):
     assert blob(H, np.zeros((0, 6), np.float32))["g"] == [1, 1, 1]
 
 
-@pytest.mark.parametrize("name", ["forest", "building", "random", "forest along x", "large boxes"])
+@pytest.mark.parametrize("name", ["forest", "building", "random", "forest along x", "large boxes",
+                                  "most boxes"])
 def test_cell_lists_give_the_verdict_of_every_box(H, name):
+    """Every box meeting a hull is listed in a cell the hull touches; the
+    blob fits the arena's room for it (213,008 bytes) even at the box
+    capacity of 4,096."""
     boxes = layouts()[name]
     bp = blob(H, boxes)
     n = len(boxes)
-    assert bp["bytes"] <= BLOB_BYTES
+    assert bp["bytes"] <= 4096 * 32 + (4096 + 4) * 4 + 32768 * 2
     assert np.all(np.diff(bp["start"]) >= 0) and np.all(bp["ids"] < n)
     # each box is listed once in every cell of its range, nowhere else
     want = sum(np.prod([int(cell(b[3 + a], a, bp)) - int(cell(b[a], a, bp)) + 1 for a in range(3)])
