@@ -183,6 +183,10 @@ typedef struct {
   int64_t n_box_tests;   /* hull-vs-box tests made (after the broad phase)   */
   int32_t bp_cells;      /* broad-phase grid cells in all (1: every box)     */
   int32_t bp_grid[3];    /* broad-phase grid cells along x, y, z             */
+  int64_t n_key_batches; /* key batches warps took from the grid-wide counter
+                            after their first batch (the refill path)        */
+  int64_t n_lane_refills; /* keys a lane started after finishing an earlier
+                             key of the same pass                           */
 } kp_info;
 
 /* Host-side copy of the tree and decomposition (tests, checkpoints).
@@ -324,6 +328,18 @@ kp_status kp_set_sample_log(kp_ctx *ctx, const kp_sample_log *log);
  * bulk-copy completion).  On expiry the launch stops, the call returns
  * KP_ERR_TIMEOUT and the context is poisoned.  Default 2e9 (2 s). */
 kp_status kp_set_wait_limit(kp_ctx *ctx, uint64_t ns);
+
+/* Launch shape of the persistent loop (no counterpart in the paper: a
+ * property of this implementation).  Caps the loop launch at max_blocks
+ * blocks (0 restores the resident maximum of the device).  Results do not
+ * depend on the launch shape: every sample's draw, integration, check and
+ * binning follow from its key alone, claims are decided by the smallest
+ * key and appends are made in key order.  With few blocks every lane runs
+ * many keys of a pass, so the key-batch counter and lane refills (kp_info
+ * n_key_batches, n_lane_refills) are exercised on small problems; tests use
+ * this.  Errors: KP_ERR_ARG (negative, or a launch that cannot be resident;
+ * the previous shape is kept). */
+kp_status kp_set_grid_limit(kp_ctx *ctx, int32_t max_blocks);
 
 /* Test hook for the bounded-wait path: one block waits on a device flag
  * that nothing ever sets, for at most the context's wait limit, then

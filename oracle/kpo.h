@@ -169,6 +169,12 @@ void kpo_box_muller(const uint32_t w[4], double z[4]);
 /* ---- building blocks, exported for the oracle's own pin tests ---- */
 void kpo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
                        uint32_t out[4]);
+/* n blocks: counters ctr [n][4] under one key, words out [n][4]. */
+void kpo_philox4x32_10_n(const uint32_t *ctr, const uint32_t key[2], uint32_t *out,
+                         int64_t n);
+/* Volume of every region as Eq. 3 takes it: the grid cell's, or the
+ * kd-tree leaf's under the free-space-obeying decomposition. */
+void kpo_region_volumes(const kpo *o, double *vol);
 /* Advances x by one integrator step under control u (Eq. 1-2). */
 void kpo_step(const kpo_config *cfg, const double *x, const double *u,
               double h, double *x_out);

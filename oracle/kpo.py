@@ -98,6 +98,8 @@ def lib():
         L.kpo_path.restype = C.c_int32
         L.kpo_path.argtypes = [vp, _i32p, C.c_int32]
         L.kpo_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.kpo_philox4x32_10_n.argtypes = [_u32p, _u32p, _u32p, C.c_int64]
+        L.kpo_region_volumes.argtypes = [vp, _f64p]
         L.kpo_step.argtypes = [C.POINTER(Config), _f64p, _f64p, C.c_double, _f64p]
         L.kpo_propagate.argtypes = [C.POINTER(Config), _f64p, _f64p, C.c_int32, _f64p]
         L.kpo_step_valid.restype = C.c_int32
@@ -169,6 +171,15 @@ def make_config(w) -> Config:
 def philox4x32_10(ctr, key) -> np.ndarray:
     out = np.zeros(4, np.uint32)
     lib().kpo_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def philox4x32_10_n(ctrs, key) -> np.ndarray:
+    """Philox blocks of many counters ([n][4]) under one key ([n][4] words)."""
+    c = np.ascontiguousarray(ctrs, np.uint32).reshape(-1, 4)
+    out = np.zeros_like(c)
+    lib().kpo_philox4x32_10_n(c.reshape(-1), np.asarray(key, np.uint32), out.reshape(-1),
+                              len(c))
     return out
 
 
@@ -414,6 +425,12 @@ class Oracle:
         lib().kpo_bin(self._h, np.asarray(x, np.float64), C.byref(r), C.byref(s),
                       C.byref(m))
         return r.value, s.value, m.value
+
+    def region_volumes(self) -> np.ndarray:
+        """Volume of every region in Eq. 3 (grid cell or kd-tree leaf)."""
+        v = np.zeros(self.R)
+        lib().kpo_region_volumes(self._h, v)
+        return v
 
     def fso_leaves(self):
         """Leaf boxes (lo, hi), each (n_leaves, 3), of the free-space-obeying

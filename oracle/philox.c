@@ -46,3 +46,8 @@ void kpo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
   }
   out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
+
+void kpo_philox4x32_10_n(const uint32_t *ctr, const uint32_t key[2], uint32_t *out,
+                         int64_t n) {
+  for (int64_t i = 0; i < n; ++i) kpo_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}

@@ -177,6 +177,10 @@ void kpo_eq345_vol(int32_t n, const uint32_t *n_valid, const uint32_t *n_invalid
   if (score_sum) *score_sum = sum;
 }
 
+void kpo_region_volumes(const kpo *o, double *vol) {
+  for (int r = 0; r < o->R; ++r) vol[r] = o->region_vol ? o->region_vol[r] : o->vol;
+}
+
 int32_t kpo_lambda(int32_t t_e, int32_t n_tree, int32_t n_ve,
                    int32_t lambda_max) {
   if (n_ve <= 0) return lambda_max;

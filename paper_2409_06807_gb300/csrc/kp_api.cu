@@ -267,6 +267,7 @@ struct kp_ctx {
   KLog log;
   uint64_t wait_ns;
   int grid[2];
+  int grid_limit;  // 0: the resident maximum; else at most this many blocks
   size_t smem;
   int blob_base;  // blob bytes without the kd-tree copy
   int blob_kd;    // blob bytes with it (0: no tree)
@@ -706,6 +707,7 @@ kp_status configure_launch(kp_ctx* ctx) {
       if (bps < 1) return fail(ctx, KP_ERR_ARG, "loop kernel cannot be resident");
       int g = bps * ctx->num_sms;
       if (g > KP_MAX_GRID) g = KP_MAX_GRID;
+      if (ctx->grid_limit > 0 && g > ctx->grid_limit) g = ctx->grid_limit;
       ctx->grid[log] = g;
     }
     return KP_OK;
@@ -732,6 +734,7 @@ kp_status configure_launch(kp_ctx* ctx) {
     KP_CUDA(occupancy(d.sys, log != 0, smem_kd, &bps));
     int g = bps * ctx->num_sms;
     if (g > KP_MAX_GRID) g = KP_MAX_GRID;
+    if (ctx->grid_limit > 0 && g > ctx->grid_limit) g = ctx->grid_limit;
     if (g < ctx->grid[log]) return KP_OK;
   }
   ctx->P.blob_bytes = ctx->blob_kd;
@@ -1112,6 +1115,8 @@ kp_status kp_get_info(kp_ctx* ctx, kp_info* out) {
   out->n_box_tests = ctx->have_tree ? (int64_t)h.tot_box_tests : 0;
   out->bp_cells = ctx->P.bp_g[0] * ctx->P.bp_g[1] * ctx->P.bp_g[2];
   for (int a = 0; a < 3; ++a) out->bp_grid[a] = ctx->P.bp_g[a];
+  out->n_key_batches = ctx->have_tree ? (int64_t)h.tot_batches : 0;
+  out->n_lane_refills = ctx->have_tree ? (int64_t)h.tot_refills : 0;
   out->n_boxes = ctx->P.n_boxes_pad;
   out->grid_blocks = ctx->grid[ctx->log_on ? 1 : 0];
   return KP_OK;
@@ -1373,6 +1378,21 @@ kp_status kp_set_wait_limit(kp_ctx* ctx, uint64_t ns) {
   if (s != KP_OK) return s;
   if (ns < 1000) return fail(ctx, KP_ERR_ARG, "wait limit below 1 us");
   ctx->wait_ns = ns;
+  return KP_OK;
+}
+
+kp_status kp_set_grid_limit(kp_ctx* ctx, int32_t max_blocks) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (max_blocks < 0) return fail(ctx, KP_ERR_ARG, "negative grid limit");
+  const int old = ctx->grid_limit;
+  ctx->grid_limit = max_blocks;
+  s = configure_launch(ctx);
+  if (s != KP_OK) {
+    ctx->grid_limit = old;
+    kp_status r = configure_launch(ctx);
+    return r != KP_OK ? r : s;
+  }
   return KP_OK;
 }
 

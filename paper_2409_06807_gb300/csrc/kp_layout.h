@@ -62,6 +62,11 @@ struct KCtl {
   unsigned long long tot_steps;
   unsigned long long tot_hull;
   unsigned long long tot_box_tests;
+  // launch-shape counters since the last reset: key batches taken from the
+  // grid-wide counter (beyond each warp's first, fixed batch), and keys
+  // started by a lane that had already run a key in the same pass
+  unsigned long long tot_batches;
+  unsigned long long tot_refills;
   // barrier words on their own 128-byte line
   uint32_t bar_count;
   uint32_t pad1[31];

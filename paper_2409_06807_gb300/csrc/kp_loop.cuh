@@ -391,8 +391,11 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
   const uint32_t lt = (1u << lane) - 1u;
 
   // per-thread counts of one pass: a thread runs at most 2^28 / 256 keys of
-  // at most 255 steps each, so 32 bits hold them
-  uint32_t n_steps = 0, n_hull = 0, n_box = 0;
+  // at most 255 steps each, so 32 bits hold them; n_refill counts the keys
+  // a lane starts after its first one, n_batch (lane 0) the batches its
+  // warp takes from the grid counter
+  uint32_t n_steps = 0, n_hull = 0, n_box = 0, n_refill = 0, n_batch = 0;
+  bool ran = false;
   // lane state: the sample being integrated
   int key = -1, v = 0, k = 0, i = 0, fail = 0;
   bool done = false;
@@ -501,6 +504,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
             want = want < n_idle_now ? n_idle_now : (want > KP_KEY_BATCH ? KP_KEY_BATCH : want);
             base = static_end + atomicAdd(&P.ctl->work_next, want);
             base = base < S ? base : S;
+            n_batch += base < S ? 1u : 0u;
             pool_end = base + want < S ? base + want : S;
           }
           base = __shfl_sync(FULL, base, 0);
@@ -516,6 +520,8 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
         const int rank = __popc(m_idle & lt);
         if (key < 0 && rank < avail) {
           key = pool_next + rank;
+          n_refill += ran ? 1u : 0u;
+          ran = true;
           v = draw_sample<SYS>(P, it, key, lam, x, u, &k, &wacc, wr);
           i = 0;
           fail = 0;
@@ -550,13 +556,16 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
       }
     }
   }
-  unsigned long long bs, bh, bb, dummy;
+  unsigned long long bs, bh, bb, brf, bbt, dummy;
   block_sum2((unsigned long long)n_steps, (unsigned long long)n_hull, sh.red, &bs, &bh);
-  block_sum2((unsigned long long)n_box, 0, sh.red, &bb, &dummy);
+  block_sum2((unsigned long long)n_box, (unsigned long long)n_refill, sh.red, &bb, &brf);
+  block_sum2((unsigned long long)n_batch, 0, sh.red, &bbt, &dummy);
   if (threadIdx.x == 0 && bs) {
     atomicAdd(&P.ctl->tot_steps, bs);
     atomicAdd(&P.ctl->tot_hull, bh);
     atomicAdd(&P.ctl->tot_box_tests, bb);
+    if (brf) atomicAdd(&P.ctl->tot_refills, brf);
+    if (bbt) atomicAdd(&P.ctl->tot_batches, bbt);
   }
 }
 
@@ -1050,6 +1059,8 @@ __device__ void init_root(const KParams& P, const RootState& root) {
   ctl->tot_steps = 0;
   ctl->tot_hull = 0;
   ctl->tot_box_tests = 0;
+  ctl->tot_batches = 0;
+  ctl->tot_refills = 0;
   ctl->work_next = 0;
   if (!ok) {
     ctl->state = KP_DEV_BAD_ROOT;

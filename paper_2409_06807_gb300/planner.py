@@ -78,7 +78,8 @@ class Info(C.Structure):
                                            "n_regions", "n_subregions", "state_dim",
                                            "control_dim", "n_boxes", "grid_blocks")] + \
         [(n, C.c_int64) for n in ("n_samples", "n_steps", "n_hull_checks", "n_box_tests")] + \
-        [("bp_cells", C.c_int32), ("bp_grid", C.c_int32 * 3)]
+        [("bp_cells", C.c_int32), ("bp_grid", C.c_int32 * 3),
+         ("n_key_batches", C.c_int64), ("n_lane_refills", C.c_int64)]
 
 
 class TreeView(C.Structure):
@@ -120,6 +121,7 @@ SIGNATURES = {
     "kp_resume": (C.c_int, [_vp, C.POINTER(Budget), C.POINTER(Traj)]),
     "kp_set_sample_log": (C.c_int, [_vp, C.POINTER(SampleLog)]),
     "kp_set_wait_limit": (C.c_int, [_vp, C.c_uint64]),
+    "kp_set_grid_limit": (C.c_int, [_vp, C.c_int32]),
     "kp_selftest_wait_timeout": (C.c_int, [_vp]),
     "kp_plan_static": (C.c_int, [C.POINTER(System), C.POINTER(Workspace), C.POINTER(Obstacles),
                                  C.POINTER(Params), C.POINTER(C.c_float), C.POINTER(Goal),
@@ -517,6 +519,10 @@ class Planner:
     # ------------------------------------------------------------------
     def set_wait_limit(self, ns):
         self._check(lib().kp_set_wait_limit(self._ctx, int(ns)), "kp_set_wait_limit")
+
+    def set_grid_limit(self, max_blocks):
+        """Caps the loop launch at max_blocks blocks (0: the resident maximum)."""
+        self._check(lib().kp_set_grid_limit(self._ctx, int(max_blocks)), "kp_set_grid_limit")
 
     def selftest_wait_timeout(self):
         return lib().kp_selftest_wait_timeout(self._ctx)
