@@ -1,11 +1,13 @@
 #!/usr/bin/env python
 """Kino-PAX planning throughput on one GB300 (or N, as independent replicas).
 
-One step = one complete planning query (Problem 1) on a fresh seeded
-synthetic layout: reset, the device-resident loop of Propagate /
+One step = complete planning queries (Problem 1) on 10 fresh seeded
+synthetic layouts, each: reset, the device-resident loop of Propagate /
 UpdateEstimates / UpdateNodeSets until a goal node is appended, and the
 trajectory read-back.  Default workload: 6D Dubins airplane in a forest of
-200 vertical boxes, 16^3 regions x 4^3 sub-regions, lambda_max 64, t_e 2^20.
+200 vertical boxes, 16^3 regions x 4^3 sub-regions, lambda_max 64, t_e 2^20;
+the double-integrator and quadrotor workloads follow as legs of the same
+line, each with its own roofline.
 
 Printed (rank 0, one JSON line): samples propagated+checked per second over
 the device time of the queries (inputs resident, L2 flushed before every
@@ -35,19 +37,38 @@ from paper_2409_06807_gb300 import workloads as W  # noqa: E402
 
 METRIC = "samples propagated+checked/s"
 MAX_ITERS = 400
+LAYOUTS_PER_STEP = 10  # one timed step plans this many layouts
 KCTL_BYTES = 512
 
-# Algorithmic lane operations per unit of work (see the design notes):
-# per sample: two Philox4x32-10 blocks (10 rounds x 10 integer ops each),
-# the control and duration maps, binning, counters and flags;
-# per integrator step: the integrator itself plus the state-box test;
-# per step hull: its 6 min/max and the broad-phase cell range (6 x 5 ops);
-# per hull-vs-box test: 8 ops, counted over the boxes the uniform-grid broad
-# phase leaves to test (the pruned count, not every box of the layout).
-OPS_PER_SAMPLE = {W.DI: 200 + 11 + 30, W.DUBINS: 200 + 11 + 30, W.QUAD: 200 + 14 + 34}
-OPS_PER_STEP = {W.DI: 6 + 18, W.DUBINS: 222 + 18, W.QUAD: 688 + 36}
+# Algorithmic lane operations per unit of work.  Counting rule: one lane
+# operation per arithmetic or logic operation the method needs; addressing,
+# loop control, padding, divergence and data movement are not counted; the
+# sine and cosine of one angle cost 6 (a 2 pi reduction of 4, then the two
+# hardware approximations), a correctly rounded division or reciprocal 4.
+# per sample: 2 Philox4x32-10 blocks (2 x 10 rounds x 6 integer ops = 120),
+#   the control map (4 per control), the duration (2), the accept compare
+#   (1), binning (20), counter and claim updates (2); the quadrotor also
+#   forms its thrust and body torques once per sample (12):
+#   DI and Dubins 120 + 3 x 4 + 2 + 1 + 20 + 2 = 157;
+#   quadrotor 120 + 4 x 4 + 2 + 1 + 20 + 2 + 12 = 173.
+# per integrator step: the integrator, then the state-box test (2 compares
+#   per state entry):
+#   DI, Euler: 3 axes x 2 FMA = 6, + 12 = 18;
+#   Dubins, RK4: 4 field evaluations x (2 sin/cos of 6 + 5 products) + 3
+#     stage points x 6 FMA + 6 entries x 4 (combination) + 1 + 4 (h/2, h/6)
+#     = 115, + 12 = 127;
+#   quadrotor, RK4: 4 x (3 sin/cos of 6 + a reciprocal of 4 + 34 products
+#     and sums) + 3 x 12 + 12 x 4 + 1 + 4 = 313, + 24 = 337.
+# per step hull (end state in the state box): 6 (min and max per axis).
+# per hull-vs-box test: 8, counted over the boxes the uniform-grid broad
+#   phase leaves to test (the pruned count); the brute-force figure beside
+#   it counts every box at every hull.
+# The oracle counts the same units during replay (oracle/work.c);
+# tests/test_bench_host.py pins this table to its count.
+OPS_PER_SAMPLE = {W.DI: 157, W.DUBINS: 157, W.QUAD: 173}
+OPS_PER_STEP = {W.DI: 18, W.DUBINS: 127, W.QUAD: 337}
 OPS_PER_BOX = 8
-OPS_PER_HULL = 6 + 30
+OPS_PER_HULL = 6
 
 
 def alg_ops(system, samples, steps, hulls, box_tests):
@@ -209,8 +230,8 @@ def workload_config(w):
         "regions": f"{w.grid[0]}x{w.grid[1]}x{w.grid[2]}x{w.speed_bins} x sub "
                    f"{w.sub[0]}x{w.sub[1]}x{w.sub[2]}",
         "lambda_max": w.lambda_max, "t_e": w.t_e, "delta": w.delta, "eps": w.eps,
-        "layouts": "one seeded synthetic layout per step (rank-offset seeds)",
-        "l2": "flushed before every timed step (256 MiB device write)",
+        "layouts": f"{LAYOUTS_PER_STEP} seeded synthetic layouts per step (rank-offset seeds)",
+        "l2": "flushed before every query (256 MiB device write)",
         "max_iters": MAX_ITERS,
     }
 
@@ -340,6 +361,118 @@ def mode_summary(rows, ok_status):
             "mean_ms": float(ms.mean()), "samples_per_s": samples / (ms.sum() / 1e3),
             "mean_samples": samples / len(rows), "steps_per_sample": steps / max(1, samples),
             "set_obstacles_ms": float(np.mean([r[2]["set_obstacles_ms"] for r in rows]))}
+
+
+def bootstrap_ci(samples, ms, reps=2000, seed=0):
+    """95 % interval of sum(samples) / sum(ms) over layouts resampled with
+    replacement (samples/s)."""
+    samples = np.asarray(samples, np.float64)
+    ms = np.asarray(ms, np.float64)
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, len(ms), size=(reps, len(ms)))
+    vals = samples[idx].sum(1) / (ms[idx].sum(1) / 1e3)
+    return [float(np.percentile(vals, 2.5)), float(np.percentile(vals, 97.5))]
+
+
+def roofline_of(system, infos, loop_ms, peak_ops, n_boxes, traffic):
+    """Achieved algorithmic lane operations per second of the loop kernel
+    (the device's work counters under the counting rule of OPS_PER_*)
+    against the lane-issue peak; beside it the same with every box tested
+    at every hull (the brute-force checker's work, which the broad phase
+    avoids: a rate of useful work done, not a fraction of the kernel's
+    own work)."""
+    samples = sum(i["n_samples"] for i in infos)
+    steps = sum(i["n_steps"] for i in infos)
+    hulls = sum(i["n_hull_checks"] for i in infos)
+    boxes = sum(i["n_box_tests"] for i in infos)
+    sec = sum(loop_ms) / 1e3
+    ops = alg_ops(system, samples, steps, hulls, boxes)
+    achieved = ops / sec / 1e12
+    brute = alg_ops(system, samples, steps, hulls, n_boxes * hulls) / sec / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
+            "frac": achieved / peak_ops, "traffic": traffic,
+            "ops_per_sample": ops / max(1, samples),
+            "work_per_sample": {"steps": steps / max(1, samples), "hulls": hulls / max(1, samples),
+                                "box_tests": boxes / max(1, samples)},
+            "brute_force_every_box": {"achieved": brute, "box_tests_per_hull": n_boxes,
+                                      "frac": brute / peak_ops}}
+
+
+def workload_leg(name, n_layouts, local, flush, peak_ops, seed0=70_000):
+    """Whole queries of another configuration (same kernels), L2 flushed
+    before each, with its own roofline."""
+    from paper_2409_06807_gb300 import planner as P
+    make = W.BY_NAME[name]
+    seeds = list(range(seed0, seed0 + n_layouts))
+    pl = P.Planner(make(seeds[0]), device=f"cuda:{local}")
+    timed_query(pl, make(seeds[0]), flush, MAX_ITERS)  # warm
+    rows, loop_ms = [], []
+    for s in seeds:
+        rows.append(timed_query(pl, make(s), flush, MAX_ITERS))
+        loop_ms.append(pl.last_launch_ms())
+    pl.close()
+    out = mode_summary(rows, P.OK)
+    w = make(seeds[0])
+    out["workload"] = f"{w.name}, {n_layouts} layouts (seeds {seeds[0]}..{seeds[-1]})"
+    out["config"] = workload_config(w)
+    out["samples_per_s_ci95"] = bootstrap_ci([r[2]["n_samples"] for r in rows],
+                                             [r[1] for r in rows])
+    out["roofline"] = roofline_of(w.system, [r[2] for r in rows], loop_ms, peak_ops,
+                                  len(w.boxes), profiled_traffic(f"kp_loop_kernel_{name}"))
+    return out
+
+
+def nodeset_leg(local, peak_ops, hbm_gbs, n_nodes=1 << 22, reps=10):
+    """The node-set pass of Algorithm 4 on a large tree: a seeded tree of
+    n_nodes nodes (the quadrotor building's system, t_e 2^23) whose V_E
+    holds a single node, so that one loop pass is almost all node-set work:
+    one Philox block per old node (counter it, v, 0, 2) against its
+    region's threshold, the in_ve write, and the count and list of V_E.
+    Time: block 0's phase timers of that phase and its barrier wait.
+    Algorithmic bytes per old node: region (4 B read) + in_ve (1 B write) +
+    in_ve re-read by the V_E list (1 B); thresholds are L2-resident."""
+    from paper_2409_06807_gb300 import planner as P
+    w = W.c3(0, t_e=1 << 23)
+    pl = P.Planner(w, device=f"cuda:{local}")
+    rng = np.random.default_rng(0)
+    n = n_nodes
+    R, ns = pl.n_regions, pl.n_sub
+    per = int(np.prod(w.sub))
+    region = rng.integers(0, R, size=n).astype(np.int32)
+    sub = (region * per + rng.integers(0, per, size=n)).astype(np.int32)
+    st = np.zeros((n, 12), np.float32)
+    lo, hi = w.x_lo[:12].copy(), w.x_hi[:12].copy()
+    st[:, :3] = rng.uniform(0.0, 1.0, size=(n, 3))
+    st[:, 3:] = 0.0
+    parent = np.maximum(np.arange(n, dtype=np.int32) - 1, -1)
+    in_ve = np.zeros(n, np.uint8)
+    in_ve[0] = 1
+    visited = np.zeros(ns, np.uint8)
+    visited[sub] = 1
+    nv = np.bincount(region, minlength=R).astype(np.uint32)
+    tree = dict(n_nodes=n, iteration=0, state=st, parent=parent, ctrl=np.zeros((n, 4), np.float32),
+                steps=np.ones(n, np.int32), region=region, sub=sub, in_ve=in_ve,
+                n_valid=nv, n_invalid=np.zeros(R, np.uint32),
+                thr=rng.integers(0, 1 << 32, size=R, dtype=np.uint64), visited=visited)
+    ms = []
+    for i in range(reps + 3):
+        pl.import_tree(tree)
+        s = pl.expand_step(1)[0]
+        if i >= 3:
+            ms.append((s["phase_ns"][8] + s["phase_ns"][9]) / 1e6)
+    pl.close()
+    t = float(np.median(ms))
+    gbs = 6.0 * n / (t / 1e3) / 1e9
+    ops = 64 * n  # one Philox block (60), the threshold compare and the V_E count (4)
+    return {"workload": f"{n} old nodes (quadrotor building system), one pass with |V_E| = 1, "
+                        f"median of {reps}",
+            "ms": t, "nodes_per_s": n / (t / 1e3),
+            "hbm": {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
+                    "frac": gbs / hbm_gbs, "bytes_per_node": 6},
+            "alu": {"achieved": ops / (t / 1e3) / 1e12, "peak": peak_ops, "unit": "Top/s",
+                    "frac": ops / (t / 1e3) / 1e12 / peak_ops, "ops_per_node": 64},
+            "note": "one 10-round Philox block per node costs more lane time than its 6 bytes "
+                    "of DRAM traffic: the pass is ALU-bound, not HBM-bound"}
 
 
 def steady_state_leg(local, peak_ops, n_frontier=65536, reps=20):
@@ -589,8 +722,9 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     make = W.BY_NAME[args.workload]
+    per = args.layouts_per_step
     n_total = args.warmup + args.steps
-    seeds = rank_seeds(rank, n_total)
+    seeds = rank_seeds(rank, n_total * per)
     layouts = [make(s) for s in seeds]
     w0 = layouts[0]
     pl = P.Planner(w0, device=f"cuda:{local}")
@@ -614,7 +748,7 @@ def run_ours(args, world, rank, local):
         info = pl.info()
         return st, step_ms, loop_ms, info
 
-    for i in range(args.warmup):
+    for i in range(args.warmup * per):
         one_query(layouts[i])
 
     barrier(world)
@@ -622,41 +756,47 @@ def run_ours(args, world, rank, local):
     rows = []
     with ClockSampler(local) as clk:
         t_wall0 = time.perf_counter()
-        for i in range(args.warmup, n_total):
+        for i in range(args.warmup * per, n_total * per):
             rows.append(one_query(layouts[i]))
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
     barrier(world)
 
-    step_ms = [r[1] for r in rows]
+    query_ms = [r[1] for r in rows]
     loop_ms = [r[2] for r in rows]
     samples = sum(r[3]["n_samples"] for r in rows)
     solved = sum(1 for r in rows if r[0] == P.OK)
-    total_ms = sum(step_ms)
+    total_ms = sum(query_ms)
     total_ms_max = max_over_ranks(total_ms, world)
     samples_all = sum_over_ranks(float(samples), world)
     value = samples_all / (total_ms_max / 1e3)
+    per_layout_rate = [r[3]["n_samples"] / (r[1] / 1e3) for r in rows]
 
     # roofline of the persistent loop kernel (dominant kernel)
-    ops = sum(alg_ops(w0.system, r[3]["n_samples"], r[3]["n_steps"], r[3]["n_hull_checks"],
-                      r[3]["n_box_tests"]) for r in rows)
-    box_tests_per_hull = (sum(r[3]["n_box_tests"] for r in rows)
-                          / max(1, sum(r[3]["n_hull_checks"] for r in rows)))
     pk, pk_kind = peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     peak_ops = n_sm * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12  # Top/s
-    achieved = ops / (sum(loop_ms) / 1e3) / 1e12
-    traffic = profiled_traffic(f"kp_loop_kernel_{args.workload}")
+    roof = roofline_of(w0.system, [r[3] for r in rows], loop_ms, peak_ops, len(w0.boxes),
+                       profiled_traffic(f"kp_loop_kernel_{args.workload}"))
     # the same denominator measured: the library's FMA microbenchmark (after
     # the timed region; 6 launches of about a millisecond)
     peak_measured = P.measure_lane_peak() / 1e12
+    roof.update({"peak_source": f"{n_sm} SMs x 128 lanes x {pk.get('sm_max_mhz')} MHz "
+                                f"({pk_kind} max SM clock)",
+                 "peak_measured": peak_measured,
+                 "frac_of_measured": roof["achieved"] / peak_measured,
+                 "peak_measured_how": "kp_measure_lane_peak: 8 independent FP32 FMA chains "
+                                      "per thread, full-occupancy grid, best of 5 launches",
+                 "work_source": "device counters of samples, integrator steps, step hulls and "
+                                "box tests (equal to the oracle's replay counts in the parity "
+                                "tests) x the lane operations per unit of bench.OPS_PER_*"})
 
     # end to end through the public API with host buffers: obstacle upload
     # from pinned staging, the query, the trajectory read-back
     torch.cuda.synchronize()
     e2e_samples = 0
     t0 = time.perf_counter()
-    for i in range(args.warmup, n_total):
+    for i in range(args.warmup * per, n_total * per):
         w = layouts[i]
         pl.set_obstacles(w.boxes)
         pl.w = w
@@ -665,13 +805,19 @@ def run_ours(args, world, rank, local):
     t_e2e = time.perf_counter() - t0
     t_e2e = max_over_ranks(t_e2e, world)
     e2e_all = sum_over_ranks(float(e2e_samples), world)
-    h2d = int(np.mean([((len(layouts[i].boxes) + 7) // 8 * 8) * 32
-                       for i in range(args.warmup, n_total)]))
-    d2h = KCTL_BYTES + 256 * 17 * 4  # header + first trajectory rows
+    h2d = per * int(np.mean([((len(layouts[i].boxes) + 7) // 8 * 8) * 32
+                             for i in range(args.warmup * per, n_total * per)]))
+    d2h = per * (KCTL_BYTES + 256 * 17 * 4)  # header + first trajectory rows, per query
 
     if rank != 0:
         return
     extra = {}
+    if args.c1_layouts > 0 and args.workload != "c1":
+        extra["c1"] = workload_leg("c1", args.c1_layouts, local, flush, peak_ops)
+    if args.c3_layouts > 0 and args.workload != "c3":
+        extra["c3"] = workload_leg("c3", args.c3_layouts, local, flush, peak_ops)
+    if args.nodeset:
+        extra["nodeset_pass"] = nodeset_leg(local, peak_ops, float(pk.get("hbm_gbs", 6800.0)))
     if args.steady:
         extra["steady_state"] = steady_state_leg(local, peak_ops)
     if args.decomp_layouts > 0:
@@ -689,33 +835,33 @@ def run_ours(args, world, rank, local):
     cpu = cpu_baseline(make) if world == 1 and not args.no_cpu else None
     if cpu is not None:
         cpu["all_cores"] = cpu_baseline_all_cores(args.workload)
-    pct = np.percentile(step_ms, [50, 99])
+    pct = np.percentile(query_ms, [50, 99])
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**workload_config(w0), "parallelism": f"replicas x{world}"},
+        "config": {**workload_config(w0), "layouts_per_step": per,
+                   "parallelism": f"replicas x{world}"},
+        "value_ci95": bootstrap_ci([r[3]["n_samples"] for r in rows], query_ms),
+        "per_layout_rate": {"median": float(np.median(per_layout_rate)),
+                            "p10": float(np.percentile(per_layout_rate, 10)),
+                            "p90": float(np.percentile(per_layout_rate, 90))},
         "solve_ms": {"p50": float(pct[0]), "p99": float(pct[1]),
-                     "mean": float(np.mean(step_ms))},
+                     "mean": float(np.mean(query_ms)), "layouts": len(rows)},
         "success_rate": solved / len(rows),
-        "loop_kernel_ms": {"mean": float(np.mean(loop_ms))},
-        "work": {"samples_per_step": samples / len(rows),
+        "loop_kernel_ms": {"mean": float(np.mean(loop_ms)),
+                           "share_of_query": float(sum(loop_ms) / total_ms)},
+        "work": {"samples_per_query": samples / len(rows),
                  "steps_per_sample": sum(r[3]["n_steps"] for r in rows) / max(1, samples),
-                 "box_tests_per_hull": box_tests_per_hull,
+                 "box_tests_per_hull": (sum(r[3]["n_box_tests"] for r in rows)
+                                        / max(1, sum(r[3]["n_hull_checks"] for r in rows))),
                  "broad_phase_grid": rows[-1][3]["bp_grid"]},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
-                     "frac": achieved / peak_ops, "traffic": traffic,
-                     "peak_source": f"{n_sm} SMs x 128 lanes x {pk.get('sm_max_mhz')} MHz "
-                                    f"({pk_kind} max SM clock)",
-                     "peak_measured": peak_measured,
-                     "frac_of_measured": achieved / peak_measured,
-                     "peak_measured_how": "kp_measure_lane_peak: 8 independent FP32 FMA chains "
-                                          "per thread, full-occupancy grid, best of 5 launches"},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_all / t_e2e, "unit": "samples/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 3 * per * args.steps,
         "clocks": clk.summary(),
         "wall_s": t_wall,
         **extra,
@@ -726,11 +872,19 @@ def run_ours(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(W.BY_NAME))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--layouts-per-step", type=int, default=LAYOUTS_PER_STEP,
+                    help="seeded layouts planned in one timed step")
+    ap.add_argument("--c1-layouts", type=int, default=200,
+                    help="layouts of the double-integrator leg (0: skip)")
+    ap.add_argument("--c3-layouts", type=int, default=10,
+                    help="layouts of the quadrotor-building leg (0: skip)")
+    ap.add_argument("--no-nodeset", dest="nodeset", action="store_false",
+                    help="skip the node-set pass measurement")
     ap.add_argument("--learned-layouts", type=int, default=1000,
                     help="held-out layouts of the learned-vs-plain comparison (0: skip)")
     ap.add_argument("--decomp-layouts", type=int, default=100,

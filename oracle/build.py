@@ -9,7 +9,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["philox.c", "model.c", "planner.c", "mlp.c"]
+SOURCES = ["philox.c", "model.c", "planner.c", "mlp.c", "work.c"]
 LIB = os.path.join(HERE, "libkpo.so")
 
 

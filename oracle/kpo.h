@@ -91,6 +91,23 @@ typedef struct {
       goal_node;
 } kpo_iter_stats;
 
+/* Algorithmic work of Propagate (Algorithm 2) since the last reset or
+ * import, counted during replay (the counting rule is in work.c). */
+typedef struct {
+  uint64_t samples;   /* samples drawn                                       */
+  uint64_t steps;     /* integrator steps run (to the first invalid one)     */
+  uint64_t hulls;     /* steps whose end state is in the state box: their
+                         hull is tested against the obstacles              */
+  uint64_t box_scan;  /* hull-vs-box tests of a scan in box order that stops
+                         at the first box met                              */
+  uint64_t box_grid;  /* the same over the boxes of the grid cells the hull
+                         overlaps (kpo_set_work_grid)                      */
+  uint64_t ops;       /* lane operations: samples, steps, hulls and the
+                         grid's box tests at their costs                   */
+  /* box_scan, box_grid and their operations are counted only after
+   * kpo_set_work_grid */
+} kpo_work;
+
 typedef struct kpo kpo;
 
 kpo *kpo_create(const kpo_config *cfg, const float *boxes, int32_t n_boxes);
@@ -165,6 +182,17 @@ int32_t kpo_set_mlp(kpo *o, const float *params, double mix);
 int32_t kpo_set_harvest(kpo *o, double *feat, double *target, int32_t capacity);
 int32_t kpo_harvest_count(const kpo *o);
 void kpo_box_muller(const uint32_t w[4], double z[4]);
+
+/* Work counting (work.c).  The grid of the pruned box count: g[a] cells
+ * along position axis a over W (default 1 x 1 x 1: every box in one cell). */
+void kpo_set_work_grid(kpo *o, const int32_t g[3]);
+void kpo_get_work(const kpo *o, kpo_work *out);
+void kpo_clear_work(kpo *o);
+/* Lane operations per unit: sample, integrator step, hull, box test. */
+uint64_t kpo_work_ops_sample(const kpo *o);
+uint64_t kpo_work_ops_step(const kpo *o);
+uint64_t kpo_work_ops_hull(void);
+uint64_t kpo_work_ops_box(void);
 
 /* ---- building blocks, exported for the oracle's own pin tests ---- */
 void kpo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],

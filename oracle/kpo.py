@@ -54,6 +54,11 @@ class Records(C.Structure):
     ]
 
 
+class Work(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("samples", "steps", "hulls", "box_scan", "box_grid",
+                                           "ops")]
+
+
 class IterStats(C.Structure):
     _fields_ = [(n, C.c_int32) for n in (
         "iteration", "n_ve", "lambda_", "n_samples", "n_valid", "n_accepted",
@@ -100,6 +105,15 @@ def lib():
         L.kpo_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         L.kpo_philox4x32_10_n.argtypes = [_u32p, _u32p, _u32p, C.c_int64]
         L.kpo_region_volumes.argtypes = [vp, _f64p]
+        L.kpo_set_work_grid.argtypes = [vp, _i32p]
+        L.kpo_get_work.argtypes = [vp, C.POINTER(Work)]
+        L.kpo_clear_work.argtypes = [vp]
+        for name in ("kpo_work_ops_sample", "kpo_work_ops_step"):
+            getattr(L, name).restype = C.c_uint64
+            getattr(L, name).argtypes = [vp]
+        for name in ("kpo_work_ops_hull", "kpo_work_ops_box"):
+            getattr(L, name).restype = C.c_uint64
+            getattr(L, name).argtypes = []
         L.kpo_step.argtypes = [C.POINTER(Config), _f64p, _f64p, C.c_double, _f64p]
         L.kpo_propagate.argtypes = [C.POINTER(Config), _f64p, _f64p, C.c_int32, _f64p]
         L.kpo_step_valid.restype = C.c_int32
@@ -425,6 +439,26 @@ class Oracle:
         lib().kpo_bin(self._h, np.asarray(x, np.float64), C.byref(r), C.byref(s),
                       C.byref(m))
         return r.value, s.value, m.value
+
+    def set_work_grid(self, g):
+        """Broad-phase grid (cells per position axis) of the pruned box count."""
+        lib().kpo_set_work_grid(self._h, np.ascontiguousarray(g, np.int32))
+
+    def work(self) -> dict:
+        """Work counted since the last reset or import (see oracle/work.c)."""
+        wk = Work()
+        lib().kpo_get_work(self._h, C.byref(wk))
+        return {n: int(getattr(wk, n)) for n, _ in Work._fields_}
+
+    def clear_work(self):
+        lib().kpo_clear_work(self._h)
+
+    def work_costs(self) -> dict:
+        """Lane operations per sample, integrator step, hull and box test."""
+        L = lib()
+        return {"sample": int(L.kpo_work_ops_sample(self._h)),
+                "step": int(L.kpo_work_ops_step(self._h)),
+                "hull": int(L.kpo_work_ops_hull()), "box": int(L.kpo_work_ops_box())}
 
     def region_volumes(self) -> np.ndarray:
         """Volume of every region in Eq. 3 (grid cell or kd-tree leaf)."""

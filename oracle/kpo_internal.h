@@ -46,6 +46,13 @@ struct kpo {
   int status;
   int goal_node;
 
+  /* algorithmic work counted during replay (work.c), since the last
+   * reset or import; wgrid: the broad-phase grid of the pruned box count */
+  kpo_work work;
+  int32_t wgrid[3];
+  int32_t *wbox;           /* [nb][6] cell range of each box in that grid,
+                              NULL until a work grid is set                */
+
   /* learned proposal */
   double *mlp;           /* parameter vector, NULL when off */
   double mix;
@@ -56,5 +63,9 @@ struct kpo {
 /* Builds the kd-tree of the free-space-obeying decomposition from the
  * obstacles (model.c).  Returns 0, or -1 past KPO_FSO_MAX_LEAVES leaves. */
 int kpo_build_fso(kpo *o);
+
+/* Work of one sample drawn / one integrator step from x0 to x1 (work.c). */
+void kpo_sample_work(kpo *o);
+void kpo_step_work(kpo *o, const double *x0, const double *x1);
 
 #endif

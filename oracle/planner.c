@@ -104,6 +104,7 @@ kpo *kpo_create(const kpo_config *cfg, const float *boxes, int32_t n_boxes) {
   o->thr = (uint64_t *)xcalloc(o->R, sizeof(uint64_t));
   o->status = KPO_ERR;
   o->goal_node = -1;
+  o->wgrid[0] = o->wgrid[1] = o->wgrid[2] = 1;
   return o;
 }
 
@@ -114,7 +115,7 @@ void kpo_destroy(kpo *o) {
   free(o->n_invalid); free(o->cov); free(o->avail); free(o->visited);
   free(o->score); free(o->p_accept); free(o->thr); free(o->mlp);
   free(o->kd_axis); free(o->kd_right); free(o->kd_leaf); free(o->kd_split);
-  free(o->leaf_lo); free(o->leaf_hi); free(o->region_vol);
+  free(o->leaf_lo); free(o->leaf_hi); free(o->region_vol); free(o->wbox);
   free(o);
 }
 
@@ -347,6 +348,7 @@ int32_t kpo_reset(kpo *o, const float *x_init) {
   o->iteration = 0;
   o->goal_node = -1;
   o->status = KPO_RUNNING;
+  kpo_clear_work(o);
   if (in_goal(o, x, NULL)) {
     o->goal_node = 0;
     o->status = KPO_SOLVED;
@@ -437,9 +439,11 @@ int32_t kpo_iterate(kpo *o, kpo_records *rec, kpo_iter_stats *st) {
       memcpy(traj, o->x + (size_t)v * d, sizeof(double) * d);
       int valid = 1, fail = 0, last = 0;
       double m_valid = INFINITY;
+      kpo_sample_work(o);
       for (int i = 1; i <= k; ++i) {
         kpo_step(&o->cfg, traj + (size_t)(i - 1) * d, u, o->cfg.dt,
                  traj + (size_t)i * d);
+        kpo_step_work(o, traj + (size_t)(i - 1) * d, traj + (size_t)i * d);
         double m;
         int ok = kpo_step_valid(o, traj + (size_t)(i - 1) * d,
                                 traj + (size_t)i * d, &m);
@@ -637,6 +641,7 @@ int32_t kpo_import(kpo *o, int32_t n_nodes, int32_t iteration,
   o->iteration = iteration;
   o->goal_node = -1;
   o->status = KPO_RUNNING;
+  kpo_clear_work(o);
   return KPO_RUNNING;
 }
 

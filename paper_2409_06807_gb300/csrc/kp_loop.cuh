@@ -426,8 +426,12 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
         break;
       }
     }
+    // finished lanes are finalised together: REFILL_MIN of them while keys
+    // remain (they are refilled at once), and once the pass's keys are all
+    // handed out, only when every lane has finished, so that the warp's
+    // last samples cost one finalise instead of one per finishing step
     const uint32_t m_free = __ballot_sync(FULL, key < 0 || done);
-    if (__popc(m_free) >= Sys::REFILL_MIN || (exhausted && m_free)) {
+    if (exhausted ? m_free == FULL : __popc(m_free) >= Sys::REFILL_MIN) {
       // ---- finalise the lanes that finished -------------------------------
       if (key >= 0 && done) {
         int r, s;

@@ -197,3 +197,17 @@ def check_downstream(w, ost, orec, gst, grec, amb, before, after, otree, vol):
         inside = np.flatnonzero(d <= float(w.goal_r))
         want = n0 + int(inside[0]) if len(inside) else -1
         assert gst["goal_node"] == want, (gst["goal_node"], want)
+
+
+def check_work(gi0, gi1, ow0, ow1):
+    """The device's work counters over one pass whose decisions all matched
+    the oracle's equal the oracle's replay count: samples, integrator steps
+    and step hulls exactly; broad-phase box tests within 2 % (the device
+    places a hull in the grid from FP32 coordinates, the oracle from FP64
+    ones, so a hull on a cell face may visit one more or one fewer cell)."""
+    for dev, orc in (("n_samples", "samples"), ("n_steps", "steps"), ("n_hull_checks", "hulls")):
+        assert gi1[dev] - gi0[dev] == ow1[orc] - ow0[orc], (dev, gi1[dev] - gi0[dev],
+                                                           ow1[orc] - ow0[orc])
+    db = gi1["n_box_tests"] - gi0["n_box_tests"]
+    ob = ow1["box_grid"] - ow0["box_grid"]
+    assert abs(db - ob) <= 0.02 * ob + 8, (db, ob)

@@ -12,13 +12,39 @@ from paper_2409_06807_gb300 import workloads as W
 
 def test_algorithmic_work_per_unit():
     # per sample, per integrator step, per step hull, per hull-vs-box test
-    for system, sample, step in ((W.DI, 241, 24), (W.DUBINS, 241, 240), (W.QUAD, 248, 724)):
+    for system, sample, step in ((W.DI, 157, 18), (W.DUBINS, 157, 127), (W.QUAD, 173, 337)):
         assert bench.alg_ops(system, 1, 0, 0, 0) == sample
         assert bench.alg_ops(system, 0, 1, 0, 0) == step
-        assert bench.alg_ops(system, 0, 0, 1, 0) == 36
+        assert bench.alg_ops(system, 0, 0, 1, 0) == 6
         assert bench.alg_ops(system, 0, 0, 0, 1) == 8
     # linear in every count
-    assert bench.alg_ops(W.DUBINS, 10, 63, 63, 95) == 10 * 241 + 63 * 240 + 63 * 36 + 95 * 8
+    assert bench.alg_ops(W.DUBINS, 10, 63, 63, 95) == 10 * 157 + 63 * 127 + 63 * 6 + 95 * 8
+
+
+@pytest.mark.parametrize("make,passes,grid", [(W.c1, 4, (16, 16, 16)), (W.c2, 3, (64, 64, 1)),
+                                              (W.c3, 2, (16, 16, 16))])
+def test_algorithmic_work_equals_the_oracle_replay_count(make, passes, grid):
+    """The roofline's work per unit is the oracle's: the oracle counts
+    samples, integrator steps, step hulls and broad-phase box tests as it
+    replays seeded passes (oracle/work.c), and costs each under the same
+    counting rule; the benchmark's table applied to those counts gives the
+    oracle's total exactly."""
+    from oracle.kpo import Oracle
+    w = make(3)
+    o = Oracle(w)
+    o.set_work_grid(grid)
+    o.reset()
+    for _ in range(passes):
+        o.iterate()
+    wk = o.work()
+    assert wk["samples"] > 0 and wk["steps"] >= wk["hulls"] > 0 and wk["box_grid"] > 0
+    assert o.work_costs() == {"sample": bench.OPS_PER_SAMPLE[w.system],
+                              "step": bench.OPS_PER_STEP[w.system],
+                              "hull": bench.OPS_PER_HULL, "box": bench.OPS_PER_BOX}
+    assert bench.alg_ops(w.system, wk["samples"], wk["steps"], wk["hulls"],
+                         wk["box_grid"]) == wk["ops"]
+    # the broad phase tests far fewer boxes than a scan of every box
+    assert wk["box_grid"] < wk["box_scan"]
 
 
 def _sampler(lines):

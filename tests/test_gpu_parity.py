@@ -8,7 +8,7 @@ import pytest
 from oracle import kpo
 from oracle.kpo import Oracle
 from paper_2409_06807_gb300 import workloads as W
-from parity_util import compare_pass, compare_trees, state_scale
+from parity_util import check_work, compare_pass, compare_trees, state_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +46,8 @@ def lockstep(P, w, n_iters, log_cap=None, grid=None):
     if grid:
         g.set_grid_limit(grid)
     o = Oracle(w)
+    bp = g.info()["bp_grid"]
+    o.set_work_grid(bp)
     vol = o.region_volumes()
     assert g.reset() == P.OK and o.reset() == kpo.RUNNING
     g.enable_log(log_cap or w.t_e)
@@ -53,6 +55,7 @@ def lockstep(P, w, n_iters, log_cap=None, grid=None):
     before = g.export_tree()
     i = -1
     for i in range(n_iters):
+        gi0, ow0 = g.info(), o.work()
         status, ost, orec = o.iterate(records=True)
         gstats = g.expand_step(1)
         if status == kpo.FULL:
@@ -68,9 +71,11 @@ def lockstep(P, w, n_iters, log_cap=None, grid=None):
         samples += ost["n_samples"]
         if flips == 0:
             compare_trees(w, after, ot)
+            check_work(gi0, g.info(), ow0, o.work())
             exact += 1
         else:
             o = Oracle(w)
+            o.set_work_grid(bp)
             o.import_(_as_input(after))
         before = after
         if gstats[0]["goal_node"] >= 0:
@@ -145,9 +150,11 @@ def frontier(P, w, grow, n_pass=1, all_in_ve=False, grid=None):
     if all_in_ve:
         t["in_ve"][:] = 1
     o = Oracle(w)
+    g = P.Planner(w)
+    bp = g.info()["bp_grid"]
+    o.set_work_grid(bp)
     o.import_(t)
     vol = o.region_volumes()
-    g = P.Planner(w)
     if grid:
         g.set_grid_limit(grid)
     g.import_tree(t)
@@ -159,6 +166,7 @@ def frontier(P, w, grow, n_pass=1, all_in_ve=False, grid=None):
     flips_total = 0
     before = start
     for _ in range(n_pass):
+        gi0, ow0 = g.info(), o.work()
         status, ost, orec = o.iterate(records=True)
         gs = g.expand_step(1)
         assert len(gs) == 1
@@ -169,8 +177,10 @@ def frontier(P, w, grow, n_pass=1, all_in_ve=False, grid=None):
         flips_total += flips
         if flips == 0:
             compare_trees(w, after, ot)
+            check_work(gi0, g.info(), ow0, o.work())
         else:
             o = Oracle(w)
+            o.set_work_grid(bp)
             o.import_(_as_input(after))
         before = after
         if status != kpo.RUNNING or gs[0]["goal_node"] >= 0:
