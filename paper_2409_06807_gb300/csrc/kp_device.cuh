@@ -232,24 +232,38 @@ struct System<KP_SYS_DI> {
   }
 };
 
-// The classic RK4 combination x + h/6 (k1 + 2 k2 + 2 k3 + k4) and its
-// stage points, in one fixed order.
-template <int D>
-__device__ __forceinline__ void rk4_stage(const float* x, const float* k, float a, float* t) {
-#pragma unroll
-  for (int i = 0; i < D; ++i) t[i] = __fmaf_rn(a, k[i], x[i]);
-}
-
-template <int D>
-__device__ __forceinline__ void rk4_combine(float* x, const float* k1, const float* k2,
-                                            const float* k3, const float* k4, float h6) {
+// One classic RK4 step x <- x + h/6 (k1 + 2 k2 + 2 k3 + k4), stage points
+// x + h/2 k1, x + h/2 k2, x + h k3.  The combination is accumulated as each
+// stage is evaluated, in the fixed order ((k1 + 2 k2) + 2 k3) + k4, so only
+// one stage derivative is live at a time (the register budget of the loop
+// kernel holds no four of them for the 12D system).  F(t, k) evaluates the
+// field at t into k.
+template <int D, class F>
+__device__ __forceinline__ void rk4_step(float* x, float h, F field) {
+  float acc[D], k[D], t[D];
+  const float hh = __fmul_rn(0.5f, h);
+  field(x, k);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    float s = __fmaf_rn(2.0f, k2[i], k1[i]);
-    s = __fmaf_rn(2.0f, k3[i], s);
-    s = __fadd_rn(s, k4[i]);
-    x[i] = __fmaf_rn(h6, s, x[i]);
+    acc[i] = k[i];
+    t[i] = __fmaf_rn(hh, k[i], x[i]);
   }
+  field(t, k);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    acc[i] = __fmaf_rn(2.0f, k[i], acc[i]);
+    t[i] = __fmaf_rn(hh, k[i], x[i]);
+  }
+  field(t, k);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    acc[i] = __fmaf_rn(2.0f, k[i], acc[i]);
+    t[i] = __fmaf_rn(h, k[i], x[i]);
+  }
+  field(t, k);
+  const float h6 = __fdiv_rn(h, 6.0f);
+#pragma unroll
+  for (int i = 0; i < D; ++i) x[i] = __fmaf_rn(h6, __fadd_rn(acc[i], k[i]), x[i]);
 }
 
 // 6D Dubins airplane (Chitsaz & LaValle 2007); classic RK4.
@@ -270,16 +284,7 @@ struct System<KP_SYS_DUBINS> {
   }
   __device__ __forceinline__ static void step(float* x, const float* u, float h,
                                               const KParams&) {
-    float k1[6], k2[6], k3[6], k4[6], t[6];
-    const float hh = __fmul_rn(0.5f, h);
-    f(x, u, k1);
-    rk4_stage<6>(x, k1, hh, t);
-    f(t, u, k2);
-    rk4_stage<6>(x, k2, hh, t);
-    f(t, u, k3);
-    rk4_stage<6>(x, k3, h, t);
-    f(t, u, k4);
-    rk4_combine<6>(x, k1, k2, k3, k4, __fdiv_rn(h, 6.0f));
+    rk4_step<6>(x, h, [&](const float* y, float* dy) { f(y, u, dy); });
   }
   __device__ __forceinline__ static float speed(const float* x) { return fabsf(x[5]); }
 };
@@ -327,16 +332,7 @@ struct System<KP_SYS_QUAD> {
   }
   __device__ __forceinline__ static void step(float* x, const float* u, float h,
                                               const KParams& P) {
-    float k1[12], k2[12], k3[12], k4[12], t[12];
-    const float hh = __fmul_rn(0.5f, h);
-    f(x, u, P, k1);
-    rk4_stage<12>(x, k1, hh, t);
-    f(t, u, P, k2);
-    rk4_stage<12>(x, k2, hh, t);
-    f(t, u, P, k3);
-    rk4_stage<12>(x, k3, h, t);
-    f(t, u, P, k4);
-    rk4_combine<12>(x, k1, k2, k3, k4, __fdiv_rn(h, 6.0f));
+    rk4_step<12>(x, h, [&](const float* y, float* dy) { f(y, u, P, dy); });
   }
   __device__ __forceinline__ static float speed(const float* x) {
     return sqrtf(__fmaf_rn(x[8], x[8], __fmaf_rn(x[7], x[7], __fmul_rn(x[6], x[6]))));

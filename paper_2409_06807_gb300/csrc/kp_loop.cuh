@@ -127,14 +127,6 @@ __device__ __forceinline__ void chunk_of(const Team& T, int n, int* c0, int* c1)
   *c1 = (int)(a + per < n ? a + per : n);
 }
 
-// Contiguous run [r0, r1) of this thread inside the block's chunk [c0, c1).
-__device__ __forceinline__ void thread_run(int c0, int c1, int* r0, int* r1) {
-  const int per = (c1 - c0 + (int)blockDim.x - 1) / (int)blockDim.x;
-  const long long a = (long long)c0 + (long long)threadIdx.x * per;
-  *r0 = (int)(a < c1 ? a : c1);
-  *r1 = (int)(a + per < c1 ? a + per : c1);
-}
-
 // Sum of blk[0..G) and of blk[0..blockIdx.x), by one warp (no block sync).
 __device__ __forceinline__ void warp_prefix(const Team& T, const uint32_t* blk,
                                             unsigned long long* before,
@@ -167,32 +159,56 @@ __device__ __forceinline__ void block_prefix(const Team& T, const uint32_t* blk,
   block_sum2(pre, tot, sh.red, before, total);
 }
 
-// Phase N': count V_E members of this block's node chunk (no draws).
-// Returns this thread's offset inside the block.
-__device__ __forceinline__ int count_ve(const KParams& P, const Team& T, int n, LoopShared& sh) {
-  int v0, v1, r0, r1;
-  chunk_of(T, n, &v0, &v1);
-  thread_run(v0, v1, &r0, &r1);
-  int c = 0;
-  for (int v = r0; v < r1; ++v) c += P.in_ve[v] ? 1 : 0;
-  int tot;
-  const int off = block_exclusive_scan(c, sh.scan, &tot);
-  if (threadIdx.x == 0) P.blk_b[T.b] = (uint32_t)tot;
-  return off;
+// Nodes of a block's chunk are visited in tiles of blockDim.x: node v0 +
+// tile * blockDim.x + threadIdx.x, so that a warp's loads and stores of the
+// per-node arrays are coalesced.
+
+// Block sum of one int per thread (every thread gets it).
+__device__ __forceinline__ int block_sum(int c, LoopShared& sh) {
+  unsigned long long a, dummy;
+  block_sum2((unsigned long long)c, 0, sh.red, &a, &dummy);
+  return (int)a;
 }
 
-// Phase L: write the V_E list (ascending node id) from the per-block counts
-// and this thread's offset; returns |V_E|.
-__device__ __forceinline__ int write_ve(const KParams& P, const Team& T, int n, LoopShared& sh,
-                                        int thread_off) {
-  int v0, v1, r0, r1;
+// Phase N': count V_E members of this block's node chunk (no draws) and
+// publish the count.
+__device__ __forceinline__ void count_ve(const KParams& P, const Team& T, int n, LoopShared& sh) {
+  int v0, v1;
   chunk_of(T, n, &v0, &v1);
-  thread_run(v0, v1, &r0, &r1);
+  int c = 0;
+  for (int v = v0 + (int)threadIdx.x; v < v1; v += (int)blockDim.x) c += P.in_ve[v] ? 1 : 0;
+  const int tot = block_sum(c, sh);
+  if (threadIdx.x == 0) P.blk_b[T.b] = (uint32_t)tot;
+}
+
+// Phase L: write the V_E list (ascending node id) from the per-block counts:
+// the block's offset is the sum of the counts before it; inside the chunk
+// each tile is compacted in node order (warp ballots, then the warps'
+// counts in order).  Returns |V_E|.
+__device__ __forceinline__ int write_ve(const KParams& P, const Team& T, int n, LoopShared& sh) {
+  int v0, v1;
+  chunk_of(T, n, &v0, &v1);
   unsigned long long off, total;
   block_prefix(T, P.blk_b, sh, &off, &total);
-  int pos = (int)off + thread_off;
-  for (int v = r0; v < r1; ++v)
-    if (P.in_ve[v]) P.ve[pos++] = v;
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5);
+  int base = (int)off;
+  for (int t0 = v0; t0 < v1; t0 += (int)blockDim.x) {
+    const int v = t0 + (int)threadIdx.x;
+    const bool m = v < v1 && P.in_ve[v];
+    const uint32_t bal = __ballot_sync(0xffffffffu, m);
+    if (lane == 0) sh.scan.warp[w] = __popc(bal);
+    __syncthreads();
+    int before = 0, tile = 0;
+    for (int q = 0; q < nw; ++q) {
+      const int cq = sh.scan.warp[q];
+      before += q < (int)w ? cq : 0;
+      tile += cq;
+    }
+    if (m) P.ve[base + before + __popc(bal & ((1u << lane) - 1u))] = v;
+    base += tile;
+    __syncthreads();
+  }
   return (int)total;
 }
 
@@ -832,8 +848,8 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int i
 
 // Phase N: Algorithm 4 node sets, one draw per old node (counter: it, v, 0,
 // purpose 2) against the threshold of its region; new nodes are in V_E.
-// Returns this thread's offset among the block's V_E members and, in
-// *n_new, the number of accepted samples of the pass (the new nodes).
+// Publishes the block chunk's V_E count; returns in *n_new the number of
+// accepted samples of the pass (the new nodes).
 // Order inside the phase: warp 0 of every region-chunk block first writes
 // its chunk's thresholds (phase T) and counts itself done; every block then
 // appends its own accepted samples (ids from t_old, in key order), which
@@ -841,9 +857,9 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int i
 // makes the node-set draws.  New nodes are counted as V_E members without
 // reading their sets.
 template <int SYS, bool LOG>
-__device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, uint32_t it,
-                                              int t_old, int lam, LoopShared& sh, int* n_new,
-                                              const unsigned char* sblob, double* sd) {
+__device__ __forceinline__ void phase_nodesets(const KParams& P, const Team& T, uint32_t it,
+                                               int t_old, int lam, LoopShared& sh, int* n_new,
+                                               const unsigned char* sblob, double* sd) {
   const int nch = P.nch;
   if (threadIdx.x < 32 && T.b < nch) {
     phase_thresholds(P, T, nch, sd);
@@ -871,23 +887,39 @@ __device__ __forceinline__ int phase_nodesets(const KParams& P, const Team& T, u
     __threadfence();
   }
   __syncthreads();
-  int v0, v1, r0, r1;
+  int v0, v1;
   chunk_of(T, t_new, &v0, &v1);
-  thread_run(v0, v1, &r0, &r1);
+  // old nodes of the chunk: four tiles at a time, their region and
+  // threshold loads issued together
+  const int o1 = v1 < t_old ? v1 : t_old;
+  const int stride = (int)blockDim.x;
   int c = 0;
-  for (int v = r0; v < r1; ++v) {
-    int e = 1;
-    if (v < t_old) {
-      const uint4 w = philox4x32_10(make_uint4(it, (uint32_t)v, 0u, 2u), P.seed_lo, P.seed_hi);
-      e = (uint64_t)w.x < P.thr[P.region[v]] ? 1 : 0;
-      P.in_ve[v] = (uint8_t)e;
+  for (int t0 = v0; t0 < o1; t0 += 4 * stride) {
+    int vq[4], rq[4];
+    uint64_t tq[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      vq[q] = t0 + q * stride + (int)threadIdx.x;
+      rq[q] = vq[q] < o1 ? __ldcg(P.region + vq[q]) : 0;
     }
-    c += e;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tq[q] = vq[q] < o1 ? __ldcg(P.thr + rq[q]) : 0ull;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (vq[q] < o1) {
+        const uint4 w =
+            philox4x32_10(make_uint4(it, (uint32_t)vq[q], 0u, 2u), P.seed_lo, P.seed_hi);
+        const int e = (uint64_t)w.x < tq[q] ? 1 : 0;
+        P.in_ve[vq[q]] = (uint8_t)e;
+        c += e;
+      }
+    }
   }
-  int tot;
-  const int off = block_exclusive_scan(c, sh.scan, &tot);
+  // new nodes are V_E members (their flags are set by the blocks that
+  // appended them, so they are counted, not read)
+  const int new0 = v0 > t_old ? v0 : t_old;
+  const int tot = block_sum(c, sh) + (v1 > new0 ? v1 - new0 : 0);
   if (threadIdx.x == 0) P.blk_b[T.b] = (uint32_t)tot;
-  return off;
 }
 
 // The loop of one query (Algorithm 1 body, repeated) run by a team of
@@ -918,9 +950,9 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
   const int nch = P.nch;
 
   // V_E list from the stored node sets
-  int ve_off = count_ve(P, T, n_tree, sh);
+  count_ve(P, T, n_tree, sh);
   if (!team_sync(T, ctl, P.wait_ns, 10)) return false;
-  int n_ve = write_ve(P, T, n_tree, sh, ve_off);
+  int n_ve = write_ve(P, T, n_tree, sh);
   if (!team_sync(T, ctl, P.wait_ns, 11)) return false;
   int lam = eq6_lambda(P.t_e, n_tree, n_ve, P.lambda_max);
   if (n_ve > 0 && lam == 0) {
@@ -966,13 +998,13 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
     if (timer) phase_ns[5] = phase_ns[7] = 0;
     const int t_old = n_tree;
     int n_acc;
-    ve_off = phase_nodesets<SYS, LOG>(P, T, it, t_old, lam, sh, &n_acc, smem, sd);
+    phase_nodesets<SYS, LOG>(P, T, it, t_old, lam, sh, &n_acc, smem, sd);
     n_tree = t_old + n_acc;
     stamp(8);
     if (!team_sync(T, ctl, P.wait_ns, 23)) return false;
     stamp(9);
     const int ve_prev = n_ve, lam_prev = lam;
-    n_ve = write_ve(P, T, n_tree, sh, ve_off);
+    n_ve = write_ve(P, T, n_tree, sh);
     lam = eq6_lambda(P.t_e, n_tree, n_ve, P.lambda_max);
     ++run;
     if (T.b == 0 && threadIdx.x == 0) {
