@@ -52,6 +52,7 @@ struct kpo {
   int32_t wgrid[3];
   int32_t *wbox;           /* [nb][6] cell range of each box in that grid,
                               NULL until a work grid is set                */
+  int32_t *wclear;         /* [cells] clearance of each cell, sixteenths   */
 
   /* learned proposal */
   double *mlp;           /* parameter vector, NULL when off */

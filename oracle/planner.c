@@ -115,7 +115,7 @@ void kpo_destroy(kpo *o) {
   free(o->n_invalid); free(o->cov); free(o->avail); free(o->visited);
   free(o->score); free(o->p_accept); free(o->thr); free(o->mlp);
   free(o->kd_axis); free(o->kd_right); free(o->kd_leaf); free(o->kd_split);
-  free(o->leaf_lo); free(o->leaf_hi); free(o->region_vol); free(o->wbox);
+  free(o->leaf_lo); free(o->leaf_hi); free(o->region_vol); free(o->wbox); free(o->wclear);
   free(o);
 }
 

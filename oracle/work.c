@@ -32,7 +32,12 @@
  * checker), and the same over the boxes listed in the uniform-grid cells
  * the hull overlaps, visited cell by cell (z slowest, then y, then x) with
  * each cell's boxes in index order, stopping at the first box met (the
- * broad phase; the grid shape is an input).
+ * broad phase; the grid shape is an input).  The broad phase first looks up
+ * the clearance of the cell holding the hull's low corner: the smallest, over
+ * boxes, of the largest per-axis gap between the cell and the box in that
+ * axis's cell units, at most 4 cells, less 1e-3, counted in whole sixteenths
+ * of a cell; a hull inside the cell grown by that much on every side is
+ * tested against no box.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -128,11 +133,23 @@ void kpo_step_work(kpo *o, const double *x0, const double *x1) {
     o->work.box_scan += 1;
     if (box_meets(o->boxes + 6 * (size_t)b, lo, hi)) break;
   }
-  /* the boxes of the grid cells the hull overlaps */
+  /* the boxes of the grid cells the hull overlaps, unless the hull lies in
+   * its low corner's cell grown by the cell's clearance */
   int c0[3], c1[3];
   for (int a = 0; a < 3; ++a) {
     c0[a] = wcell(o, a, lo[a]);
     c1[a] = wcell(o, a, hi[a]);
+  }
+  {
+    const double r =
+        o->wclear[c0[0] + o->wgrid[0] * (c0[1] + o->wgrid[1] * c0[2])] / 16.0;
+    int inside = r > 0.0;
+    for (int a = 0; a < 3 && inside; ++a) {
+      const double s = (double)o->wgrid[a] / (o->cfg.ws_hi[a] - o->cfg.ws_lo[a]);
+      const double tl = (lo[a] - o->cfg.ws_lo[a]) * s, th = (hi[a] - o->cfg.ws_lo[a]) * s;
+      if (!(tl >= c0[a] - r && th <= c0[a] + 1 + r)) inside = 0;
+    }
+    if (inside) return;
   }
   uint64_t n = 0;
   int hit = 0;
@@ -168,6 +185,28 @@ void kpo_set_work_grid(kpo *o, const int32_t g[3]) {
       o->wbox[6 * (size_t)b + a] = wcell(o, a, o->boxes[6 * (size_t)b + a]);
       o->wbox[6 * (size_t)b + 3 + a] = wcell(o, a, o->boxes[6 * (size_t)b + 3 + a]);
     }
+  /* each cell's clearance: the L-infinity gap (per axis in cell units) to
+   * the nearest box, at most 4 cells, less 1e-3, in whole sixteenths */
+  const int C = o->wgrid[0] * o->wgrid[1] * o->wgrid[2];
+  free(o->wclear);
+  o->wclear = (int32_t *)malloc(sizeof(int32_t) * (size_t)C);
+  for (int c = 0; c < C; ++c) {
+    const int cc[3] = {c % o->wgrid[0], (c / o->wgrid[0]) % o->wgrid[1],
+                       c / (o->wgrid[0] * o->wgrid[1])};
+    double r = 4.0;
+    for (int b = 0; b < o->nb; ++b) {
+      double gap = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double s = (double)o->wgrid[a] / (o->cfg.ws_hi[a] - o->cfg.ws_lo[a]);
+        const double bl = (o->boxes[6 * (size_t)b + a] - o->cfg.ws_lo[a]) * s;
+        const double bh = (o->boxes[6 * (size_t)b + 3 + a] - o->cfg.ws_lo[a]) * s;
+        gap = fmax(gap, fmax(bl - (cc[a] + 1), cc[a] - bh));
+      }
+      r = fmin(r, gap);
+    }
+    const double v = (r - 1e-3) * 16.0;
+    o->wclear[c] = v >= 1.0 ? (int32_t)fmin(255.0, floor(v)) : 0;
+  }
 }
 
 void kpo_get_work(const kpo *o, kpo_work *out) { *out = o->work; }

@@ -424,8 +424,15 @@ long long bp_ranges(const float* fb, int nb, const kp_workspace& ws, const int g
 // useless to the grid and the flat shapes win; boxes of every orientation
 // keep the cube.  If no shape fits, the finest of 8^3, 4^3, 2^3 and 1 cell
 // (every box) that fits is used.
+//
+// With 'clearance', a byte per cell follows: the cell's clearance, the
+// smallest over boxes of the largest per-axis gap between the cell and the
+// box, in that axis's cell units (an L-infinity distance), capped at
+// KP_BP_CLEAR_CAP cells, less KP_BP_CLEAR_MARGIN, in sixteenths of a cell
+// rounded down.  A hull inside its cell grown by that much on every side is
+// separated from every box along some axis, so it meets none.
 size_t build_blob(unsigned char* blob, const float* boxes, int nb, const kp_workspace& ws,
-                  KParams& P, size_t max_bytes = KP_BLOB_BYTES) {
+                  KParams& P, size_t max_bytes = KP_BLOB_BYTES, bool clearance = true) {
   const int pad = (nb + 7) / 8 * 8;
   float* fb = reinterpret_cast<float*>(blob);
   for (int b = 0; b < pad; ++b) {
@@ -504,7 +511,45 @@ size_t build_blob(unsigned char* blob, const float* boxes, int nb, const kp_work
       for (int y = lo3[(size_t)b * 3 + 1]; y <= hi3[(size_t)b * 3 + 1]; ++y)
         for (int x = lo3[(size_t)b * 3]; x <= hi3[(size_t)b * 3]; ++x)
           ids[cursor[cell(x, y, z)]++] = (uint16_t)b;
-  const size_t bytes = ids_off + round16((size_t)start[C] * 2);
+  size_t bytes = ids_off + round16((size_t)start[C] * 2);
+  P.bp_clear_off = -1;
+  if (clearance && bytes + round16((size_t)C) <= max_bytes) {
+    // every box lowers the clearance of the cells within the cap of it
+    std::vector<double> rc((size_t)C, (double)KP_BP_CLEAR_CAP);
+    double sc[3];
+    for (int a = 0; a < 3; ++a) sc[a] = (double)g[a] / ((double)ws.hi[a] - (double)ws.lo[a]);
+    for (int b = 0; b < nb; ++b) {
+      double bl[3], bh[3];
+      int c0[3], c1[3];
+      for (int a = 0; a < 3; ++a) {
+        bl[a] = ((double)fb[b * 8 + a] - (double)ws.lo[a]) * sc[a];
+        bh[a] = ((double)fb[b * 8 + 4 + a] - (double)ws.lo[a]) * sc[a];
+        const double f0 = std::floor(bl[a]) - KP_BP_CLEAR_CAP, f1 = std::floor(bh[a]) + KP_BP_CLEAR_CAP;
+        c0[a] = f0 < 0.0 ? 0 : (f0 > g[a] - 1 ? g[a] - 1 : (int)f0);
+        c1[a] = f1 < 0.0 ? 0 : (f1 > g[a] - 1 ? g[a] - 1 : (int)f1);
+      }
+      for (int z = c0[2]; z <= c1[2]; ++z)
+        for (int y = c0[1]; y <= c1[1]; ++y)
+          for (int x = c0[0]; x <= c1[0]; ++x) {
+            const int cc[3] = {x, y, z};
+            double gap = 0.0;
+            for (int a = 0; a < 3; ++a) {
+              const double ga = std::max(bl[a] - (double)(cc[a] + 1), (double)cc[a] - bh[a]);
+              gap = std::max(gap, ga);
+            }
+            double& r = rc[(size_t)cell(x, y, z)];
+            r = std::min(r, gap);
+          }
+    }
+    unsigned char* q = blob + bytes;
+    for (int c = 0; c < C; ++c) {
+      const double v = (rc[c] - KP_BP_CLEAR_MARGIN) * 16.0;
+      q[c] = v >= 1.0 ? (unsigned char)std::min(255.0, std::floor(v)) : 0;
+    }
+    std::memset(q + C, 0, round16((size_t)C) - (size_t)C);
+    P.bp_clear_off = (int32_t)bytes;
+    bytes += round16((size_t)C);
+  }
   P.n_boxes_pad = pad;
   P.blob_bytes = (int32_t)bytes;
   for (int a = 0; a < 3; ++a) {
@@ -825,6 +870,7 @@ void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* 
   P.vol = vol;
   P.fso = d.fso;
   P.kd_smem_off = -1;
+  P.bp_clear_off = -1;
   if (d.fso) {
     P.kd_node = reinterpret_cast<const int32_t*>(A + lay.kd_node);
     P.kd_split = reinterpret_cast<const float*>(A + lay.kd_split);
@@ -1313,6 +1359,7 @@ kp_status kp_grow(kp_ctx* ctx, void* dev_arena, size_t arena_bytes, int32_t t_e)
   for (int a = 0; a < 3; ++a) P.bp_g[a] = old.bp_g[a];
   P.bp_start_off = old.bp_start_off;
   P.bp_ids_off = old.bp_ids_off;
+  P.bp_clear_off = old.bp_clear_off;
   for (int a = 0; a < 3; ++a) P.bp_scale[a] = old.bp_scale[a];
   P.nch = old.nch;
   P.sd_bytes = old.sd_bytes;
@@ -1892,8 +1939,9 @@ bool try_admit(kp_server* s, PendingQuery& q) {
   const int nch = region_chunks(s->team_blocks, d.R_pad);
   P.nch = nch;
   P.sd_bytes = KS_SD_DOUBLES * 8;
+  // no cell clearances: the host would spend milliseconds per query on them
   const size_t blob_bytes = build_blob(s->blob.data(), q.boxes.empty() ? nullptr : q.boxes.data(),
-                                       (int)(q.boxes.size() / 6), q.ws, P, KS_BLOB_MAX);
+                                       (int)(q.boxes.size() / 6), q.ws, P, KS_BLOB_MAX, false);
   if (blob_bytes > (size_t)KS_BLOB_MAX || d.R_pad / nch > KS_SD_DOUBLES) {
     pool_free(s, off, lay.total);
     finish_now(s, q.id, KP_ERR_ARG, q.t_submit);

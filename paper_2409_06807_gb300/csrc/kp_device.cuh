@@ -474,37 +474,45 @@ __device__ __forceinline__ bool box_meets_hull(float4 bl, float4 bh, float lx, f
   return (int32_t)s >= 0;
 }
 
-// Broad-phase cell of a coordinate (same FP32 arithmetic as the host build).
-__device__ __forceinline__ int bp_cell(float v, float lo, float scale, int g) {
-  const float t = __fmul_rn(__fsub_rn(v, lo), scale);
+// Broad-phase cell of a coordinate already in cell units (the host build
+// uses the same FP32 arithmetic): clamped to [0, g - 1].
+__device__ __forceinline__ int bp_cell_of(float t, int g) {
   return t >= 0.0f ? (t < (float)g ? (int)t : g - 1) : 0;
 }
 
 // Exact coarse-then-fine collision test of a step hull (the paper's coarse
-// phase, Sec. III-B): only boxes listed in the uniform-grid cells the hull
-// touches are tested.  A box meeting the hull shares a point with it; that
-// point's cell lies in both cell ranges (the cell map is monotone), so the
-// box is in one of the visited lists: the verdict equals testing every box.
-// 'tests' counts the box tests made.
+// phase, Sec. III-B).  First the clearance of the cell holding the hull's
+// low corner: a hull inside that cell grown by its clearance on every side
+// meets no box (the clearance is a lower bound on the L-infinity gap, per
+// axis in cell units, from the cell to every box; the host subtracts a
+// margin far above the FP32 rounding of the cell coordinates).  Otherwise
+// only the boxes listed in the uniform-grid cells the hull touches are
+// tested: a box meeting the hull shares a point with it, that point's cell
+// lies in both cell ranges (the cell map is monotone), so the box is in
+// one of the visited lists.  Either way the verdict equals testing every
+// box.  'tests' counts the box tests made.
 __device__ __forceinline__ bool hull_hits_grid(const KParams& P, const float4* __restrict__ sbox,
                                                const uint16_t* __restrict__ sstart,
-                                               const uint16_t* __restrict__ sids, float lx,
+                                               const uint16_t* __restrict__ sids,
+                                               const uint8_t* __restrict__ sclear, float lx,
                                                float ly, float lz, float hx, float hy, float hz,
                                                uint32_t* tests) {
   const int gx = P.bp_g[0], gy = P.bp_g[1], gz = P.bp_g[2];
-  // an axis of one cell maps every coordinate to cell 0: skip its lookup
-  int x0 = 0, x1 = 0, y0 = 0, y1 = 0, z0 = 0, z1 = 0;
-  if (gx > 1) {
-    x0 = bp_cell(lx, P.ws_lo[0], P.bp_scale[0], gx);
-    x1 = bp_cell(hx, P.ws_lo[0], P.bp_scale[0], gx);
-  }
-  if (gy > 1) {
-    y0 = bp_cell(ly, P.ws_lo[1], P.bp_scale[1], gy);
-    y1 = bp_cell(hy, P.ws_lo[1], P.bp_scale[1], gy);
-  }
-  if (gz > 1) {
-    z0 = bp_cell(lz, P.ws_lo[2], P.bp_scale[2], gz);
-    z1 = bp_cell(hz, P.ws_lo[2], P.bp_scale[2], gz);
+  const float tlx = __fmul_rn(__fsub_rn(lx, P.ws_lo[0]), P.bp_scale[0]);
+  const float thx = __fmul_rn(__fsub_rn(hx, P.ws_lo[0]), P.bp_scale[0]);
+  const float tly = __fmul_rn(__fsub_rn(ly, P.ws_lo[1]), P.bp_scale[1]);
+  const float thy = __fmul_rn(__fsub_rn(hy, P.ws_lo[1]), P.bp_scale[1]);
+  const float tlz = __fmul_rn(__fsub_rn(lz, P.ws_lo[2]), P.bp_scale[2]);
+  const float thz = __fmul_rn(__fsub_rn(hz, P.ws_lo[2]), P.bp_scale[2]);
+  const int x0 = bp_cell_of(tlx, gx), x1 = bp_cell_of(thx, gx);
+  const int y0 = bp_cell_of(tly, gy), y1 = bp_cell_of(thy, gy);
+  const int z0 = bp_cell_of(tlz, gz), z1 = bp_cell_of(thz, gz);
+  if (sclear != nullptr) {
+    const float r = (float)sclear[x0 + gx * (y0 + gy * z0)] * 0.0625f;
+    const float fx = (float)x0, fy = (float)y0, fz = (float)z0;
+    if (r > 0.0f && tlx >= fx - r && thx <= fx + 1.0f + r && tly >= fy - r &&
+        thy <= fy + 1.0f + r && tlz >= fz - r && thz <= fz + 1.0f + r)
+      return false;
   }
   uint32_t n = 0;
   bool hit = false;

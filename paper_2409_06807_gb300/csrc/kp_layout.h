@@ -33,7 +33,12 @@ constexpr int KP_TRAJ_ROWS = 16384;    // longest root-to-goal chain returned
 constexpr int KP_BP_MAX_G = 16;        // finest broad-phase grid per axis
 constexpr int KP_BP_MAX_IDS = 32768;   // broad-phase (cell, box) entries
 constexpr int KP_BLOB_BYTES = 4096 * 32 + (KP_BP_MAX_G * KP_BP_MAX_G * KP_BP_MAX_G + 4) * 4 +
-                              KP_BP_MAX_IDS * 2;  // arena room for the obstacle blob
+                              KP_BP_MAX_IDS * 2 +
+                              KP_BP_MAX_G * KP_BP_MAX_G * KP_BP_MAX_G;  // arena room for the obstacle blob
+// per-cell clearance of the broad-phase grid: stored in 1/16 of a cell,
+// computed up to KP_BP_CLEAR_CAP cells, less a margin for FP32 rounding
+constexpr int KP_BP_CLEAR_CAP = 4;
+constexpr double KP_BP_CLEAR_MARGIN = 1e-3;
 constexpr int KP_FSO_MAX_LEAVES = 16384; // regions of a kd-tree decomposition
 // floats per kept end state (one aligned row of whole 32-byte sectors per key)
 __host__ __device__ constexpr int kp_xs_stride(int D) { return D <= 8 ? 8 : 16; }
@@ -153,7 +158,9 @@ struct KParams {
   uint32_t seed_lo, seed_hi;
   // obstacles: a blob staged whole into shared memory:
   //   [n_boxes_pad][8] floats (lo.xyz, pad, hi.xyz, pad), then the
-  //   broad-phase grid: uint16 cell_start[bp_g[0] bp_g[1] bp_g[2] + 1], uint16 ids[...]
+  //   broad-phase grid: uint16 cell_start[bp_g[0] bp_g[1] bp_g[2] + 1], uint16 ids[...],
+  //   then (optionally) uint8 clearance[cells]: q / 16 cells of free space
+  //   around the cell in every axis (L-infinity, in each axis's cell units)
   const float* boxes;
   int32_t n_boxes_pad;
   int32_t blob_bytes;
@@ -161,6 +168,7 @@ struct KParams {
   int32_t bp_g[3];       // broad-phase cells along x, y, z (1 1 1: every box in one cell)
   int32_t bp_start_off;  // byte offsets inside the blob
   int32_t bp_ids_off;
+  int32_t bp_clear_off;  // the cells' clearances (uint8), -1: none
   float bp_scale[3];     // cells per unit length, per axis
   // tree, SoA over t_e nodes
   float* st;          // [D][t_e]

@@ -402,6 +402,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
   const float4* sbox = reinterpret_cast<const float4*>(sblob);
   const uint16_t* sstart = reinterpret_cast<const uint16_t*>(sblob + P.bp_start_off);
   const uint16_t* sids = reinterpret_cast<const uint16_t*>(sblob + P.bp_ids_off);
+  const uint8_t* sclear = P.bp_clear_off >= 0 ? sblob + P.bp_clear_off : nullptr;
   const uint32_t FULL = 0xffffffffu;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt = (1u << lane) - 1u;
@@ -563,7 +564,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
       if (ok) {
         ++n_hull;
         // hull of the step; + 0.0f turns a -0 into +0 for the box test
-        ok = !hull_hits_grid(P, sbox, sstart, sids, fminf(px, x[0]) + 0.0f,
+        ok = !hull_hits_grid(P, sbox, sstart, sids, sclear, fminf(px, x[0]) + 0.0f,
                              fminf(py, x[1]) + 0.0f, fminf(pz, x[2]) + 0.0f,
                              fmaxf(px, x[0]) + 0.0f, fmaxf(py, x[1]) + 0.0f,
                              fmaxf(pz, x[2]) + 0.0f, &n_box);
