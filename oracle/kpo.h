@@ -187,6 +187,9 @@ void kpo_box_muller(const uint32_t w[4], double z[4]);
  * along position axis a over W (default 1 x 1 x 1: every box in one cell). */
 void kpo_set_work_grid(kpo *o, const int32_t g[3]);
 void kpo_get_work(const kpo *o, kpo_work *out);
+/* The work grid's cell clearances in sixteenths of a cell (cells in index
+ * order, x fastest); returns the cell count (0 before kpo_set_work_grid). */
+int32_t kpo_work_clearance(const kpo *o, int32_t *out);
 void kpo_clear_work(kpo *o);
 /* Lane operations per unit: sample, integrator step, hull, box test. */
 uint64_t kpo_work_ops_sample(const kpo *o);

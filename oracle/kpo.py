@@ -108,6 +108,8 @@ def lib():
         L.kpo_set_work_grid.argtypes = [vp, _i32p]
         L.kpo_get_work.argtypes = [vp, C.POINTER(Work)]
         L.kpo_clear_work.argtypes = [vp]
+        L.kpo_work_clearance.restype = C.c_int32
+        L.kpo_work_clearance.argtypes = [vp, _i32p]
         for name in ("kpo_work_ops_sample", "kpo_work_ops_step"):
             getattr(L, name).restype = C.c_uint64
             getattr(L, name).argtypes = [vp]
@@ -449,6 +451,12 @@ class Oracle:
         wk = Work()
         lib().kpo_get_work(self._h, C.byref(wk))
         return {n: int(getattr(wk, n)) for n, _ in Work._fields_}
+
+    def work_clearance(self) -> np.ndarray:
+        """Cell clearances (sixteenths of a cell) of the work grid."""
+        out = np.zeros(4096 * 16, np.int32)
+        n = lib().kpo_work_clearance(self._h, out)
+        return out[:n]
 
     def clear_work(self):
         lib().kpo_clear_work(self._h)

@@ -212,3 +212,10 @@ void kpo_set_work_grid(kpo *o, const int32_t g[3]) {
 void kpo_get_work(const kpo *o, kpo_work *out) { *out = o->work; }
 
 void kpo_clear_work(kpo *o) { memset(&o->work, 0, sizeof o->work); }
+
+int32_t kpo_work_clearance(const kpo *o, int32_t *out) {
+  const int C = o->wgrid[0] * o->wgrid[1] * o->wgrid[2];
+  if (!o->wclear) return 0;
+  memcpy(out, o->wclear, sizeof(int32_t) * (size_t)C);
+  return C;
+}

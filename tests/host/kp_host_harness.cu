@@ -60,9 +60,11 @@ extern "C" {
 // Builds the obstacle blob of nb boxes (host rows lo xyz, hi xyz) for the
 // workspace [lo, hi] into 'blob' (room for max_bytes).  Writes the grid's
 // cells per axis, its scale (cells per unit length), the byte offsets of
-// the cell starts and of the box ids, and returns the blob's size.
+// the cell starts and of the box ids, of the cells' clearances (-1 without),
+// and returns the blob's size.
 int kpt_blob(const float* boxes, int nb, const float* lo, const float* hi, int max_bytes,
-             unsigned char* blob, int* g3, float* scale3, int* start_off, int* ids_off) {
+             unsigned char* blob, int* g3, float* scale3, int* start_off, int* ids_off,
+             int* clear_off) {
   const kp_workspace ws = unit_workspace(lo, hi, nullptr);
   KParams P{};
   const size_t bytes = build_blob(blob, nb > 0 ? boxes : nullptr, nb, ws, P, (size_t)max_bytes);
@@ -72,8 +74,12 @@ int kpt_blob(const float* boxes, int nb, const float* lo, const float* hi, int m
   }
   *start_off = P.bp_start_off;
   *ids_off = P.bp_ids_off;
+  *clear_off = P.bp_clear_off;
   return (int)bytes;
 }
+
+// The arena's room for the obstacle blob (KP_BLOB_BYTES).
+int kpt_blob_bytes(void) { return KP_BLOB_BYTES; }
 
 // Builds the kd-tree over the boxes' faces; writes each leaf's box (lo xyz,
 // hi xyz) in depth-first order, up to 'cap' leaves.  Returns the leaf

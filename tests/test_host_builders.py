@@ -24,7 +24,6 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "tests", "host", "kp_host_harness.cu")
 OUT = os.path.join(ROOT, "tests", "host", "_build", "libkphost.so")
 CSRC = os.path.join(ROOT, "paper_2409_06807_gb300", "csrc")
-BLOB_BYTES = 1 << 20
 LO, HI = np.zeros(3, np.float32), np.ones(3, np.float32)
 
 
@@ -54,7 +53,9 @@ def H():
     i32 = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
     L.kpt_blob.restype = C.c_int
     L.kpt_blob.argtypes = [f32, C.c_int, f32, f32, C.c_int, u8, i32, f32,
-                           C.POINTER(C.c_int), C.POINTER(C.c_int)]
+                           C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.kpt_blob_bytes.restype = C.c_int
+    L.kpt_blob_bytes.argtypes = []
     L.kpt_kd_leaves.restype = C.c_int
     L.kpt_kd_leaves.argtypes = [f32, C.c_int, f32, f32, f32, C.c_int]
     u64 = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
@@ -69,18 +70,21 @@ def H():
     return L
 
 
-def blob(H, boxes, max_bytes=BLOB_BYTES):
+def blob(H, boxes, max_bytes=None):
+    if max_bytes is None:
+        max_bytes = H.kpt_blob_bytes()  # the arena's room for the blob
     boxes = np.ascontiguousarray(boxes, np.float32).reshape(-1, 6)
     buf = np.zeros(max(max_bytes, 16), np.uint8)
     g = np.zeros(3, np.int32)
     scale = np.zeros(3, np.float32)
-    so, io = C.c_int(), C.c_int()
+    so, io, co = C.c_int(), C.c_int(), C.c_int()
     n = H.kpt_blob(boxes if len(boxes) else np.zeros((1, 6), np.float32), len(boxes), LO, HI,
-                   max_bytes, buf, g, scale, C.byref(so), C.byref(io))
+                   max_bytes, buf, g, scale, C.byref(so), C.byref(io), C.byref(co))
     C_ = int(np.prod(g))
     start = buf[so.value:so.value + 2 * (C_ + 1)].view(np.uint16).astype(np.int64)
     ids = buf[io.value:io.value + 2 * int(start[-1])].view(np.uint16).astype(np.int64)
-    return dict(bytes=n, g=g.tolist(), scale=scale, start=start, ids=ids)
+    clear = buf[co.value:co.value + C_].copy() if co.value >= 0 else None
+    return dict(bytes=n, g=g.tolist(), scale=scale, start=start, ids=ids, clear=clear)
 
 
 def cell(v, a, bp):
@@ -141,12 +145,12 @@ def test_grid_shape_follows_the_obstacles(H):
                                   "most boxes"])
 def test_cell_lists_give_the_verdict_of_every_box(H, name):
     """Every box meeting a hull is listed in a cell the hull touches; the
-    blob fits the arena's room for it (213,008 bytes) even at the box
+    blob fits the arena's room for it (KP_BLOB_BYTES) even at the box
     capacity of 4,096."""
     boxes = layouts()[name]
     bp = blob(H, boxes)
     n = len(boxes)
-    assert bp["bytes"] <= 4096 * 32 + (4096 + 4) * 4 + 32768 * 2
+    assert bp["bytes"] <= H.kpt_blob_bytes()
     assert np.all(np.diff(bp["start"]) >= 0) and np.all(bp["ids"] < n)
     # each box is listed once in every cell of its range, nowhere else
     want = sum(np.prod([int(cell(b[3 + a], a, bp)) - int(cell(b[a], a, bp)) + 1 for a in range(3)])
@@ -157,6 +161,51 @@ def test_cell_lists_give_the_verdict_of_every_box(H, name):
         for h in hulls(rng, 400, size):
             meets = np.flatnonzero(np.all(boxes[:, :3] <= h[3:], 1) & np.all(h[:3] <= boxes[:, 3:], 1))
             assert set(meets.tolist()) <= listed(bp, h)
+
+
+def clear_by_cell(bp, h):
+    """The device's clearance test of hull h in float32: inside the cell of
+    its low corner grown by that cell's clearance on every side."""
+    t = [(np.float32(np.float32(h[a]) - LO[a]) * bp["scale"][a],
+          np.float32(np.float32(h[3 + a]) - LO[a]) * bp["scale"][a]) for a in range(3)]
+    c0 = [int(cell(h[a], a, bp)) for a in range(3)]
+    gx, gy, _ = bp["g"]
+    r = np.float32(bp["clear"][c0[0] + gx * (c0[1] + gy * c0[2])]) * np.float32(0.0625)
+    return bool(r > 0 and all(t[a][0] >= np.float32(c0[a]) - r and
+                              t[a][1] <= np.float32(c0[a]) + np.float32(1.0) + r for a in range(3)))
+
+
+@pytest.mark.parametrize("name", ["forest", "building", "random", "forest along y", "large boxes"])
+def test_cell_clearance_never_hides_a_box(H, name):
+    """A hull that the cell clearance declares free meets no box (every box
+    tested, closed sets), on hulls scattered over the workspace and on hulls
+    that graze the boxes' faces; and the clearance does declare most hulls
+    away from the obstacles free.  The clearances equal the ones the
+    oracle's work count computes from the same rule in its own code."""
+    boxes = layouts()[name]
+    bp = blob(H, boxes)
+    assert bp["clear"] is not None
+    rng = np.random.default_rng(13)
+    free = tested = 0
+    grazing = []
+    for b in boxes[rng.integers(0, len(boxes), 300)]:
+        a = int(rng.integers(0, 3))
+        side = int(rng.integers(0, 2))
+        p = rng.uniform(b[:3], b[3:]).astype(np.float32)
+        p[a] = b[3 * side + a] + np.float32((2 * side - 1) * rng.uniform(0.0, 0.02))
+        d = rng.uniform(-0.004, 0.004, 3).astype(np.float32)
+        grazing.append(np.concatenate([np.minimum(p, p + d), np.maximum(p, p + d)]))
+    for h in list(hulls(rng, 3000, 0.006)) + grazing:
+        if clear_by_cell(bp, h):
+            free += 1
+            meets = np.all(boxes[:, :3] <= h[3:], 1) & np.all(h[:3] <= boxes[:, 3:], 1)
+            assert not meets.any(), (h, np.flatnonzero(meets)[:3])
+        tested += 1
+    if name != "large boxes":
+        assert free > 0.3 * tested, (free, tested)
+    o = Oracle(W.tiny(W.DI, seed=0, n_boxes=0).with_(boxes=np.ascontiguousarray(boxes)))
+    o.set_work_grid(bp["g"])
+    np.testing.assert_array_equal(o.work_clearance(), bp["clear"].astype(np.int32))
 
 
 def test_grid_respects_the_byte_budget(H):
