@@ -341,6 +341,22 @@ kp_status kp_set_wait_limit(kp_ctx *ctx, uint64_t ns);
  * the previous shape is kept). */
 kp_status kp_set_grid_limit(kp_ctx *ctx, int32_t max_blocks);
 
+/* Bounds-checked build (no counterpart in the paper: a testing aid).  The
+ * library compiled with KP_CHECK defined (paper_2409_06807_gb300/build.py,
+ * check=True) checks every array index the loop kernel derives (node ids,
+ * sample keys, regions, sub-regions, V_E positions, accepted-sample slots,
+ * block slots, broad-phase cells, box lists and box ids) against its
+ * array: an index out of range records the site, is replaced by 0 so that
+ * no access leaves its array (nothing traps), and the launch stops at its
+ * next barrier; the call then returns KP_ERR_CUDA with the site in
+ * kp_last_error and the context is poisoned.  kp_bounds_checked returns 1
+ * in that build, 0 otherwise.  kp_selftest_bounds looks up an index one
+ * past the tree through the checked path and returns what the launch
+ * reports (KP_ERR_CUDA, site 97, in the checked build); in the normal build
+ * it launches nothing and returns KP_ERR_STATE. */
+int32_t kp_bounds_checked(void);
+kp_status kp_selftest_bounds(kp_ctx *ctx);
+
 /* Test hook for the bounded-wait path: one block waits on a device flag
  * that nothing ever sets, for at most the context's wait limit, then
  * reports.  Returns KP_ERR_TIMEOUT (and poisons the context) when the wait
@@ -362,14 +378,22 @@ kp_status kp_selftest_wait_timeout(kp_ctx *ctx);
  *  - Size limit: problems whose arena (kp_required_bytes) exceeds
  *    KP_STATIC_SCRATCH_BYTES return KP_ERR_OOM without touching the device.
  *  - Set-up: the first call on a device looks up the scratch's device
- *    address (once per device, with that device current); make that first
- *    call before any stream capture.
+ *    address (once per device, with that device current).
  *  - Sharing: all calls on a device share the scratch, which keeps the last
  *    call's contents; every call clears what must start at zero.  Calls
  *    whose GPU work overlaps (other streams or host threads) race on the
  *    scratch and must be serialised by the caller.
+ *  - Obstacles: the call builds the broad-phase grid of the step-hull test
+ *    on the device in the scratch (the finest cube of 16^3, 8^3, 4^3, 2^3
+ *    or 1 cell whose box lists fit), with the cells' clearances; verdicts
+ *    equal testing every box, as in kp_plan.
  *  - Work is enqueued on cuda_stream (NULL = legacy default stream) and the
- *    call waits for it.  Returns as kp_plan; error codes carry no message. */
+ *    call blocks until it is done (it synchronises that stream and copies
+ *    to pageable host memory), so it must not be called while that stream
+ *    is being captured.  Returns as kp_plan (a replay mismatch of the
+ *    sample log cannot occur here: the log is off); error codes carry no
+ *    message; KP_ERR_ARG also when no block of the loop kernel can be
+ *    resident with this problem's shared memory. */
 #define KP_STATIC_SCRATCH_BYTES (16u << 20)
 kp_status kp_plan_static(const kp_system *sys, const kp_workspace *ws,
                          const kp_obstacles *obs, const kp_params *prm,

@@ -33,15 +33,18 @@ def _deps():
     return out
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+LIB_CHECK = os.path.join(HERE, "libkinopax_check.so")
+
+
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def _compile(unit: str, extra) -> str:
-    obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+def _compile(unit: str, extra, build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, unit.replace(".cu", ".o"))
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, unit), "-o", obj,
            *extra]
@@ -51,21 +54,27 @@ def _compile(unit: str, extra) -> str:
     return obj
 
 
-def build_planner(force: bool = False, verbose_ptxas: bool = False) -> str:
-    """Compile the planner library if any source changed; returns its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build_planner(force: bool = False, verbose_ptxas: bool = False, check: bool = False) -> str:
+    """Compile the planner library if any source changed; returns its path.
+    check=True builds the bounds-checked variant (KP_CHECK defined: every
+    array index the loop kernel derives is checked, see include/kp.h) into
+    its own library, libkinopax_check.so."""
+    lib, build_dir = (LIB_CHECK, BUILD + "_check") if check else (LIB, BUILD)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    if check:
+        extra = extra + ["-DKP_CHECK"]
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        objs = list(ex.map(lambda u: _compile(u, extra), UNITS))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda u: _compile(u, extra, build_dir), UNITS))
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -85,6 +85,17 @@ __global__ void kp_import_avail_kernel(KParams P, int n) {
     P.avail[P.region[v]] = 1;
 }
 
+// The bounds check itself (checked build only): an index one past the
+// tree is looked up through the checked-index path, which records the
+// error and reads element 0 instead.
+__global__ void kp_bounds_selftest_kernel(KParams P) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+#ifdef KP_CHECK
+  const int v = KP_IDX(P, P.t_e, P.t_e, 97);
+  P.ctl->n_edges = (int)P.in_ve[v];
+#endif
+}
+
 // Bounded wait on a flag that nothing sets; records the timeout.
 __global__ void kp_wait_selftest_kernel(KParams P) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -551,6 +562,7 @@ size_t build_blob(unsigned char* blob, const float* boxes, int nb, const kp_work
     bytes += round16((size_t)C);
   }
   P.n_boxes_pad = pad;
+  P.bp_n_ids = start[C];
   P.blob_bytes = (int32_t)bytes;
   for (int a = 0; a < 3; ++a) {
     P.bp_g[a] = g[a];
@@ -921,6 +933,8 @@ kp_status check_launch(kp_ctx* ctx, const KCtl& h) {
   if (h.err == KP_DEV_ERR_REPLAY)
     return fail(ctx, KP_ERR_STATE, "appended sample differs from its first derivation (site %d)",
                 h.err_where);
+  if (h.err == KP_DEV_ERR_BOUNDS)
+    return fail(ctx, KP_ERR_CUDA, "array index out of range (site %d)", h.err_where);
   if (h.err != 0) return fail(ctx, KP_ERR_CUDA, "device error %d", h.err);
   return KP_OK;
 }
@@ -1360,6 +1374,7 @@ kp_status kp_grow(kp_ctx* ctx, void* dev_arena, size_t arena_bytes, int32_t t_e)
   P.bp_start_off = old.bp_start_off;
   P.bp_ids_off = old.bp_ids_off;
   P.bp_clear_off = old.bp_clear_off;
+  P.bp_n_ids = old.bp_n_ids;
   for (int a = 0; a < 3; ++a) P.bp_scale[a] = old.bp_scale[a];
   P.nch = old.nch;
   P.sd_bytes = old.sd_bytes;
@@ -1441,6 +1456,23 @@ kp_status kp_set_grid_limit(kp_ctx* ctx, int32_t max_blocks) {
     return r != KP_OK ? r : s;
   }
   return KP_OK;
+}
+
+kp_status kp_selftest_bounds(kp_ctx* ctx) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+#ifndef KP_CHECK
+  return fail(ctx, KP_ERR_STATE, "not the bounds-checked build");
+#else
+  KP_CUDA(cudaMemsetAsync(ctx->arena + ctx->lay.ctl + offsetof(KCtl, err), 0, 8, ctx->stream));
+  KParams P = params_now(ctx);
+  kp_bounds_selftest_kernel<<<1, 32, 0, ctx->stream>>>(P);
+  KP_CUDA(cudaGetLastError());
+  KCtl h;
+  s = read_ctl(ctx, &h);
+  if (s != KP_OK) return s;
+  return check_launch(ctx, h);
+#endif
 }
 
 kp_status kp_selftest_wait_timeout(kp_ctx* ctx) {
@@ -1544,29 +1576,84 @@ constexpr int kStaticMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_base[kStaticMaxDevices];  // device address of the scratch, per device
 
-// Raw {lo, hi} box rows -> the obstacle blob the loop kernel reads, with a
-// one-cell broad-phase grid (every box in the single cell).
-__global__ void kp_static_blob_kernel(unsigned char* blob, const float* raw, int n, int pad,
-                                      int start_off, int ids_off) {
+// Raw {lo, hi} box rows -> the obstacle blob the loop kernel reads: padded
+// boxes, then a uniform broad-phase grid of g[0] g[1] g[2] cells (cell
+// starts, box ids of each cell in box order) and each cell's clearance, the
+// same structure the host builder makes for a context, built here by one
+// block of the device (the no-allocation path has no host staging).  A box
+// is listed in every cell of its range on each axis, the cell of a
+// coordinate v being the FP32 (v - lo) * scale clamped to [0, g - 1], as in
+// the hull test.  The clearance of a cell: the smallest over boxes of the
+// largest per-axis gap between the cell and the box in cell units, at most
+// KP_BP_CLEAR_CAP cells, less KP_BP_CLEAR_MARGIN, in sixteenths, rounded
+// down.  Shared memory: C + 1 ints of cell counts, then offsets.
+__global__ void __launch_bounds__(1024) kp_static_blob_kernel(
+    unsigned char* blob, const float* raw, int n, int pad, int gx, int gy, int gz, float sx,
+    float sy, float sz, float lx, float ly, float lz, int start_off, int ids_off, int clear_off) {
+  extern __shared__ int kcount[];
   float* dst = reinterpret_cast<float*>(blob);
   uint16_t* start = reinterpret_cast<uint16_t*>(blob + start_off);
   uint16_t* ids = reinterpret_cast<uint16_t*>(blob + ids_off);
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < pad; b += gridDim.x * blockDim.x) {
+  const int C = gx * gy * gz;
+  const int g3[3] = {gx, gy, gz};
+  const float s3[3] = {sx, sy, sz}, l3[3] = {lx, ly, lz};
+  for (int b = threadIdx.x; b < pad; b += blockDim.x) {
     float* o = dst + (size_t)b * 8;
     if (b < n) {
       const float* in = raw + (size_t)b * 6;
       o[0] = in[0] + 0.0f; o[1] = in[1] + 0.0f; o[2] = in[2] + 0.0f; o[3] = 0.0f;
       o[4] = in[3] + 0.0f; o[5] = in[4] + 0.0f; o[6] = in[5] + 0.0f; o[7] = 0.0f;
-      ids[b] = (uint16_t)b;
     } else {
       o[0] = o[1] = o[2] = INFINITY;
       o[4] = o[5] = o[6] = -INFINITY;
       o[3] = o[7] = 0.0f;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    start[0] = 0;
-    start[1] = (uint16_t)n;
+  __syncthreads();
+  auto in_range = [&](int b, const int* cc) {
+    for (int a = 0; a < 3; ++a) {
+      const int c0 = bp_cell_of(__fmul_rn(__fsub_rn(dst[b * 8 + a], l3[a]), s3[a]), g3[a]);
+      const int c1 = bp_cell_of(__fmul_rn(__fsub_rn(dst[b * 8 + 4 + a], l3[a]), s3[a]), g3[a]);
+      if (cc[a] < c0 || cc[a] > c1) return false;
+    }
+    return true;
+  };
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    const int cc[3] = {c % gx, (c / gx) % gy, c / (gx * gy)};
+    int k = 0;
+    double r = (double)KP_BP_CLEAR_CAP;
+    for (int b = 0; b < n; ++b) {
+      k += in_range(b, cc) ? 1 : 0;
+      double gap = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double bl = ((double)dst[b * 8 + a] - (double)l3[a]) * (double)s3[a];
+        const double bh = ((double)dst[b * 8 + 4 + a] - (double)l3[a]) * (double)s3[a];
+        gap = fmax(gap, fmax(bl - (double)(cc[a] + 1), (double)cc[a] - bh));
+      }
+      r = fmin(r, gap);
+    }
+    kcount[c] = k;
+    const double v = (r - KP_BP_CLEAR_MARGIN) * 16.0;
+    blob[clear_off + c] = v >= 1.0 ? (unsigned char)fmin(255.0, floor(v)) : (unsigned char)0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // cell starts: an exclusive prefix over the counts
+    int acc = 0;
+    for (int c = 0; c < C; ++c) {
+      start[c] = (uint16_t)acc;
+      acc += kcount[c];
+    }
+    start[C] = (uint16_t)acc;
+  }
+  __syncthreads();
+  // the ids, within the room the host counted for them (the same FP32 cell
+  // arithmetic gives the same count; the bound only guards the blob)
+  const int room = (clear_off - ids_off) / 2;
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    const int cc[3] = {c % gx, (c / gx) % gy, c / (gx * gy)};
+    int pos = start[c];
+    for (int b = 0; b < n && pos < room; ++b)
+      if (in_range(b, cc)) ids[pos++] = (uint16_t)b;
   }
 }
 
@@ -1597,6 +1684,14 @@ __global__ void __launch_bounds__(256) kp_lane_peak_kernel(int iters) {
 }
 
 }  // namespace
+
+extern "C" int32_t kp_bounds_checked(void) {
+#ifdef KP_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 extern "C" kp_status kp_measure_lane_peak(void* cuda_stream, double* lane_ops_per_s) {
   if (!lane_ops_per_s) return KP_ERR_ARG;
@@ -1685,11 +1780,37 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   fill_params(P, d, lay, sys, ws, prm, A);
   const int pad = (nb + 7) / 8 * 8;
   P.n_boxes_pad = pad;
-  P.bp_g[0] = P.bp_g[1] = P.bp_g[2] = 1;
-  P.bp_start_off = pad * 32;
-  P.bp_ids_off = P.bp_start_off + 16;
-  P.blob_bytes = P.bp_ids_off + (int32_t)round16((size_t)nb * 2);
-  for (int a = 0; a < 3; ++a) P.bp_scale[a] = (float)(1.0 / ((double)ws->hi[a] - (double)ws->lo[a]));
+  // the broad-phase grid: the finest cube of 16^3, 8^3, 4^3, 2^3, 1 whose
+  // (cell, box) entries and blob fit (counted here, built on the device)
+  int gc = KP_BP_MAX_G;
+  for (;; gc /= 2) {
+    float sc[3];
+    long long entries = 0;
+    for (int a = 0; a < 3; ++a) sc[a] = (float)((double)gc / ((double)ws->hi[a] - (double)ws->lo[a]));
+    for (int b = 0; b < nb; ++b) {
+      long long cells = 1;
+      for (int a = 0; a < 3; ++a) {
+        const float lo = obs->boxes[(size_t)b * 6 + a] + 0.0f, hi = obs->boxes[(size_t)b * 6 + 3 + a] + 0.0f;
+        cells *= host_bp_cell(hi, ws->lo[a], sc[a], gc) - host_bp_cell(lo, ws->lo[a], sc[a], gc) + 1;
+      }
+      entries += cells;
+    }
+    const size_t cells3 = (size_t)gc * gc * gc;
+    const size_t bytes = (size_t)pad * 32 + round16((cells3 + 1) * 2) + round16((size_t)entries * 2) +
+                         round16(cells3);
+    if (gc == 1 || (entries <= KP_BP_MAX_IDS && bytes <= (size_t)KP_BLOB_BYTES)) {
+      for (int a = 0; a < 3; ++a) {
+        P.bp_g[a] = gc;
+        P.bp_scale[a] = sc[a];
+      }
+      P.bp_start_off = pad * 32;
+      P.bp_ids_off = P.bp_start_off + (int32_t)round16((cells3 + 1) * 2);
+      P.bp_clear_off = P.bp_ids_off + (int32_t)round16((size_t)entries * 2);
+      P.bp_n_ids = (int32_t)entries;
+      P.blob_bytes = P.bp_clear_off + (int32_t)round16(cells3);
+      break;
+    }
+  }
   for (int a = 0; a < 3; ++a) P.goal_c[a] = goal->center[a];
   P.goal_r2 = (float)((double)goal->radius * (double)goal->radius);
   P.seed_lo = (uint32_t)(prm->seed & 0xffffffffu);
@@ -1703,18 +1824,28 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
     cudaGetLastError();
     return KP_ERR_CUDA;
   }
-  const int min_ch = d.R_pad / (d.R_pad < 128 ? d.R_pad : 128);
-  const int sd = min_ch > 1024 ? min_ch : 1024;
-  P.sd_bytes = sd * 8;
-  const size_t smem = (size_t)P.blob_bytes + (size_t)sd * 8;
-  if (occupancy(d.sys, false, smem, &bps) != cudaSuccess || bps < 1) {
-    cudaGetLastError();
-    return KP_ERR_CUDA;
-  }
-  int grid = bps * num_sms;
-  if (grid > KP_MAX_GRID) grid = KP_MAX_GRID;
+  // as configure_launch: the grid with room for any chunking, the chunks
+  // of that grid, then the score scratch those chunks need
+  int grid = 0;
+  auto shape = [&](int sd) -> kp_status {
+    const size_t smem = (size_t)P.blob_bytes + (size_t)sd * 8;
+    if (occupancy(d.sys, false, smem, &bps) != cudaSuccess) {
+      cudaGetLastError();
+      return KP_ERR_CUDA;
+    }
+    if (bps < 1) return KP_ERR_ARG;  // no block of this shape can be resident
+    grid = bps * num_sms;
+    if (grid > KP_MAX_GRID) grid = KP_MAX_GRID;
+    P.sd_bytes = sd * 8;
+    return KP_OK;
+  };
+  const int min_ch = d.R_pad / (d.R_pad < 1024 ? d.R_pad : 1024);
+  kp_status ss = shape(min_ch > 1024 ? min_ch : 1024);
+  if (ss != KP_OK) return ss;
   P.nch = region_chunks(grid, d.R_pad);
-  if (d.R_pad / P.nch > sd) return KP_ERR_ARG;  // a chunk's scores exceed the scratch
+  ss = shape(d.R_pad / P.nch > P.nch ? d.R_pad / P.nch : P.nch);
+  if (ss != KP_OK) return ss;
+  const size_t smem = (size_t)P.blob_bytes + (size_t)P.sd_bytes;
 
   cudaError_t e = cudaSuccess;
   auto ok = [&](cudaError_t r) {
@@ -1725,9 +1856,10 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   // the device into the box slots
   if (nb > 0)
     ok(cudaMemcpyAsync(A + lay.traj, obs->boxes, (size_t)nb * 24, cudaMemcpyHostToDevice, stream));
-  kp_static_blob_kernel<<<(pad + 255) / 256 > 0 ? (pad + 255) / 256 : 1, 256, 0, stream>>>(
+  kp_static_blob_kernel<<<1, 1024, (size_t)(P.bp_g[0] * P.bp_g[1] * P.bp_g[2] + 1) * 4, stream>>>(
       reinterpret_cast<unsigned char*>(A + lay.boxes), reinterpret_cast<const float*>(A + lay.traj),
-      nb, pad, P.bp_start_off, P.bp_ids_off);
+      nb, pad, P.bp_g[0], P.bp_g[1], P.bp_g[2], P.bp_scale[0], P.bp_scale[1], P.bp_scale[2],
+      ws->lo[0], ws->lo[1], ws->lo[2], P.bp_start_off, P.bp_ids_off, P.bp_clear_off);
   ok(cudaGetLastError());
   // everything that must start from zero (the scratch keeps old contents)
   ok(cudaMemsetAsync(A + lay.ctl, 0, sizeof(KCtl), stream));
@@ -1764,6 +1896,7 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
   ok(cudaStreamSynchronize(stream));
   if (e != cudaSuccess) return KP_ERR_CUDA;
   if (h.err == KP_DEV_ERR_TIMEOUT) return KP_ERR_TIMEOUT;
+  if (h.err == KP_DEV_ERR_REPLAY) return KP_ERR_STATE;  // as kp_plan reports it
   if (h.err != 0) return KP_ERR_CUDA;
   if (h.state == KP_DEV_BAD_ROOT) return KP_ERR_ARG;
   traj->n_edges = 0;

@@ -34,6 +34,22 @@ __device__ __forceinline__ void raise_error(KCtl* ctl, int code, int where) {
   if (atomicCAS(&ctl->err, 0, code) == 0) ctl->err_where = where;
 }
 
+// Array indices of the loop kernel.  In the bounds-checked build (KP_CHECK
+// defined) an index outside [0, n) records KP_DEV_ERR_BOUNDS with its site
+// and 0 is used in its place, so that no access leaves its array, nothing
+// traps, and every block stops at its next barrier; the host reports the
+// site.  Otherwise the index is used as it is.
+#ifdef KP_CHECK
+__device__ __forceinline__ long long kp_checked(KCtl* ctl, long long i, long long n, int site) {
+  if (i >= 0 && i < n) return i;
+  raise_error(ctl, KP_DEV_ERR_BOUNDS, site);
+  return 0;
+}
+#define KP_IDX(P, i, n, site) ((int)kp_checked((P).ctl, (long long)(i), (long long)(n), (site)))
+#else
+#define KP_IDX(P, i, n, site) (i)
+#endif
+
 // A team of blocks that plans one query: block index within the team, team
 // size, and the team's barrier words.  The single-query launch is one team
 // of the whole grid; the server launch splits its grid into teams.
@@ -508,7 +524,7 @@ __device__ __forceinline__ bool hull_hits_grid(const KParams& P, const float4* _
   const int y0 = bp_cell_of(tly, gy), y1 = bp_cell_of(thy, gy);
   const int z0 = bp_cell_of(tlz, gz), z1 = bp_cell_of(thz, gz);
   if (sclear != nullptr) {
-    const float r = (float)sclear[x0 + gx * (y0 + gy * z0)] * 0.0625f;
+    const float r = (float)sclear[KP_IDX(P, x0 + gx * (y0 + gy * z0), gx * gy * gz, 60)] * 0.0625f;
     const float fx = (float)x0, fy = (float)y0, fz = (float)z0;
     if (r > 0.0f && tlx >= fx - r && thx <= fx + 1.0f + r && tly >= fy - r &&
         thy <= fy + 1.0f + r && tlz >= fz - r && thz <= fz + 1.0f + r)
@@ -519,10 +535,10 @@ __device__ __forceinline__ bool hull_hits_grid(const KParams& P, const float4* _
   for (int cz = z0; cz <= z1 && !hit; ++cz)
     for (int cy = y0; cy <= y1 && !hit; ++cy)
       for (int cx = x0; cx <= x1 && !hit; ++cx) {
-        const int c = cx + gx * (cy + gy * cz);
+        const int c = KP_IDX(P, cx + gx * (cy + gy * cz), gx * gy * gz, 61);
         const int e = sstart[c + 1];
         for (int q = sstart[c]; q < e; ++q) {
-          const int b = sids[q];
+          const int b = KP_IDX(P, sids[KP_IDX(P, q, P.bp_n_ids, 62)], P.n_boxes_pad, 63);
           ++n;
           if (box_meets_hull(sbox[2 * b], sbox[2 * b + 1], lx, ly, lz, hx, hy, hz)) {
             hit = true;

@@ -15,7 +15,9 @@ enum { KP_DEV_RUNNING = 0, KP_DEV_SOLVED = 1, KP_DEV_FULL = 2, KP_DEV_BAD_ROOT =
 // launch errors stored in KCtl::err
 // KP_DEV_ERR_REPLAY: with the sample log on, an accepted sample re-derived
 // from its key when it is appended differed from its first derivation.
-enum { KP_DEV_OK = 0, KP_DEV_ERR_TIMEOUT = 1, KP_DEV_ERR_REPLAY = 2 };
+// KP_DEV_ERR_BOUNDS (bounds-checked build only): an array index outside its
+// array; err_where holds the site.
+enum { KP_DEV_OK = 0, KP_DEV_ERR_TIMEOUT = 1, KP_DEV_ERR_REPLAY = 2, KP_DEV_ERR_BOUNDS = 3 };
 // per-sample flag bits
 enum {
   KP_F_VALID = 1,
@@ -169,6 +171,7 @@ struct KParams {
   int32_t bp_start_off;  // byte offsets inside the blob
   int32_t bp_ids_off;
   int32_t bp_clear_off;  // the cells' clearances (uint8), -1: none
+  int32_t bp_n_ids;      // (cell, box) entries of the grid
   float bp_scale[3];     // cells per unit length, per axis
   // tree, SoA over t_e nodes
   float* st;          // [D][t_e]

@@ -176,9 +176,10 @@ __device__ __forceinline__ void count_ve(const KParams& P, const Team& T, int n,
   int v0, v1;
   chunk_of(T, n, &v0, &v1);
   int c = 0;
-  for (int v = v0 + (int)threadIdx.x; v < v1; v += (int)blockDim.x) c += P.in_ve[v] ? 1 : 0;
+  for (int v = v0 + (int)threadIdx.x; v < v1; v += (int)blockDim.x)
+    c += P.in_ve[KP_IDX(P, v, P.t_e, 1)] ? 1 : 0;
   const int tot = block_sum(c, sh);
-  if (threadIdx.x == 0) P.blk_b[T.b] = (uint32_t)tot;
+  if (threadIdx.x == 0) P.blk_b[KP_IDX(P, T.b, KP_MAX_GRID, 2)] = (uint32_t)tot;
 }
 
 // Phase L: write the V_E list (ascending node id) from the per-block counts:
@@ -195,7 +196,7 @@ __device__ __forceinline__ int write_ve(const KParams& P, const Team& T, int n, 
   int base = (int)off;
   for (int t0 = v0; t0 < v1; t0 += (int)blockDim.x) {
     const int v = t0 + (int)threadIdx.x;
-    const bool m = v < v1 && P.in_ve[v];
+    const bool m = v < v1 && P.in_ve[KP_IDX(P, v, P.t_e, 3)];
     const uint32_t bal = __ballot_sync(0xffffffffu, m);
     if (lane == 0) sh.scan.warp[w] = __popc(bal);
     __syncthreads();
@@ -205,7 +206,7 @@ __device__ __forceinline__ int write_ve(const KParams& P, const Team& T, int n, 
       before += q < (int)w ? cq : 0;
       tile += cq;
     }
-    if (m) P.ve[base + before + __popc(bal & ((1u << lane) - 1u))] = v;
+    if (m) P.ve[KP_IDX(P, base + before + __popc(bal & ((1u << lane) - 1u)), P.t_e, 4)] = v;
     base += tile;
     __syncthreads();
   }
@@ -343,7 +344,7 @@ __device__ __forceinline__ int draw_controls(const KParams& P, uint32_t it, int 
   constexpr int N = System<SYS>::N;
   const int p = key / lam;
   const int j = key - p * lam;
-  const int v = P.ve[p];
+  const int v = KP_IDX(P, P.ve[KP_IDX(P, p, P.t_e, 5)], P.t_e, 6);
   const uint4 w0 = philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 0u), P.seed_lo, P.seed_hi);
   const uint4 w1 = philox4x32_10(make_uint4(it, (uint32_t)v, (uint32_t)j, 1u), P.seed_lo, P.seed_hi);
   wr[0] = w0.x; wr[1] = w0.y; wr[2] = w0.z; wr[3] = w0.w;
@@ -456,6 +457,9 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
         const bool valid = fail == 0;
         uint32_t f = 0;
         if (valid) {
+          r = KP_IDX(P, r, P.R, 7);
+          s = KP_IDX(P, s, (long long)P.R * P.n_sub_per, 8);
+          key = KP_IDX(P, key, P.t_e, 9);
           atomicAdd(&P.n_valid[r], 1u);
           f = KP_F_VALID;
           const bool cont = P.visited[s] == 0;
@@ -490,9 +494,9 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
                                    4 * q + 3 < D ? x[4 * q + 3] : 0.0f);
           }
         } else {
-          atomicAdd(&P.n_invalid[r], 1u);
+          atomicAdd(&P.n_invalid[KP_IDX(P, r, P.R, 10)], 1u);
         }
-        P.flags[key] = (uint8_t)f;
+        P.flags[KP_IDX(P, key, P.t_e, 11)] = (uint8_t)f;
         if (LOG && key < P.log.capacity) {
           P.log.node[key] = v;
           P.log.k[key] = k;
@@ -640,9 +644,12 @@ __device__ __forceinline__ void phase_accept(const KParams& P, const Team& T, in
     }
 #pragma unroll
     for (int q = 0; q < KP_ACC_KPL; ++q)
-      s[q] = (f[q] & KP_F_CONTENDER) ? P.cs[t0 + 32 * q + (int)lane] : 0;
+      s[q] = (f[q] & KP_F_CONTENDER) ? P.cs[KP_IDX(P, t0 + 32 * q + (int)lane, P.t_e, 12)] : 0;
 #pragma unroll
-    for (int q = 0; q < KP_ACC_KPL; ++q) c[q] = (f[q] & KP_F_CONTENDER) ? P.claim[s[q]] : 0u;
+    for (int q = 0; q < KP_ACC_KPL; ++q)
+      c[q] = (f[q] & KP_F_CONTENDER)
+                 ? P.claim[KP_IDX(P, s[q], (long long)P.R * P.n_sub_per, 13)]
+                 : 0u;
 #pragma unroll
     for (int q = 0; q < KP_ACC_KPL; ++q) {
       const int key = t0 + 32 * q + (int)lane;
@@ -651,7 +658,9 @@ __device__ __forceinline__ void phase_accept(const KParams& P, const Team& T, in
       const bool win = (f[q] & KP_F_CONTENDER) && c[q] == (uint32_t)key;
       const bool acc = valid && (win || (f[q] & KP_F_BERN));
       const uint32_t m = __ballot_sync(FULL, acc);
-      if (acc) P.acc_key[a + n_acc + __popc(m & lt)] = (uint32_t)key | (win ? 0x80000000u : 0u);
+      if (acc)
+        P.acc_key[KP_IDX(P, a + n_acc + __popc(m & lt), P.t_e, 14)] =
+            (uint32_t)key | (win ? 0x80000000u : 0u);
       n_acc += __popc(m);
       if (LOG && key < b && key < P.log.capacity)
         P.log.flags[key] =
@@ -678,7 +687,7 @@ __device__ __forceinline__ void phase_accept(const KParams& P, const Team& T, in
   block_sum2((unsigned long long)n_valid, 0, sh.red, &bv, &dummy);
   if (threadIdx.x == 0) {
     if (T.b == 0) P.ctl->work_next = 0;  // the expand phase is over
-    P.blk_a[T.b] = (uint32_t)block_acc;
+    P.blk_a[KP_IDX(P, T.b, KP_MAX_GRID, 15)] = (uint32_t)block_acc;
     if (bv) atomicAdd(&P.ctl->it_valid, (uint32_t)bv);
   }
 }
@@ -726,7 +735,7 @@ __device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, in
     sd[i] = sc;
   }
   warp_pairwise(sd, ch);
-  if (lane == 0) P.chunk_sum[T.b] = sd[0];
+  if (lane == 0) P.chunk_sum[KP_IDX(P, T.b, KP_MAX_GRID, 16)] = sd[0];
   __syncwarp();
 }
 
@@ -783,9 +792,9 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int i
 #pragma unroll
     for (int q = 0; q < KP_WARPS; ++q)
       if (j >= sh.acc_off[q] && j < sh.acc_off[q] + sh.acc_n[q]) w = q;
-    const uint32_t e = P.acc_key[sh.acc_a[w] + (j - sh.acc_off[w])];
-    const int key = (int)(e & 0x7fffffffu);
-    const int id = id0 + j;
+    const uint32_t e = P.acc_key[KP_IDX(P, sh.acc_a[w] + (j - sh.acc_off[w]), P.t_e, 17)];
+    const int key = KP_IDX(P, (int)(e & 0x7fffffffu), P.t_e, 18);
+    const int id = KP_IDX(P, id0 + j, P.t_e, 19);
     float x[D], u[N];
     int k;
     uint32_t wacc, wr[4];
@@ -803,6 +812,8 @@ __device__ __forceinline__ void materialise(const KParams& P, uint32_t it, int i
     }
     int r, s;
     bin_state<SYS>(x, P, &r, &s, sblob);
+    r = KP_IDX(P, r, P.R, 20);
+    s = KP_IDX(P, s, (long long)P.R * P.n_sub_per, 21);
 #pragma unroll
     for (int d = 0; d < D; ++d) P.st[(size_t)d * P.t_e + id] = x[d];
 #pragma unroll
@@ -901,7 +912,7 @@ __device__ __forceinline__ void phase_nodesets(const KParams& P, const Team& T, 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       vq[q] = t0 + q * stride + (int)threadIdx.x;
-      rq[q] = vq[q] < o1 ? __ldcg(P.region + vq[q]) : 0;
+      rq[q] = vq[q] < o1 ? KP_IDX(P, __ldcg(P.region + KP_IDX(P, vq[q], P.t_e, 22)), P.R, 23) : 0;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) tq[q] = vq[q] < o1 ? __ldcg(P.thr + rq[q]) : 0ull;
@@ -920,7 +931,7 @@ __device__ __forceinline__ void phase_nodesets(const KParams& P, const Team& T, 
   // appended them, so they are counted, not read)
   const int new0 = v0 > t_old ? v0 : t_old;
   const int tot = block_sum(c, sh) + (v1 > new0 ? v1 - new0 : 0);
-  if (threadIdx.x == 0) P.blk_b[T.b] = (uint32_t)tot;
+  if (threadIdx.x == 0) P.blk_b[KP_IDX(P, T.b, KP_MAX_GRID, 24)] = (uint32_t)tot;
 }
 
 // The loop of one query (Algorithm 1 body, repeated) run by a team of

@@ -97,6 +97,7 @@ class SampleLog(C.Structure):
 
 
 _lib = None
+_lib_path = LIB_PATH
 
 # every entry point of include/kp.h: name -> (restype, argtypes)
 _vp = C.c_void_p
@@ -123,6 +124,8 @@ SIGNATURES = {
     "kp_set_wait_limit": (C.c_int, [_vp, C.c_uint64]),
     "kp_set_grid_limit": (C.c_int, [_vp, C.c_int32]),
     "kp_selftest_wait_timeout": (C.c_int, [_vp]),
+    "kp_bounds_checked": (C.c_int32, []),
+    "kp_selftest_bounds": (C.c_int, [_vp]),
     "kp_plan_static": (C.c_int, [C.POINTER(System), C.POINTER(Workspace), C.POINTER(Obstacles),
                                  C.POINTER(Params), C.POINTER(C.c_float), C.POINTER(Goal),
                                  C.POINTER(Budget), C.POINTER(Traj), _vp]),
@@ -156,15 +159,23 @@ SIGNATURES = {
 }
 
 
+def use_library(path):
+    """Selects the planner library later calls use (for example the
+    bounds-checked build of build.build_planner(check=True)); contexts made
+    with another library must be closed first."""
+    global _lib, _lib_path
+    _lib, _lib_path = None, path
+
+
 def lib():
     """The loaded planner library.  Raises when it has not been built."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
+        if not os.path.exists(_lib_path):
             raise RuntimeError(
-                f"CUDA planner library missing ({LIB_PATH}); build it with "
+                f"CUDA planner library missing ({_lib_path}); build it with "
                 "paper_2409_06807_gb300.build.build_planner()")
-        L = C.CDLL(LIB_PATH)
+        L = C.CDLL(_lib_path)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(L, name)
             fn.restype = res
@@ -523,6 +534,9 @@ class Planner:
     def set_grid_limit(self, max_blocks):
         """Caps the loop launch at max_blocks blocks (0: the resident maximum)."""
         self._check(lib().kp_set_grid_limit(self._ctx, int(max_blocks)), "kp_set_grid_limit")
+
+    def selftest_bounds(self):
+        return lib().kp_selftest_bounds(self._ctx)
 
     def selftest_wait_timeout(self):
         return lib().kp_selftest_wait_timeout(self._ctx)

@@ -15,12 +15,19 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def P():
+    import os
     import torch
     if not torch.cuda.is_available():
         pytest.fail("CUDA device required")
     from paper_2409_06807_gb300.build import build_planner
-    build_planner()
     from paper_2409_06807_gb300 import planner
+    if os.environ.get("KP_TEST_BOUNDS_CHECKED") == "1":
+        # tests/test_gpu_checked.py reruns suites of this file on the
+        # bounds-checked build, in a process of their own
+        planner.use_library(build_planner(check=True))
+        assert planner.lib().kp_bounds_checked() == 1
+    else:
+        build_planner()
     return planner
 
 

@@ -59,8 +59,12 @@ def test_alone_and_in_the_mix_are_identical(S):
 
 def test_server_results_revalidated_and_match_single_launch(S):
     """Solved server queries re-validate under the oracle; the single-query
-    launch on the same inputs returns the same trajectory within the parity
-    tolerance."""
+    launch on the same inputs returns the same trajectory bit for bit.  Both
+    run the same explicitly rounded FP32 arithmetic on the same keys, and
+    the obstacle test's verdict is exact whatever the broad-phase grid (the
+    server's blob is built without cell clearances, within its 48 KB room),
+    so status, edge count, states, controls and durations must agree
+    exactly."""
     P, serve = S
     qs = [W.c1(s) for s in range(3)] + [W.c2(s, t_e=1 << 18) for s in range(2)]
     srv = serve.Server(4 << 30, team_blocks=32, max_slots=16, idle_ms=50)
@@ -68,6 +72,8 @@ def test_server_results_revalidated_and_match_single_launch(S):
     srv.drain()
     for w, i in zip(qs, ids):
         st, tr = srv.result(i)
+        st1, tr1 = P.Planner(w).plan(max_iters=100)
+        assert st1 == st
         if st != P.OK:
             continue
         o = Oracle(w)
@@ -80,10 +86,7 @@ def test_server_results_revalidated_and_match_single_launch(S):
             assert np.max(np.abs(x_end - tr["states"][e]) / scale) <= 1e-4
             prev = tr["states"][e].astype(np.float64)
         assert np.linalg.norm(prev[:3] - w.goal_c) <= float(w.goal_r) * (1 + 1e-6)
-        st1, tr1 = P.Planner(w).plan(max_iters=100)
-        assert st1 == st
-        if len(tr1["steps"]) == len(tr["steps"]):
-            assert np.max(np.abs(tr1["states"] - tr["states"]) / scale) <= 1e-4
+        assert _same(tr1, tr), (len(tr1["steps"]), len(tr["steps"]))
     srv.close()
 
 

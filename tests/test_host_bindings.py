@@ -129,3 +129,45 @@ def test_arena_grows_by_the_per_node_rows():
     q2 = _required(W.c3(0).with_(t_e=1 << 21))
     # 12D: state 48, control 16, kept end state 64
     assert abs((q2 - q) - (191 + 24 + 4 + 32) * (1 << 20)) <= 256 * 32
+
+
+def test_arena_one_byte_short_is_refused_before_any_device_work():
+    """Failure injection on the host: an arena one byte smaller than
+    kp_required_bytes makes kp_create return KP_ERR_OOM and leave *out NULL,
+    a network arena one byte short makes kp_mlp_create do the same, and a
+    server pool below its control area makes kp_server_create do the same.
+    The arena pointer given is an aligned address nothing backs: the size
+    check comes before any device call, so no GPU is needed and nothing is
+    touched."""
+    import ctypes as C
+    from paper_2409_06807_gb300 import planner
+    from paper_2409_06807_gb300 import workloads as W
+    L = planner.lib()
+    fake = C.c_void_p(1 << 20)  # 256-byte aligned, never dereferenced
+    for w in (W.c1(0), W.c2(0), W.c3(0)):
+        s, ws, p = planner.structs(w)
+        need = L.kp_required_bytes(C.byref(s), C.byref(ws), len(w.boxes), C.byref(p))
+        boxes = w.boxes.astype(np.float32).reshape(-1)
+        obs = planner.Obstacles(boxes.ctypes.data_as(C.POINTER(C.c_float)), len(w.boxes))
+        out = C.c_void_p(12345)
+        st = L.kp_create(C.byref(s), C.byref(ws), C.byref(obs), C.byref(p), fake, need - 1,
+                         None, C.byref(out))
+        assert st == planner.ERR_OOM and out.value is None
+        # misaligned arena: an argument error, also before any device call
+        st = L.kp_create(C.byref(s), C.byref(ws), C.byref(obs), C.byref(p),
+                         C.c_void_p((1 << 20) + 16), need, None, C.byref(out))
+        assert st == planner.ERR_ARG and out.value is None
+    m_need = L.kp_mlp_required_bytes(4096)
+    params = np.zeros(L.kp_mlp_num_params(), np.float32)
+    out = C.c_void_p(12345)
+    st = L.kp_mlp_create(fake, m_need - 1, 4096, params.ctypes.data_as(C.POINTER(C.c_float)),
+                         None, C.byref(out))
+    assert st == planner.ERR_OOM and out.value is None
+
+    class Cfg(C.Structure):
+        _fields_ = [("team_blocks", C.c_int32), ("max_slots", C.c_int32), ("idle_ms", C.c_double)]
+    c = Cfg(16, 64, 50.0)
+    ctl = L.kp_server_required_bytes(64)
+    out = C.c_void_p(12345)
+    st = L.kp_server_create(C.byref(c), fake, ctl - 1, None, C.byref(out))
+    assert st == planner.ERR_OOM and out.value is None

@@ -54,17 +54,59 @@ def static_plan(P, w, max_iters=200, capacity=1024):
     return st, dict(states=states[:n, : w.d], ctrls=ctrls[:n, : w.n_ctrl], steps=steps[:n])
 
 
-def test_static_plan_matches_kp_plan_on_consecutive_calls(P):
-    for seed in (0, 1):  # two calls in a row share the static scratch
-        w = W.c1(seed)
-        st_ref, ref = P.Planner(w).plan(max_iters=200, capacity=1024)
-        st, got = static_plan(P, w)
-        assert st == st_ref == P.OK
-        assert np.array_equal(got["steps"], ref["steps"])
-        scale = state_scale(w)
+def _same_as_kp_plan(P, w, max_iters=200):
+    st_ref, ref = P.Planner(w).plan(max_iters=max_iters, capacity=1024)
+    st, got = static_plan(P, w, max_iters=max_iters)
+    assert st == st_ref
+    assert np.array_equal(got["steps"], ref["steps"])
+    scale = state_scale(w)
+    if len(got["steps"]):
         assert np.max(np.abs(got["states"] - ref["states"]) / scale) <= 1e-4
         span = np.asarray(w.u_hi[: w.n_ctrl]) - np.asarray(w.u_lo[: w.n_ctrl])
         assert np.max(np.abs(got["ctrls"] - ref["ctrls"]) / span) <= 1e-6
+    return st, got
+
+
+def _revalidate(w, traj):
+    """Every returned edge re-propagated in FP64 from its parent state by the
+    oracle and checked densely (100 sub-steps per integrator step)."""
+    from oracle.kpo import Oracle
+    o = Oracle(w)
+    scale = state_scale(w)
+    prev = np.asarray(w.x_init, np.float64)
+    for e in range(len(traj["steps"])):
+        depth, x_end = o.dense_check(prev, traj["ctrls"][e].astype(np.float64),
+                                     int(traj["steps"][e]), 100)
+        assert depth <= 1e-4, f"edge {e} penetrates by {depth}"
+        assert np.max(np.abs(x_end - traj["states"][e]) / scale) <= 1e-4
+        prev = traj["states"][e].astype(np.float64)
+    assert np.linalg.norm(prev[:3] - w.goal_c) <= float(w.goal_r) * (1 + 1e-6)
+
+
+def test_static_plan_matches_kp_plan_on_consecutive_calls(P):
+    for seed in (0, 1):  # two calls in a row share the static scratch
+        st, got = _same_as_kp_plan(P, W.c1(seed))
+        assert st == P.OK
+        _revalidate(W.c1(seed), got)
+
+
+def test_static_plan_calls_of_changing_shape(P):
+    """Calls whose shapes differ share the scratch: a Dubins forest query
+    (4,096 regions, 200 boxes), a double-integrator query (512 regions, 16
+    boxes), the forest again, and a forest query over an 8,192-region state
+    grid.  The scratch keeps what the larger call left (tables, box rows,
+    the grid); each call must still return kp_plan's result, and every
+    solved trajectory re-validates under the oracle."""
+    sg = (0, 0, 0, 4, 2, 2, 0, 0, 0, 0, 0, 0)
+    seq = [W.c2(3, t_e=60000, lambda_max=32), W.c1(1), W.c2(3, t_e=60000, lambda_max=32),
+           W.c2(5, t_e=40000, lambda_max=32, grid=(8, 8, 8), state_grid=sg)]
+    solved = 0
+    for w in seq:
+        st, got = _same_as_kp_plan(P, w)
+        if st == P.OK:
+            solved += 1
+            _revalidate(w, got)
+    assert solved >= 3
 
 
 def test_static_plan_refuses_oversized_problem(P):
