@@ -422,6 +422,63 @@ def workload_leg(name, n_layouts, local, flush, peak_ops, seed0=70_000):
     return out
 
 
+def static_leg(local, n_layouts=100, seed0=80_000):
+    """kp_plan_static (no allocation: static device scratch, broad-phase grid
+    built on the device each call) against kp_plan on the same
+    double-integrator layouts: per-query time from CUDA events on the
+    stream around each call, and identical results."""
+    import ctypes as C
+    import torch
+    from paper_2409_06807_gb300 import planner as P
+    seeds = list(range(seed0, seed0 + n_layouts))
+    stream = torch.cuda.current_stream(local)
+    pl = P.Planner(W.c1(seeds[0]), device=f"cuda:{local}", stream=stream)
+    cap = 1024
+    states = np.zeros((cap, 12), np.float32)
+    ctrls = np.zeros((cap, 4), np.float32)
+    steps = np.zeros(cap, np.int32)
+    t = P.Traj(cap, 0, states.ctypes.data_as(C.POINTER(C.c_float)),
+               ctrls.ctypes.data_as(C.POINTER(C.c_float)),
+               steps.ctypes.data_as(C.POINTER(C.c_int32)))
+    ms_s, ms_p, same = [], [], 0
+    for i, sd in enumerate([seeds[0]] + seeds):
+        w = W.c1(sd)
+        s_, ws, prm = P.structs(w)
+        boxes = np.ascontiguousarray(w.boxes, np.float32).reshape(-1)
+        obs = P.Obstacles(boxes.ctypes.data_as(C.POINTER(C.c_float)), len(w.boxes))
+        x = np.ascontiguousarray(w.x_init, np.float32)
+        g = P.goal_struct(w)
+        b = P.Budget(MAX_ITERS, 0.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = P.lib().kp_plan_static(C.byref(s_), C.byref(ws), C.byref(obs), C.byref(prm),
+                                    x.ctypes.data_as(C.POINTER(C.c_float)), C.byref(g),
+                                    C.byref(b), C.byref(t), C.c_void_p(stream.cuda_stream))
+        e1.record(stream)
+        e1.synchronize()
+        n = t.n_edges
+        got = steps[:max(n, 0)].copy()
+        pl.set_obstacles(w.boxes)
+        pl.w = w
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        pl.plan_async(max_iters=MAX_ITERS, capacity=cap)
+        e3.record(stream)
+        st_p, tr = pl.plan_result()
+        if i == 0:
+            continue  # warm-up
+        ms_s.append(e0.elapsed_time(e1))
+        ms_p.append(e2.elapsed_time(e3))
+        same += int(st == st_p and np.array_equal(got, tr["steps"]))
+    pl.close()
+    return {"workload": f"double integrator, {n_layouts} layouts (seeds {seeds[0]}..{seeds[-1]})",
+            "static_p50_ms": float(np.median(ms_s)), "plan_p50_ms": float(np.median(ms_p)),
+            "static_mean_ms": float(np.mean(ms_s)), "plan_mean_ms": float(np.mean(ms_p)),
+            "same_result": same / n_layouts,
+            "note": "static: obstacle rows copied and the grid built on the device inside "
+                    "the timed call; kp_plan: the grid was built by kp_set_obstacles before"}
+
+
 def nodeset_leg(local, peak_ops, hbm_gbs, n_nodes=1 << 22, reps=10):
     """The node-set pass of Algorithm 4 on a large tree: a seeded tree of
     n_nodes nodes (the quadrotor building's system, t_e 2^23) whose V_E
@@ -676,6 +733,7 @@ def serving_leg(n_queries, rate_hz, pool_gb, local, flush):
     recs = S.run_arrivals(srv, arrivals, max_iters=MAX_ITERS)
     wall = time.perf_counter() - t0
     batched = S.summarize(recs, wall)
+    batched["by_system"] = S.summarize_by_system(recs)
     batched["teams"] = srv.stats()["teams"]
     srv.close()
     # the same queries, one at a time on the whole GPU
@@ -818,6 +876,8 @@ def run_ours(args, world, rank, local):
         extra["c3"] = workload_leg("c3", args.c3_layouts, local, flush, peak_ops)
     if args.nodeset:
         extra["nodeset_pass"] = nodeset_leg(local, peak_ops, float(pk.get("hbm_gbs", 6800.0)))
+    if args.static_layouts > 0:
+        extra["static_entry"] = static_leg(local, args.static_layouts)
     if args.steady:
         extra["steady_state"] = steady_state_leg(local, peak_ops)
     if args.decomp_layouts > 0:
@@ -883,6 +943,8 @@ def main():
                     help="layouts of the double-integrator leg (0: skip)")
     ap.add_argument("--c3-layouts", type=int, default=10,
                     help="layouts of the quadrotor-building leg (0: skip)")
+    ap.add_argument("--static-layouts", type=int, default=100,
+                    help="layouts of the kp_plan_static timing (0: skip)")
     ap.add_argument("--no-nodeset", dest="nodeset", action="store_false",
                     help="skip the node-set pass measurement")
     ap.add_argument("--learned-layouts", type=int, default=1000,

@@ -130,6 +130,7 @@ def run_arrivals(server, arrivals, max_iters=400, timeout_s=300.0):
     per-query records with latency measured from arrival to completion."""
     t0 = time.perf_counter()
     ids = {}
+    kinds = {}
     recs = []
     i = 0
     while i < len(arrivals) or len(recs) < len(arrivals):
@@ -137,10 +138,12 @@ def run_arrivals(server, arrivals, max_iters=400, timeout_s=300.0):
         while i < len(arrivals) and arrivals[i][0] <= now:
             qid = server.submit(arrivals[i][1], max_iters=max_iters)
             ids[qid] = arrivals[i][0]
+            kinds[qid] = (arrivals[i][1].system, arrivals[i][1].t_e, len(arrivals[i][1].boxes))
             i += 1
         for d in server.poll():
             t_done = time.perf_counter() - t0
             d["arrival_s"] = ids[d["id"]]
+            d["system"], d["t_e"], d["boxes"] = kinds[d["id"]]
             d["done_s"] = t_done
             d["latency_ms"] = 1e3 * (t_done - ids[d["id"]])
             recs.append(d)
@@ -162,6 +165,25 @@ def summarize(recs, wall_s):
                 samples_per_s=float(sum(r["samples"] for r in recs)) / wall_s,
                 status={STATUS_NAMES.get(k, k): int(v) for k, v in
                         zip(*np.unique([r["status"] for r in recs], return_counts=True))})
+
+
+def summarize_by_system(recs):
+    """Per system: queries, success rate, latency p50/p99 and, for the
+    queries that ended without a solution, their count and the node caps
+    they had (a cap below what the system needs fails by construction)."""
+    out = {}
+    for sysid in sorted({r["system"] for r in recs}):
+        rs = [r for r in recs if r["system"] == sysid]
+        lat = np.array([r["latency_ms"] for r in rs])
+        fail = [r for r in rs if r["status"] != OK]
+        out[str(sysid)] = dict(
+            queries=len(rs), success=float(np.mean([r["status"] == OK for r in rs])),
+            p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+            failures=len(fail),
+            failed_t_e_median=float(np.median([r["t_e"] for r in fail])) if fail else None,
+            solved_t_e_median=float(np.median([r["t_e"] for r in rs if r["status"] == OK]))
+            if len(fail) < len(rs) else None)
+    return out
 
 
 def autotune(sample_queries, team_candidates=(8, 16, 32, 64), lambda_candidates=(32, 64, 128),

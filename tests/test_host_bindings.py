@@ -43,6 +43,25 @@ def test_serving_summary():
     assert s["status"] == {"OK": 75, "NO_SOLUTION": 25}
 
 
+def test_serving_summary_by_system():
+    """Failures are attributed to their system with the node caps they had."""
+    recs = []
+    for i in range(30):
+        sysid = i % 3
+        t_e = 1 << (14 + i % 7)
+        ok = not (sysid == 2 and t_e < (1 << 19))
+        recs.append(dict(latency_ms=float(i + 1), status=OK if ok else NO_SOLUTION,
+                         samples=10, system=sysid, t_e=t_e, boxes=10))
+    by = serve.summarize_by_system(recs)
+    assert sorted(by) == ["0", "1", "2"]
+    assert by["0"]["success"] == 1.0 and by["0"]["failures"] == 0
+    assert by["0"]["failed_t_e_median"] is None
+    fails = [r for r in recs if r["system"] == 2 and r["status"] != OK]
+    assert by["2"]["failures"] == len(fails) > 0
+    assert by["2"]["failed_t_e_median"] == float(np.median([r["t_e"] for r in fails]))
+    assert by["2"]["queries"] == 10 and by["2"]["success"] == (10 - len(fails)) / 10
+
+
 def _required(w, n_boxes=None, edit=None):
     import ctypes as C
     from paper_2409_06807_gb300 import planner
