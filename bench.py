@@ -674,7 +674,7 @@ def learned_leg(n_layouts, local, flush, peak_tflops):
     from paper_2409_06807_gb300 import mlp as M
     from paper_2409_06807_gb300 import planner as P
     t0 = time.perf_counter()
-    feats, targs = M.harvest(W.c2, list(range(0, 1000)), 2_000_000)
+    feats, targs = M.harvest(W.c2, list(range(0, 1000)), 2_000_000)  # 2,000 per layout
     t_harvest = time.perf_counter() - t0
     net = M.Mlp(max_batch=4096)
     epochs, batch = 4, 4096
@@ -698,11 +698,43 @@ def learned_leg(n_layouts, local, flush, peak_tflops):
         rows = [timed_query(pl, W.c2(s), flush, MAX_ITERS) for s in seeds]
         out[mode] = mode_summary(rows, P.OK)
     pl.close()
+    # the gain on fixed frontiers (new sub-regions per sample and per step,
+    # same keys) and the gain the network phase needs to break even (its
+    # time over the expand's on the same passes)
+    cov = {m: [0, 0, 0, 0, 0] for m in ("plain", "learned")}
+    for fs in range(20_000, 20_008):
+        wf = W.c2(fs)
+        g = P.Planner(wf, device=f"cuda:{local}")
+        g.reset()
+        g.expand_step(3)  # the frontier: 3 plain passes
+        t = g.export_tree()
+        g.close()
+        for mode, mix in (("plain", 0.0), ("learned", 0.5)):
+            g = P.Planner(wf, device=f"cuda:{local}")
+            g.attach_mlp(net if mix > 0 else None, mix)
+            g.import_tree(t)
+            st = g.expand_step(1)[0]
+            inf = g.info()
+            c = cov[mode]
+            c[0] += int(g.export_tree()["visited"].sum()) - int(t["visited"].sum())
+            c[1] += inf["n_samples"]
+            c[2] += inf["n_steps"]
+            c[3] += st["phase_ns"][0] + st["phase_ns"][1]
+            c[4] += st["phase_ns"][3] + st["phase_ns"][6]
+            g.close()
+    (n0, s0, k0, _, _), (n1, s1, k1, e1, f1) = cov["plain"], cov["learned"]
     return {
+        "frontier_gain": {"new_subregions_per_sample": (n1 / s1) / (n0 / s0) - 1.0,
+                          "new_subregions_per_step": (n1 / k1) / (n0 / k0) - 1.0,
+                          "break_even": f1 / e1,
+                          "how": "one pass over 8 frontiers (each the tree after 3 plain "
+                                 "passes of a forest, seeds 20000..20007), same keys; break-even "
+                                 "= network phase time / expand time of those passes"},
         "workload": f"Dubins forest (200 boxes), {n_layouts} held-out layouts (seeds "
                     f"{seeds[0]}..{seeds[-1]}), mix 0.5 learned / uniform draws",
         "harvest": {"pairs": int(feats.shape[0]), "seconds": t_harvest,
-                    "layout_seeds": "plain runs from seed 0"},
+                    "layout_seeds": "plain runs on seeds 0..999, an even random share of "
+                                    "each run's pairs"},
         "training": {"epochs": epochs, "batch": batch, "loss_per_epoch": hist,
                      "ms": train_ms, "tflops": train_tflops,
                      "frac_of_bf16_peak": train_tflops / peak_tflops},

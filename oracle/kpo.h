@@ -166,8 +166,9 @@ int32_t kpo_path(const kpo *o, int32_t *nodes, int32_t cap);
  * (k - k_min) / (k_max - k_min) * 2 - 1 for the duration.
  * Learned draw of a sample (selector word < mix * 2^32): normals z_0..z_3
  * by Box-Muller from Philox purpose 3 words, q = clamp(mean + exp(log_std)
- * z, -1, 1), u_i = lo_i + (hi_i - lo_i)(q_i + 1)/2, k = k_min +
- * floor((k_max - k_min)(q_3 + 1)/2 + 1/2).  Only 6D systems. */
+ * z, -1, 1), u_i = lo_i + (hi_i - lo_i)(q_i + 1)/2 for the controls; the
+ * duration k stays the uniform draw (purpose 1, word 0), so a learned
+ * sample costs the integrator steps a uniform one does.  Only 6D systems. */
 int32_t kpo_mlp_num_params(void);
 void kpo_mlp_forward(const double *p, const double *x, int32_t M, double *out);
 double kpo_mlp_loss_grad(const double *p, const double *x, const double *t,

@@ -431,9 +431,8 @@ int32_t kpo_iterate(kpo *o, kpo_records *rec, kpo_iter_stats *st) {
         }
         for (int i = 0; i < N; ++i)
           u[i] = o->cfg.u_lo[i] + (o->cfg.u_hi[i] - o->cfg.u_lo[i]) * (q[i] + 1.0) * 0.5;
-        k = o->cfg.k_min +
-            (int)floor((double)(o->cfg.k_max - o->cfg.k_min) * (q[3] + 1.0) * 0.5 + 0.5);
-        if (k > o->cfg.k_max) k = o->cfg.k_max;
+        /* the duration keeps the uniform draw (the network's duration
+         * output is trained but not drawn from) */
       }
       /* PropagateODE with the validity check after every step */
       memcpy(traj, o->x + (size_t)v * d, sizeof(double) * d);

@@ -334,7 +334,8 @@ __device__ __forceinline__ void box_muller4(uint4 w, float* z) {
 // parent's node id.  Counter (it, node, j, purpose): purpose 0 the control
 // words (kept in wr), purpose 1 (duration, accept word, selector); with a
 // network attached and the selector below the mix threshold, the control
-// and duration come from the node's Gaussian with normals from purpose 3.
+// comes from the node's Gaussian with normals from purpose 3 (the duration
+// keeps the uniform draw).
 // The expand phase and the node-set phase (which appends accepted samples
 // by their keys) both draw through this function, so both see the same
 // numbers.
@@ -358,13 +359,10 @@ __device__ __forceinline__ int draw_controls(const KParams& P, uint32_t it, int 
     box_muller4(w3, z);
     mlp_heads(P.net_raw + (size_t)p * MLP_OUT, mean, ls);
 #pragma unroll
-    for (int d = 0; d < 4; ++d) q[d] = fminf(fmaxf(__fmaf_rn(expf(ls[d]), z[d], mean[d]), -1.0f), 1.0f);
+    for (int d = 0; d < N; ++d) q[d] = fminf(fmaxf(__fmaf_rn(expf(ls[d]), z[d], mean[d]), -1.0f), 1.0f);
 #pragma unroll
     for (int d = 0; d < N; ++d)
       u[d] = __fmaf_rn(P.u_scale[d], __fmul_rn(__fadd_rn(q[d], 1.0f), 0.5f), P.u_lo[d]);
-    const int kk = P.k_min + (int)floorf(__fmaf_rn((float)(P.k_span - 1),
-                                                   __fmul_rn(__fadd_rn(q[3], 1.0f), 0.5f), 0.5f));
-    *k = kk < P.k_min + (int)P.k_span - 1 ? kk : P.k_min + (int)P.k_span - 1;
   }
   *wacc = w1.y;
   return v;

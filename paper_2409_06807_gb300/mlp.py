@@ -131,15 +131,21 @@ class Mlp:
         return loss.value if want_loss else None
 
 
-def harvest(make_workload, seeds, n_pairs, max_iters=400, planner=None):
-    """Plain planner runs on the given layouts until n_pairs training pairs
-    (parent features -> draw of a sample that reached a new sub-region) are
-    collected.  Returns CUDA tensors (features [n, 32], targets [n, 4])."""
+def harvest(make_workload, seeds, n_pairs, max_iters=400, planner=None, per_query_cap=1 << 18,
+            seed=0):
+    """Plain planner runs on the given layouts; from each, an even share of
+    n_pairs training pairs (parent features -> draw of a sample that reached
+    a new sub-region), chosen uniformly at random (seeded) among all the
+    pairs that query produced, so that every layout and every stage of its
+    search is represented.  Returns CUDA tensors (features [n, 32], targets
+    [n, 4]) of at most n_pairs rows."""
     import torch
     from .planner import Planner
     w0 = make_workload(seeds[0])
     pl = planner or Planner(w0)
-    pl.set_harvest(n_pairs)
+    pl.set_harvest(per_query_cap)
+    share = -(-n_pairs // len(seeds))  # ceil
+    rng = np.random.Generator(np.random.PCG64(seed))
     feats, targs, have = [], [], 0
     for s in seeds:
         w = make_workload(s)
@@ -148,9 +154,12 @@ def harvest(make_workload, seeds, n_pairs, max_iters=400, planner=None):
         pl.harvest_reset()
         pl.plan(max_iters=max_iters, x_init=w.x_init)
         f, t = pl.harvest()
-        take = min(len(f), n_pairs - have)
-        feats.append(f[:take].clone())
-        targs.append(t[:take].clone())
+        take = min(len(f), share, n_pairs - have)
+        if take <= 0:
+            continue
+        idx = torch.from_numpy(np.sort(rng.choice(len(f), size=take, replace=False))).to(f.device)
+        feats.append(f.index_select(0, idx).clone())
+        targs.append(t.index_select(0, idx).clone())
         have += take
         if have >= n_pairs:
             break

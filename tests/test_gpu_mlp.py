@@ -128,7 +128,8 @@ def test_harvest_matches_oracle(M, fso):
 def test_learned_pass_matches_oracle(M):
     """One pass from the root with a network attached: samples whose
     selector picks the uniform draw match the oracle as in the plain
-    planner; learned samples draw controls within BF16 tolerance."""
+    planner; learned samples draw their controls within BF16 tolerance and
+    their durations exactly (the uniform draw)."""
     import torch
     mlp, P = M
     w = W.c2(0, lambda_max=256)
@@ -156,7 +157,8 @@ def test_learned_pass_matches_oracle(M):
     ok = (grec["flags"][uni] & 1) == (orec["flags"][uni] & 1)
     amb = orec["m_valid"][uni] < 1e-4
     assert np.all(ok | amb)
-    assert np.all(np.abs(grec["k"][learned] - orec["k"][learned]) <= 1)
+    # the duration is the uniform draw for learned samples too
+    assert np.array_equal(grec["k"], orec["k"])
 
 
 def test_learned_plan_revalidated(M):
@@ -231,3 +233,60 @@ def test_gradients_match_oracle_large_ragged_batch(M):
     for blk_g, blk_r in zip(mlp.split(g), kpo.mlp_split(ref)):
         err = np.linalg.norm(blk_g - blk_r) / max(np.linalg.norm(blk_r), 1e-12)
         assert err < 3e-2, err
+
+
+def _frontier_coverage(P, net, mix, seeds):
+    """New sub-regions reached, samples and integrator steps of one pass
+    over each oracle-grown frontier (3 passes of the Dubins forest), with
+    the network attached at 'mix' (0: the uniform draw alone)."""
+    from oracle.kpo import Oracle
+    new = samples = steps = 0
+    expand_ns = net_ns = 0
+    for s in seeds:
+        w = W.c2(s)
+        src = Oracle(w)
+        src.reset()
+        for _ in range(3):
+            src.iterate()
+        t = src.export()
+        t["state"] = t["state"].astype(np.float32)
+        t["ctrl"] = t["ctrl"].astype(np.float32)
+        g = P.Planner(w)
+        g.attach_mlp(net if mix > 0 else None, mix)
+        g.import_tree(t)
+        before = int(g.export_tree()["visited"].sum())
+        st = g.expand_step(1)[0]
+        inf = g.info()
+        new += int(g.export_tree()["visited"].sum()) - before
+        samples += inf["n_samples"]
+        steps += inf["n_steps"]
+        expand_ns += st["phase_ns"][0] + st["phase_ns"][1]
+        net_ns += st["phase_ns"][3] + st["phase_ns"][6]
+        g.close()
+    return new, samples, steps, expand_ns, net_ns
+
+
+def test_learned_gain_and_its_break_even(M):
+    """What the trained network gains over the method without it, on the
+    same frontiers and the same random stream: a network trained on pairs
+    harvested evenly from 200 plain forest runs (2,000 a layout) reaches
+    more new sub-regions per sample than the uniform draw alone.  Whether
+    that pays depends on the network phase each pass adds before the
+    expand; the gain needed to break even is that phase's time over the
+    expand's (measured here, on the same passes).  Both are printed for
+    the record; the benchmark reports them on 1,000 held-out layouts."""
+    mlp, P = M
+    feats, targs = mlp.harvest(W.c2, list(range(200)), 400_000)
+    assert 300_000 <= feats.shape[0] <= 400_000
+    net = mlp.Mlp(max_batch=4096)
+    hist = mlp.train(net, feats, targs, epochs=4, batch=4096, lr=1e-3)
+    assert hist[-1] < hist[0]
+    seeds = list(range(20_000, 20_008))
+    n0, s0, k0, e0, _ = _frontier_coverage(P, net, 0.0, seeds)
+    n1, s1, k1, e1, f1 = _frontier_coverage(P, net, 0.5, seeds)
+    assert s0 == s1  # same frontiers, same keys
+    gain = (n1 / s1) / (n0 / s0) - 1.0
+    break_even = f1 / e1
+    print(f"learned: {gain:+.3f} new sub-regions per sample, {(n1 / k1) / (n0 / k0) - 1:+.3f} per "
+          f"integrator step; network phase / expand = {break_even:.3f}")
+    assert gain > 0.01, gain

@@ -131,8 +131,22 @@ def test_learned_draw_and_harvest():
                     for k, n in enumerate(rec["node"])])
     learned = sel < 2 ** 31
     assert 0.4 < learned.mean() < 0.6
-    # learned durations sit at the middle of [k_min, k_max]
-    mid = w.k_min + math.floor((w.k_max - w.k_min) * 0.5 + 0.5)
-    assert np.mean(np.abs(rec["k"][learned] - mid) <= 1) > 0.9
+    # every duration, learned or not, is the uniform draw of purpose 1
+    kw = np.array([kpo.philox4x32_10([st["iteration"], n, k % st["lambda"], 1],
+                                     [w.seed & 0xFFFFFFFF, w.seed >> 32])[0]
+                   for k, n in enumerate(rec["node"])], np.uint64)
+    span = w.k_max - w.k_min + 1
+    assert np.array_equal(rec["k"], w.k_min + ((kw * span) >> 32).astype(np.int64))
+    # learned controls sit at the middle of U (narrow Gaussians centred at
+    # 0): the pass's new nodes follow its accepted keys in order
+    t = o.export()
+    acc = np.flatnonzero(rec["flags"] & 16)
+    ctrl = t["ctrl"][t["n_nodes"] - len(acc):]
+    lo, hi = np.asarray(w.u_lo[:3], np.float64), np.asarray(w.u_hi[:3], np.float64)
+    q = 2 * (ctrl - lo) / (hi - lo) - 1
+    lrn = learned[acc]
+    assert lrn.any() and (~lrn).any()
+    assert np.max(np.abs(q[lrn])) < 0.2
+    assert np.max(np.abs(q[~lrn])) > 0.5
     hf, ht = o.harvest()
     assert len(hf) > 0 and np.all(np.abs(ht) <= 1.0 + 1e-12)
