@@ -567,6 +567,7 @@ size_t build_blob(unsigned char* blob, const float* boxes, int nb, const kp_work
   for (int a = 0; a < 3; ++a) {
     P.bp_g[a] = g[a];
     P.bp_scale[a] = scale[a];
+    P.bp_last[a] = (float)(g[a] - 1);
   }
   P.bp_start_off = (int32_t)start_off;
   P.bp_ids_off = (int32_t)ids_off;
@@ -831,6 +832,7 @@ void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* 
   P = KParams{};
   P.sys = d.sys;
   P.dt = sys->dt;
+  P.dt_sixth = sys->dt / 6.0f;  // the same correctly rounded FP32 division the device made
   P.k_min = sys->k_min;
   P.k_span = (uint32_t)(sys->k_max - sys->k_min + 1);
   for (int i = 0; i < 12; ++i) {
@@ -1376,6 +1378,7 @@ kp_status kp_grow(kp_ctx* ctx, void* dev_arena, size_t arena_bytes, int32_t t_e)
   P.bp_clear_off = old.bp_clear_off;
   P.bp_n_ids = old.bp_n_ids;
   for (int a = 0; a < 3; ++a) P.bp_scale[a] = old.bp_scale[a];
+  for (int a = 0; a < 3; ++a) P.bp_last[a] = old.bp_last[a];
   P.nch = old.nch;
   P.sd_bytes = old.sd_bytes;
   P.mlp_W1 = old.mlp_W1;
@@ -1612,8 +1615,10 @@ __global__ void __launch_bounds__(1024) kp_static_blob_kernel(
   __syncthreads();
   auto in_range = [&](int b, const int* cc) {
     for (int a = 0; a < 3; ++a) {
-      const int c0 = bp_cell_of(__fmul_rn(__fsub_rn(dst[b * 8 + a], l3[a]), s3[a]), g3[a]);
-      const int c1 = bp_cell_of(__fmul_rn(__fsub_rn(dst[b * 8 + 4 + a], l3[a]), s3[a]), g3[a]);
+      float f;
+      const float last = (float)(g3[a] - 1);
+      const int c0 = bp_cell_of(__fmul_rn(__fsub_rn(dst[b * 8 + a], l3[a]), s3[a]), last, &f);
+      const int c1 = bp_cell_of(__fmul_rn(__fsub_rn(dst[b * 8 + 4 + a], l3[a]), s3[a]), last, &f);
       if (cc[a] < c0 || cc[a] > c1) return false;
     }
     return true;
@@ -1802,6 +1807,7 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
       for (int a = 0; a < 3; ++a) {
         P.bp_g[a] = gc;
         P.bp_scale[a] = sc[a];
+        P.bp_last[a] = (float)(gc - 1);
       }
       P.bp_start_off = pad * 32;
       P.bp_ids_off = P.bp_start_off + (int32_t)round16((cells3 + 1) * 2);

@@ -206,8 +206,12 @@ __device__ __forceinline__ float unit24(uint32_t w) {
 // 2pi), 2pi split into C1 = fl32(2pi) and C2 = 2pi - C1 so that k C1 is
 // exact for |k| < 2^11 (|x| below ~1.2e4 rad); then the hardware sin/cos
 // approximations on r in [-pi, pi] (absolute error below 1e-6).
+// k is rounded to the nearest integer (ties to even) by adding and
+// subtracting 1.5 * 2^23: exact for |x / 2pi| < 2^22, and kept on the FP32
+// pipe instead of the slower conversion unit.
 __device__ __forceinline__ void sincos_reduced(float x, float* s, float* c) {
-  const float k = rintf(__fmul_rn(x, 0.159154943091895336f));
+  const float k =
+      __fsub_rn(__fadd_rn(__fmul_rn(x, 0.159154943091895336f), 12582912.0f), 12582912.0f);
   float r = __fmaf_rn(-k, 6.28318548202514648f, x);
   r = __fmaf_rn(-k, -1.74845560007448838e-07f, r);
   __sincosf(r, s, c);
@@ -249,13 +253,14 @@ struct System<KP_SYS_DI> {
 };
 
 // One classic RK4 step x <- x + h/6 (k1 + 2 k2 + 2 k3 + k4), stage points
-// x + h/2 k1, x + h/2 k2, x + h k3.  The combination is accumulated as each
+// x + h/2 k1, x + h/2 k2, x + h k3; h6 = h / 6, rounded as an FP32 division
+// (KParams::dt_sixth).  The combination is accumulated as each
 // stage is evaluated, in the fixed order ((k1 + 2 k2) + 2 k3) + k4, so only
 // one stage derivative is live at a time (the register budget of the loop
 // kernel holds no four of them for the 12D system).  F(t, k) evaluates the
 // field at t into k.
 template <int D, class F>
-__device__ __forceinline__ void rk4_step(float* x, float h, F field) {
+__device__ __forceinline__ void rk4_step(float* x, float h, float h6, F field) {
   float acc[D], k[D], t[D];
   const float hh = __fmul_rn(0.5f, h);
   field(x, k);
@@ -277,7 +282,6 @@ __device__ __forceinline__ void rk4_step(float* x, float h, F field) {
     t[i] = __fmaf_rn(h, k[i], x[i]);
   }
   field(t, k);
-  const float h6 = __fdiv_rn(h, 6.0f);
 #pragma unroll
   for (int i = 0; i < D; ++i) x[i] = __fmaf_rn(h6, __fadd_rn(acc[i], k[i]), x[i]);
 }
@@ -299,8 +303,8 @@ struct System<KP_SYS_DUBINS> {
     dx[5] = u[2];
   }
   __device__ __forceinline__ static void step(float* x, const float* u, float h,
-                                              const KParams&) {
-    rk4_step<6>(x, h, [&](const float* y, float* dy) { f(y, u, dy); });
+                                              const KParams& P) {
+    rk4_step<6>(x, h, P.dt_sixth, [&](const float* y, float* dy) { f(y, u, dy); });
   }
   __device__ __forceinline__ static float speed(const float* x) { return fabsf(x[5]); }
 };
@@ -348,7 +352,7 @@ struct System<KP_SYS_QUAD> {
   }
   __device__ __forceinline__ static void step(float* x, const float* u, float h,
                                               const KParams& P) {
-    rk4_step<12>(x, h, [&](const float* y, float* dy) { f(y, u, P, dy); });
+    rk4_step<12>(x, h, P.dt_sixth, [&](const float* y, float* dy) { f(y, u, P, dy); });
   }
   __device__ __forceinline__ static float speed(const float* x) {
     return sqrtf(__fmaf_rn(x[8], x[8], __fmaf_rn(x[7], x[7], __fmul_rn(x[6], x[6]))));
@@ -491,9 +495,19 @@ __device__ __forceinline__ bool box_meets_hull(float4 bl, float4 bh, float lx, f
 }
 
 // Broad-phase cell of a coordinate already in cell units (the host build
-// uses the same FP32 arithmetic): clamped to [0, g - 1].
-__device__ __forceinline__ int bp_cell_of(float t, int g) {
-  return t >= 0.0f ? (t < (float)g ? (int)t : g - 1) : 0;
+// uses the same FP32 arithmetic), clamped to [0, g - 1] (NaN to 0); last =
+// g - 1 as a float.  The floor is taken on the FP32 pipe: adding 2^23 with
+// rounding down leaves floor(t) in the low mantissa bits (exact for t in
+// [0, 2^23)); the cell comes back both as an int and as a float.
+__device__ __forceinline__ int bp_cell_of(float t, float last, float* ft) {
+  const float v = __fadd_rd(fminf(fmaxf(t, 0.0f), last), 8388608.0f);
+  *ft = __fsub_rn(v, 8388608.0f);
+  return __float_as_int(v) - 0x4B000000;
+}
+
+// A byte as a float, on the FP32 pipe (exact).
+__device__ __forceinline__ float byte_as_float(uint32_t q) {
+  return __fsub_rn(__int_as_float(0x4B000000 | q), 8388608.0f);
 }
 
 // Exact coarse-then-fine collision test of a step hull (the paper's coarse
@@ -520,12 +534,14 @@ __device__ __forceinline__ bool hull_hits_grid(const KParams& P, const float4* _
   const float thy = __fmul_rn(__fsub_rn(hy, P.ws_lo[1]), P.bp_scale[1]);
   const float tlz = __fmul_rn(__fsub_rn(lz, P.ws_lo[2]), P.bp_scale[2]);
   const float thz = __fmul_rn(__fsub_rn(hz, P.ws_lo[2]), P.bp_scale[2]);
-  const int x0 = bp_cell_of(tlx, gx), x1 = bp_cell_of(thx, gx);
-  const int y0 = bp_cell_of(tly, gy), y1 = bp_cell_of(thy, gy);
-  const int z0 = bp_cell_of(tlz, gz), z1 = bp_cell_of(thz, gz);
+  float fx, fy, fz, dummy;
+  const int x0 = bp_cell_of(tlx, P.bp_last[0], &fx), x1 = bp_cell_of(thx, P.bp_last[0], &dummy);
+  const int y0 = bp_cell_of(tly, P.bp_last[1], &fy), y1 = bp_cell_of(thy, P.bp_last[1], &dummy);
+  const int z0 = bp_cell_of(tlz, P.bp_last[2], &fz), z1 = bp_cell_of(thz, P.bp_last[2], &dummy);
   if (sclear != nullptr) {
-    const float r = (float)sclear[KP_IDX(P, x0 + gx * (y0 + gy * z0), gx * gy * gz, 60)] * 0.0625f;
-    const float fx = (float)x0, fy = (float)y0, fz = (float)z0;
+    const float r =
+        __fmul_rn(byte_as_float(sclear[KP_IDX(P, x0 + gx * (y0 + gy * z0), gx * gy * gz, 60)]),
+                  0.0625f);
     if (r > 0.0f && tlx >= fx - r && thx <= fx + 1.0f + r && tly >= fy - r &&
         thy <= fy + 1.0f + r && tlz >= fz - r && thz <= fz + 1.0f + r)
       return false;

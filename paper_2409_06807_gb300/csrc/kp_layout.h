@@ -116,6 +116,7 @@ struct KParams {
   // system (Sec. II)
   int32_t sys;
   float dt;
+  float dt_sixth;   // dt / 6 (RK4 combination), IEEE FP32 division on the host
   int32_t k_min;
   uint32_t k_span;  // k_max - k_min + 1
   float x_lo[12], x_hi[12];
@@ -173,6 +174,7 @@ struct KParams {
   int32_t bp_clear_off;  // the cells' clearances (uint8), -1: none
   int32_t bp_n_ids;      // (cell, box) entries of the grid
   float bp_scale[3];     // cells per unit length, per axis
+  float bp_last[3];      // bp_g - 1 per axis, as a float
   // tree, SoA over t_e nodes
   float* st;          // [D][t_e]
   int32_t* parent;
