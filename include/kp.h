@@ -93,7 +93,7 @@ typedef struct {
  * the server. */
 typedef struct {
   float lo[3], hi[3];
-  int32_t grid[3];
+  int32_t grid[3];            /* 1 .. 4096, and grid[a] * sub[a] <= 2^22    */
   int32_t speed_bins;         /* >= 1 (1: no speed bins)                    */
   float speed_hi;
   int32_t sub[3];

@@ -222,6 +222,9 @@ const char* check_inputs(const kp_system* sys, const kp_workspace* ws, int32_t n
       return "bad workspace";
     if (ws->grid[a] < 1 || ws->sub[a] < 1 || ws->grid[a] > 4096 || ws->sub[a] > 4096)
       return "bad grid";
+    // fine cells per axis below 2^22: the device floors cell coordinates by
+    // an add of 2^23, exact below it
+    if ((long long)ws->grid[a] * ws->sub[a] > (1 << 22)) return "bad grid";
   }
   if (ws->speed_bins < 1 || ws->speed_bins > 4096) return "bad speed bins";
   if (ws->speed_bins > 1 && !(ws->speed_hi > 0.0f)) return "bad speed range";
@@ -853,6 +856,10 @@ void fill_params(KParams& P, const Dims& d, const Layout& lay, const kp_system* 
   for (int a = 0; a < 3; ++a) {
     P.ws_lo[a] = ws->lo[a];
     P.n_fine[a] = ws->grid[a] * ws->sub[a];
+    P.n_fine_last[a] = (float)(P.n_fine[a] - 1);
+    P.sub_shift[a] = -1;
+    for (int b = 0; b < 16; ++b)
+      if (ws->sub[a] == (1 << b)) P.sub_shift[a] = b;
     P.fine_scale[a] = (float)((double)P.n_fine[a] / ((double)ws->hi[a] - (double)ws->lo[a]));
     P.sub[a] = ws->sub[a];
     P.grid[a] = ws->grid[a];

@@ -193,9 +193,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-// 24 high bits of a word as a float in [0, 1), exact.
+// 24 high bits of a word as a float in [0, 1), exact.  Each 12-bit half is
+// made a float by placing it in the mantissa of 2^23 and subtracting 2^23
+// (FP32 pipe, no conversion instruction); hi * 2^12 + lo < 2^24 is exact.
 __device__ __forceinline__ float unit24(uint32_t w) {
-  return __uint2float_rn(w >> 8) * 5.9604644775390625e-08f;
+  const float hi = __fsub_rn(__uint_as_float(0x4B000000u | (w >> 20)), 8388608.0f);
+  const float lo = __fsub_rn(__uint_as_float(0x4B000000u | ((w >> 8) & 0xFFFu)), 8388608.0f);
+  return __fmul_rn(__fmaf_rn(hi, 4096.0f, lo), 5.9604644775390625e-08f);
 }
 
 // ---------------------------------------------------------------------------
@@ -410,9 +414,11 @@ __device__ __forceinline__ void bin_state(const float* x, const KParams& P, int*
   int cell[3], fine[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
+    // the floor of fine_cell on the FP32 pipe (as the broad phase's cells)
     const float t = __fmul_rn(__fsub_rn(x[a], P.ws_lo[a]), P.fine_scale[a]);
-    const int f = fine_cell(t, P.n_fine[a]);
-    cell[a] = f / P.sub[a];
+    const float v = __fadd_rd(fminf(fmaxf(t, 0.0f), P.n_fine_last[a]), 8388608.0f);
+    const int f = __float_as_int(v) - 0x4B000000;
+    cell[a] = P.sub_shift[a] >= 0 ? f >> P.sub_shift[a] : f / P.sub[a];
     fine[a] = f - cell[a] * P.sub[a];
   }
   int sb = 0;

@@ -127,7 +127,9 @@ struct KParams {
   float ws_lo[3];
   float fine_scale[3];  // fine cells per unit length
   int32_t n_fine[3];    // grid * sub per axis
+  float n_fine_last[3]; // n_fine - 1 per axis, as a float
   int32_t sub[3];
+  int32_t sub_shift[3]; // log2(sub) when sub is a power of two, else -1
   int32_t grid[3];
   int32_t speed_bins;
   float speed_scale;    // speed_bins / speed_hi

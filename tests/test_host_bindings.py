@@ -127,6 +127,15 @@ def test_box_count_and_decomposition_limits():
         ws.grid[0] = ws.grid[1] = ws.grid[2] = 4096
     assert _required(w, edit=huge) == 0
 
+    def fine_axis(n_sub):
+        def edit(s, ws, p):  # one axis of 4096 cells x n_sub sub-cells, the others 1 x 1
+            ws.grid[0], ws.grid[1], ws.grid[2] = 4096, 1, 1
+            ws.sub[0], ws.sub[1], ws.sub[2] = n_sub, 1, 1
+        return edit
+    # at most 2^22 fine cells along an axis (the device's exact cell floor)
+    assert _required(w, edit=fine_axis(1024)) > 0
+    assert _required(w, edit=fine_axis(2048)) == 0
+
     def quad_massless(s, ws, p):
         s.phys[0] = 0.0
     assert _required(W.c3(0)) > 0 and _required(W.c3(0), edit=quad_massless) == 0
