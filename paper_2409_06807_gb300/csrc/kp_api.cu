@@ -1291,15 +1291,9 @@ kp_status kp_import_tree(kp_ctx* ctx, const kp_tree_view* v) {
   h.iteration = v->iteration;
   h.goal_node = KP_NO_GOAL;
   h.state = KP_DEV_RUNNING;
-  // keep the barrier generation the device already holds
+  // the barrier word starts at 0 (no launch is in flight)
   kp_status rs = ensure_pinned(ctx, sizeof(KCtl));
   if (rs != KP_OK) return rs;
-  KP_CUDA(cudaMemcpyAsync(ctx->pinned, ctx->arena + L.ctl, sizeof(KCtl), cudaMemcpyDeviceToHost,
-                          ctx->stream));
-  KP_CUDA(cudaStreamSynchronize(ctx->stream));
-  KCtl cur;
-  std::memcpy(&cur, ctx->pinned, sizeof(KCtl));
-  h.bar_gen = cur.bar_gen;
   std::memcpy(ctx->pinned, &h, sizeof(KCtl));
   KP_CUDA(cudaMemcpyAsync(ctx->arena + L.ctl, ctx->pinned, sizeof(KCtl), cudaMemcpyHostToDevice,
                           ctx->stream));

@@ -51,49 +51,45 @@ __device__ __forceinline__ long long kp_checked(KCtl* ctl, long long i, long lon
 #endif
 
 // A team of blocks that plans one query: block index within the team, team
-// size, and the team's barrier words.  The single-query launch is one team
+// size, and the team's barrier word.  The single-query launch is one team
 // of the whole grid; the server launch splits its grid into teams.
 struct Team {
   int b, nb;
-  uint32_t* bar_count;
-  uint32_t* bar_gen;
+  uint32_t* bar;
 };
 
-// Barrier of a team of co-resident blocks (cooperative launch).  Every wait
-// is bounded by
-// 'limit_ns' of device time; on expiry the block records KP_ERR_TIMEOUT and
-// all blocks leave at their next barrier.  Returns false when the launch
-// must stop.  Sense is carried by a generation counter: a block reads the
-// generation, arrives, and the last arriver resets the count and publishes
-// the next generation with release semantics.
-// With 'watch' given, thread 0 also reads that word after the barrier and
-// the block gets its value in *watched (one load per block instead of one
-// per thread on a word every block reads).
+// Barrier of a team of co-resident blocks (cooperative launch) on one word
+// whose top bit is the phase.  Every block but the team's block 0 adds 1,
+// block 0 adds 2^31 - (nb - 1): the arrivals sum to 2^31, so the top bit
+// flips with the last arrival and the low 31 bits come back to 0, with no
+// reset and no second word.  A block waits until the top bit differs from
+// the one its own arrival saw.  The low bits start at 0 (the reset and
+// import paths write the word) and stay below 2^31 while any arrival is
+// out, so the bit cannot flip early.  Every wait is bounded by 'limit_ns'
+// of device time; on expiry the block records KP_ERR_TIMEOUT and all blocks
+// leave at their next barrier (the word is then left mid-phase: a launch
+// that timed out poisons its context).  Returns false when the launch must
+// stop.  With 'watch' given, thread 0 also reads that word after the
+// barrier and the block gets its value in *watched (one load per block
+// instead of one per thread on a word every block reads).
 __device__ __forceinline__ bool team_sync(const Team& T, KCtl* ctl, uint64_t limit_ns, int where,
                                           const int* watch = nullptr, int* watched = nullptr) {
-  const uint32_t nblocks = (uint32_t)T.nb;
   __shared__ int s_ok, s_watch;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    uint32_t gen = ld_acquire(T.bar_gen);
+    const uint32_t add = T.b == 0 ? 0x80000000u - (uint32_t)(T.nb - 1) : 1u;
     __threadfence();
-    uint32_t ticket = atomicAdd(T.bar_count, 1u);
-    if (ticket == nblocks - 1) {
-      *T.bar_count = 0;
-      __threadfence();
-      st_release(T.bar_gen, gen + 1);
-    } else {
-      const uint64_t t0 = global_ns();
-      uint32_t spins = 0;
-      while (ld_acquire(T.bar_gen) == gen) {
-        if ((++spins & 63u) == 0) {
-          if (*((volatile int*)&ctl->err) != 0) { ok = 0; break; }
-          if (global_ns() - t0 > limit_ns) {
-            raise_error(ctl, KP_DEV_ERR_TIMEOUT, where);
-            ok = 0;
-            break;
-          }
+    const uint32_t seen = atomicAdd(T.bar, add) & 0x80000000u;
+    const uint64_t t0 = global_ns();
+    uint32_t spins = 0;
+    while ((ld_acquire(T.bar) & 0x80000000u) == seen) {
+      if ((++spins & 63u) == 0) {
+        if (*((volatile int*)&ctl->err) != 0) { ok = 0; break; }
+        if (global_ns() - t0 > limit_ns) {
+          raise_error(ctl, KP_DEV_ERR_TIMEOUT, where);
+          ok = 0;
+          break;
         }
       }
     }

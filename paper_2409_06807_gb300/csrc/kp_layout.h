@@ -74,11 +74,9 @@ struct KCtl {
   // started by a lane that had already run a key in the same pass
   unsigned long long tot_batches;
   unsigned long long tot_refills;
-  // barrier words on their own 128-byte line
-  uint32_t bar_count;
+  // grid barrier word (top bit: phase) on its own 128-byte line
+  uint32_t bar;
   uint32_t pad1[31];
-  uint32_t bar_gen;
-  uint32_t pad2[31];
   // never set: target of the bounded-wait self test
   uint32_t never_set;
   uint32_t pad3[31];
@@ -276,7 +274,7 @@ struct KServerDev {
   uint32_t done_seq;   // completion records published
   uint32_t pad[30];
   uint32_t team_slot[KS_MAX_TEAMS];
-  uint32_t team_bar[KS_MAX_TEAMS][64];  // [0] count, [32] generation
+  uint32_t team_bar[KS_MAX_TEAMS][32];  // [0] barrier word, one 128-byte line a team
 };
 
 struct KServerArgs {

@@ -1077,7 +1077,7 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParam
     return;
   }
   if (!stage_boxes(P, reinterpret_cast<float4*>(smem), sh)) return;
-  const Team T{(int)blockIdx.x, (int)gridDim.x, &ctl->bar_count, &ctl->bar_gen};
+  const Team T{(int)blockIdx.x, (int)gridDim.x, &ctl->bar};
   run_loop<SYS, LOG>(P, T, smem, sh, max_iters, max_ns);
 }
 
@@ -1143,7 +1143,7 @@ __global__ void kp_reset_kernel(KParams P, RootState root) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.R; r += gridDim.x * blockDim.x)
     P.thr[r] = 1ull << 32;
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  P.ctl->bar_count = 0;
+  P.ctl->bar = 0;
   init_root<SYS>(P, root);
 }
 

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_server_kernel(KSer
   if (team >= n_teams) return;  // blocks past the last full team stay idle
   KServerDev* dev = A.dev;
   KCtl* sctl = &dev->sctl;
-  const Team T{b, A.team_blocks, &dev->team_bar[team][0], &dev->team_bar[team][32]};
+  const Team T{b, A.team_blocks, &dev->team_bar[team][0]};
   KParams& P = *reinterpret_cast<KParams*>(smem);
   unsigned char* blob = smem + ((sizeof(KParams) + 127) & ~(size_t)127);
   for (;;) {
