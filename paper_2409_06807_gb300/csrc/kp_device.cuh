@@ -65,7 +65,11 @@ struct Team {
 // reset and no second word.  A block waits until the top bit differs from
 // the one its own arrival saw.  The low bits start at 0 (the reset and
 // import paths write the word) and stay below 2^31 while any arrival is
-// out, so the bit cannot flip early.  Every wait is bounded by 'limit_ns'
+// out, so the bit cannot flip early.  Ordering: each arrival is a fence then
+// a relaxed add, so the adds form one release sequence; the wait's acquire
+// load that sees the flip synchronises with every block's fence, and the
+// closing __syncthreads carries that to the block's other threads (a fence
+// after the wait measured slower and adds nothing).  Every wait is bounded by 'limit_ns'
 // of device time; on expiry the block records KP_ERR_TIMEOUT and all blocks
 // leave at their next barrier (the word is then left mid-phase: a launch
 // that timed out poisons its context).  Returns false when the launch must
@@ -93,7 +97,6 @@ __device__ __forceinline__ bool team_sync(const Team& T, KCtl* ctl, uint64_t lim
         }
       }
     }
-    __threadfence();
     if (ok && *((volatile int*)&ctl->err) != 0) ok = 0;
     s_ok = ok;
     if (watch) s_watch = *((volatile const int*)watch);
