@@ -238,8 +238,9 @@ template <>
 struct System<KP_SYS_DI> {
   static constexpr int D = 6, N = 3;
   // finished lanes a warp waits for before it finalises and refills them
-  // (measured on the GB300: cheap steps favour large refill groups)
-  static constexpr int REFILL_MIN = 28;
+  // (measured on the GB300: cheap steps favour large refill groups; for
+  // Euler steps the whole warp, 32)
+  static constexpr int REFILL_MIN = 32;
   __device__ __forceinline__ static void step(float* x, const float* u, float h,
                                               const KParams&) {
 #pragma unroll
@@ -293,7 +294,7 @@ __device__ __forceinline__ void rk4_step(float* x, float h, float h6, F field) {
 template <>
 struct System<KP_SYS_DUBINS> {
   static constexpr int D = 6, N = 3;
-  static constexpr int REFILL_MIN = 20;
+  static constexpr int REFILL_MIN = 16;
   __device__ __forceinline__ static void f(const float* x, const float* u, float* dx) {
     float sp, cp, st, ct;
     sincos_reduced(x[3], &sp, &cp);
@@ -317,7 +318,7 @@ struct System<KP_SYS_DUBINS> {
 template <>
 struct System<KP_SYS_QUAD> {
   static constexpr int D = 12, N = 4;
-  static constexpr int REFILL_MIN = 8;
+  static constexpr int REFILL_MIN = 12;
   __device__ __forceinline__ static void f(const float* x, const float* u, const KParams& P,
                                            float* dx) {
     // phys: m g l c Ixx Iyy Izz; recip: 1/m 1/Ixx 1/Iyy 1/Izz

@@ -430,26 +430,29 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
   int pool_next = gw * b0 < S ? gw * b0 : S;
   int pool_end = pool_next + b0 < S ? pool_next + b0 : S;
   bool exhausted = S <= 0;
-  // bound on the phase's device time, checked warp-uniformly
+  // bound on the phase's device time, checked warp-uniformly at every
+  // refill (a sample runs at most 255 steps, so refills are at most 255
+  // iterations apart)
   const uint64_t t_phase = global_ns();
-  uint32_t guard = 0;
 
   for (;;) {
-    if ((++guard & 1023u) == 0) {
-      const uint64_t now = __shfl_sync(FULL, global_ns(), 0);
-      if (now - t_phase > P.wait_ns) {
-        if (lane == 0) raise_error(P.ctl, KP_DEV_ERR_TIMEOUT, 30);
-        break;
-      }
-    }
     // finished lanes are finalised together: REFILL_MIN of them while keys
     // remain (they are refilled at once), and once the pass's keys are all
     // handed out, only when every lane has finished, so that the warp's
     // last samples cost one finalise instead of one per finishing step
     const uint32_t m_free = __ballot_sync(FULL, key < 0 || done);
     if (exhausted ? m_free == FULL : __popc(m_free) >= Sys::REFILL_MIN) {
+      const uint64_t now = __shfl_sync(FULL, global_ns(), 0);
+      if (now - t_phase > P.wait_ns) {
+        if (lane == 0) raise_error(P.ctl, KP_DEV_ERR_TIMEOUT, 30);
+        break;
+      }
       // ---- finalise the lanes that finished -------------------------------
       if (key >= 0 && done) {
+        // steps run, and hull tests (every step but one that left the
+        // state box)
+        n_steps += (uint32_t)i;
+        n_hull += (uint32_t)(fail < 0 ? i - 1 : i);
         int r, s;
         bin_state<SYS>(x, P, &r, &s, sblob);
         const bool valid = fail == 0;
@@ -500,7 +503,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
           P.log.k[key] = k;
 #pragma unroll
           for (int d = 0; d < 4; ++d) P.log.uraw[4 * (size_t)key + d] = wr[d];
-          P.log.fail_step[key] = fail;
+          P.log.fail_step[key] = fail < 0 ? -fail : fail;
           P.log.region[key] = r;
           P.log.sub[key] = s;
 #pragma unroll
@@ -561,10 +564,9 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
       const float px = x[0], py = x[1], pz = x[2];
       Sys::step(x, u, P.dt, P);
       ++i;
-      ++n_steps;
-      bool ok = in_state_box<D>(x, P);
-      if (ok) {
-        ++n_hull;
+      const bool inbox = in_state_box<D>(x, P);
+      bool ok = inbox;
+      if (inbox) {
         // hull of the step; + 0.0f turns a -0 into +0 for the box test
         ok = !hull_hits_grid(P, sbox, sstart, sids, sclear, fminf(px, x[0]) + 0.0f,
                              fminf(py, x[1]) + 0.0f, fminf(pz, x[2]) + 0.0f,
@@ -573,7 +575,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
       }
       if (!ok) {
         done = true;
-        fail = i;
+        fail = inbox ? i : -i;  // negative: the end state left the state box
       } else if (i >= k) {
         done = true;
       }
