@@ -209,12 +209,12 @@ __device__ __forceinline__ float unit24(uint32_t w) {
 // 2pi), 2pi split into C1 = fl32(2pi) and C2 = 2pi - C1 so that k C1 is
 // exact for |k| < 2^11 (|x| below ~1.2e4 rad); then the hardware sin/cos
 // approximations on r in [-pi, pi] (absolute error below 1e-6).
-// k is rounded to the nearest integer (ties to even) by adding and
-// subtracting 1.5 * 2^23: exact for |x / 2pi| < 2^22, and kept on the FP32
-// pipe instead of the slower conversion unit.
+// k is rounded to the nearest integer (ties to even) by adding 1.5 * 2^23
+// to x / 2pi in the same fused multiply-add (one rounding) and subtracting
+// it again: exact for |x / 2pi| < 2^22, and kept on the FP32 pipe instead
+// of the slower conversion unit.
 __device__ __forceinline__ void sincos_reduced(float x, float* s, float* c) {
-  const float k =
-      __fsub_rn(__fadd_rn(__fmul_rn(x, 0.159154943091895336f), 12582912.0f), 12582912.0f);
+  const float k = __fsub_rn(__fmaf_rn(x, 0.159154943091895336f, 12582912.0f), 12582912.0f);
   float r = __fmaf_rn(-k, 6.28318548202514648f, x);
   r = __fmaf_rn(-k, -1.74845560007448838e-07f, r);
   __sincosf(r, s, c);
