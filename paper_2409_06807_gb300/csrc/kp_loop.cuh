@@ -704,6 +704,38 @@ __device__ __forceinline__ void warp_pairwise(double* buf, int n) {
   __syncwarp();
 }
 
+// The same tree for n <= 32 KP_TREE_PER_LANE, in registers: lane l loads
+// the m = max(n / 32, 1) values l m .. l m + m - 1 through load(i), adds
+// the tree's levels of stride below m in place, and the levels of stride m,
+// 2m, ... across lanes by shuffles (left operand the lower index, as in
+// the shared-memory tree).  Every lane gets the sum.  No shared memory and
+// no warp barrier per level.
+constexpr int KP_TREE_PER_LANE = 8;
+
+template <class L>
+__device__ __forceinline__ double warp_tree_sum(int n, L load) {
+  const int lane = (int)(threadIdx.x & 31u);
+  const int m = n >= 32 ? n >> 5 : 1;
+  double v[KP_TREE_PER_LANE];
+#pragma unroll
+  for (int q = 0; q < KP_TREE_PER_LANE; ++q) {
+    const int i = lane * m + q;
+    v[q] = q < m && i < n ? load(i) : 0.0;
+  }
+#pragma unroll
+  for (int st = 1; st < KP_TREE_PER_LANE; st <<= 1)
+#pragma unroll
+    for (int q = 0; q + st < KP_TREE_PER_LANE; q += 2 * st)
+      if (st < m) v[q] = __dadd_rn(v[q], v[q + st]);
+  double sum = v[0];
+  const int lanes = n / m;
+  for (int d = 1; d < lanes; d <<= 1) {
+    const double o = __shfl_down_sync(0xffffffffu, sum, d);
+    if ((lane & (2 * d - 1)) == 0) sum = __dadd_rn(sum, o);
+  }
+  return __shfl_sync(0xffffffffu, sum, 0);
+}
+
 // Phase S (warp 0): Eq. 3-4 for this block's region chunk and its pairwise
 // partial sum (published before the grid barrier that ends the phase).
 // Every operation is an explicitly rounded IEEE double operation in the
@@ -734,8 +766,15 @@ __device__ __forceinline__ void phase_scores(const KParams& P, const Team& T, in
     if (r < P.R) P.score[r] = sc;
     sd[i] = sc;
   }
-  warp_pairwise(sd, ch);
-  if (lane == 0) P.chunk_sum[KP_IDX(P, T.b, KP_MAX_GRID, 16)] = sd[0];
+  double part;
+  if (ch <= 32 * KP_TREE_PER_LANE) {
+    __syncwarp();
+    part = warp_tree_sum(ch, [&](int i) { return sd[i]; });
+  } else {
+    warp_pairwise(sd, ch);
+    part = sd[0];
+  }
+  if (lane == 0) P.chunk_sum[KP_IDX(P, T.b, KP_MAX_GRID, 16)] = part;
   __syncwarp();
 }
 
@@ -747,9 +786,14 @@ __device__ __forceinline__ void phase_thresholds(const KParams& P, const Team& T
                                                  double* sd) {
   if (T.b >= nch) return;
   const int lane = (int)(threadIdx.x & 31u);
-  for (int i = lane; i < nch; i += 32) sd[i] = __ldcg(P.chunk_sum + i);
-  warp_pairwise(sd, nch);
-  const double sum = sd[0];
+  double sum;
+  if (nch <= 32 * KP_TREE_PER_LANE) {
+    sum = warp_tree_sum(nch, [&](int i) { return __ldcg(P.chunk_sum + i); });
+  } else {
+    for (int i = lane; i < nch; i += 32) sd[i] = __ldcg(P.chunk_sum + i);
+    warp_pairwise(sd, nch);
+    sum = sd[0];
+  }
   if (T.b == 0 && lane == 0) P.ctl->score_sum = sum;
   const int ch = P.R_pad / nch;
   const int r0 = T.b * ch;
