@@ -279,8 +279,9 @@ kp_status kp_plan(kp_ctx *ctx, const float *x_init, const kp_goal *goal,
                   const kp_budget *budget, kp_traj *traj);
 
 /* kp_plan in two halves.  kp_plan_async validates its arguments and
- * enqueues the whole query (reset, loop, trajectory extraction) on the
- * context's stream without waiting; traj_capacity is the number of
+ * enqueues the whole query (reset, loop, trajectory extraction: one launch
+ * of the persistent loop kernel) on the context's stream without waiting;
+ * traj_capacity is the number of
  * trajectory rows kp_plan_result will read back.  kp_plan_result waits
  * for that work and fills traj as kp_plan does (KP_ERR_STATE when no
  * kp_plan_async is pending). */
@@ -289,8 +290,10 @@ kp_status kp_plan_async(kp_ctx *ctx, const float *x_init, const kp_goal *goal,
 kp_status kp_plan_result(kp_ctx *ctx, kp_traj *traj);
 
 /* Device duration, in milliseconds, of the most recent launch of the
- * persistent loop kernel, from CUDA events the library records on the
- * context's stream around that launch (waits for it to finish). */
+ * persistent loop kernel (for kp_plan and kp_plan_async that launch also
+ * holds the reset and the trajectory extraction), from CUDA events the
+ * library records on the context's stream around it (waits for it to
+ * finish). */
 kp_status kp_last_launch_ms(kp_ctx *ctx, float *ms);
 
 /* Status snapshot (synchronises the stream). */

@@ -34,7 +34,8 @@ cudaError_t launch_server(const KServerArgs& A, int grid, size_t smem, cudaStrea
 #define KP_DECLARE_SYS(name)                                                                   \
   cudaError_t loop_occupancy_##name(bool log, size_t smem, int* blocks_per_sm);                \
   cudaError_t launch_loop_##name(const KParams& P, int grid, size_t smem, int max_iters,        \
-                                 uint64_t max_ns, bool log, cudaStream_t stream);              \
+                                 uint64_t max_ns, bool log, cudaStream_t stream,               \
+                                 const RootState& root, int mode);                             \
   cudaError_t launch_reset_##name(const KParams& P, const RootState& root, cudaStream_t stream);
 KP_DECLARE_SYS(di)
 KP_DECLARE_SYS(dubins)
@@ -325,17 +326,22 @@ cudaError_t occupancy(int sys, bool log, size_t smem, int* bps) {
   }
 }
 
-cudaError_t launch_loop(kp_ctx* c, const KParams& P, int max_iters, uint64_t max_ns) {
+// mode: KP_LOOP_RESET (Algorithm 1's initialisation from root first) and
+// KP_LOOP_EXTRACT (the root-to-goal chain after the passes), or 0.
+cudaError_t launch_loop(kp_ctx* c, const KParams& P, int max_iters, uint64_t max_ns,
+                        const RootState& root = RootState{}, int mode = 0) {
   const bool log = c->log_on;
   const int g = c->grid[log ? 1 : 0];
   cudaError_t e = cudaEventRecord(c->ev_loop0, c->stream);
   if (e != cudaSuccess) return e;
   switch (c->dims.sys) {
-    case KP_SYS_DI: e = launch_loop_di(P, g, c->smem, max_iters, max_ns, log, c->stream); break;
-    case KP_SYS_DUBINS:
-      e = launch_loop_dubins(P, g, c->smem, max_iters, max_ns, log, c->stream);
+    case KP_SYS_DI:
+      e = launch_loop_di(P, g, c->smem, max_iters, max_ns, log, c->stream, root, mode);
       break;
-    default: e = launch_loop_quad(P, g, c->smem, max_iters, max_ns, log, c->stream);
+    case KP_SYS_DUBINS:
+      e = launch_loop_dubins(P, g, c->smem, max_iters, max_ns, log, c->stream, root, mode);
+      break;
+    default: e = launch_loop_quad(P, g, c->smem, max_iters, max_ns, log, c->stream, root, mode);
   }
   if (e != cudaSuccess) return e;
   e = cudaEventRecord(c->ev_loop1, c->stream);
@@ -804,23 +810,11 @@ kp_status configure_launch(kp_ctx* ctx) {
   return KP_OK;
 }
 
-kp_status clear_tables(kp_ctx* ctx) {
-  const Dims& d = ctx->dims;
-  const Layout& L = ctx->lay;
-  KP_CUDA(cudaMemsetAsync(ctx->arena + L.visited, 0, d.n_sub, ctx->stream));
-  KP_CUDA(cudaMemsetAsync(ctx->arena + L.claim, 0xff, d.n_sub * 4, ctx->stream));
-  KP_CUDA(cudaMemsetAsync(ctx->arena + L.n_valid, 0, (size_t)d.R * 4, ctx->stream));
-  KP_CUDA(cudaMemsetAsync(ctx->arena + L.n_invalid, 0, (size_t)d.R * 4, ctx->stream));
-  KP_CUDA(cudaMemsetAsync(ctx->arena + L.cov, 0, (size_t)d.R * 4, ctx->stream));
-  KP_CUDA(cudaMemsetAsync(ctx->arena + L.avail, 0, (size_t)d.R, ctx->stream));
-  return KP_OK;
-}
-
+// Algorithm 1's initialisation: one launch clears the tables and writes
+// the root (kp_reset_kernel).
 kp_status enqueue_reset(kp_ctx* ctx, const float* x_init) {
   for (int i = 0; i < ctx->dims.D; ++i)
     if (std::isnan(x_init[i])) return fail(ctx, KP_ERR_ARG, "NaN in x_init");
-  kp_status s = clear_tables(ctx);
-  if (s != KP_OK) return s;
   RootState root{};
   for (int i = 0; i < ctx->dims.D; ++i) root.x[i] = x_init[i];
   KParams P = params_now(ctx);
@@ -1092,14 +1086,16 @@ kp_status kp_plan_async(kp_ctx* ctx, const float* x_init, const kp_goal* goal,
   if (ctx->plan_pending) return fail(ctx, KP_ERR_STATE, "kp_plan_result not called");
   s = ensure_pinned(ctx, sizeof(KCtl) + traj_bytes);
   if (s != KP_OK) return s;
+  for (int i = 0; i < ctx->dims.D; ++i)
+    if (std::isnan(x_init[i])) return fail(ctx, KP_ERR_ARG, "NaN in x_init");
   ctx->goal = *goal;
-  s = enqueue_reset(ctx, x_init);
-  if (s != KP_OK) return s;
+  RootState root{};
+  for (int i = 0; i < ctx->dims.D; ++i) root.x[i] = x_init[i];
   KParams P = params_now(ctx);
   const uint64_t max_ns = budget->max_ms > 0.0 ? (uint64_t)(budget->max_ms * 1e6) : 0ull;
-  KP_CUDA(launch_loop(ctx, P, budget->max_iters, max_ns));
-  kp_extract_kernel<<<1, 32, 0, ctx->stream>>>(P);
-  KP_CUDA(cudaGetLastError());
+  // one launch: initialisation, the passes, the chain
+  KP_CUDA(launch_loop(ctx, P, budget->max_iters, max_ns, root, KP_LOOP_RESET | KP_LOOP_EXTRACT));
+  ctx->have_tree = true;
   ctx->plan_pending = true;
   ctx->plan_rows = rows;
   return KP_OK;
@@ -1414,9 +1410,7 @@ kp_status kp_resume(kp_ctx* ctx, const kp_budget* budget, kp_traj* traj) {
   if (s != KP_OK) return s;
   KParams P = params_now(ctx);
   const uint64_t max_ns = budget->max_ms > 0.0 ? (uint64_t)(budget->max_ms * 1e6) : 0ull;
-  KP_CUDA(launch_loop(ctx, P, budget->max_iters, max_ns));
-  kp_extract_kernel<<<1, 32, 0, ctx->stream>>>(P);
-  KP_CUDA(cudaGetLastError());
+  KP_CUDA(launch_loop(ctx, P, budget->max_iters, max_ns, RootState{}, KP_LOOP_EXTRACT));
   ctx->plan_pending = true;
   ctx->plan_rows = rows;
   return kp_plan_result(ctx, traj);
@@ -1883,15 +1877,16 @@ extern "C" kp_status kp_plan_static(const kp_system* sys, const kp_workspace* ws
     switch (d.sys) {
       case KP_SYS_DI:
         ok(launch_reset_di(P, root, stream));
-        ok(launch_loop_di(P, grid, smem, budget->max_iters, max_ns, false, stream));
+        ok(launch_loop_di(P, grid, smem, budget->max_iters, max_ns, false, stream, root, 0));
         break;
       case KP_SYS_DUBINS:
         ok(launch_reset_dubins(P, root, stream));
-        ok(launch_loop_dubins(P, grid, smem, budget->max_iters, max_ns, false, stream));
+        ok(launch_loop_dubins(P, grid, smem, budget->max_iters, max_ns, false, stream, root,
+                              0));
         break;
       default:
         ok(launch_reset_quad(P, root, stream));
-        ok(launch_loop_quad(P, grid, smem, budget->max_iters, max_ns, false, stream));
+        ok(launch_loop_quad(P, grid, smem, budget->max_iters, max_ns, false, stream, root, 0));
     }
   }
   if (e == cudaSuccess) {

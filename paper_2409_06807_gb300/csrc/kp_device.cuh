@@ -75,9 +75,12 @@ struct Team {
 // that timed out poisons its context).  Returns false when the launch must
 // stop.  With 'watch' given, thread 0 also reads that word after the
 // barrier and the block gets its value in *watched (one load per block
-// instead of one per thread on a word every block reads).
+// instead of one per thread on a word every block reads).  With check_err
+// false the wait ignores the control block's error word (the barriers
+// around a launch's own initialisation, which clears that word).
 __device__ __forceinline__ bool team_sync(const Team& T, KCtl* ctl, uint64_t limit_ns, int where,
-                                          const int* watch = nullptr, int* watched = nullptr) {
+                                          const int* watch = nullptr, int* watched = nullptr,
+                                          bool check_err = true) {
   __shared__ int s_ok, s_watch;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -89,7 +92,7 @@ __device__ __forceinline__ bool team_sync(const Team& T, KCtl* ctl, uint64_t lim
     uint32_t spins = 0;
     while ((ld_acquire(T.bar) & 0x80000000u) == seen) {
       if ((++spins & 63u) == 0) {
-        if (*((volatile int*)&ctl->err) != 0) { ok = 0; break; }
+        if (check_err && *((volatile int*)&ctl->err) != 0) { ok = 0; break; }
         if (global_ns() - t0 > limit_ns) {
           raise_error(ctl, KP_DEV_ERR_TIMEOUT, where);
           ok = 0;
@@ -97,7 +100,7 @@ __device__ __forceinline__ bool team_sync(const Team& T, KCtl* ctl, uint64_t lim
         }
       }
     }
-    if (ok && *((volatile int*)&ctl->err) != 0) ok = 0;
+    if (ok && check_err && *((volatile int*)&ctl->err) != 0) ok = 0;
     s_ok = ok;
     if (watch) s_watch = *((volatile const int*)watch);
   }

@@ -22,11 +22,14 @@ cudaError_t KP_CAT(loop_occupancy_, KP_SYS_NAME)(bool log, size_t smem, int* blo
 
 cudaError_t KP_CAT(launch_loop_, KP_SYS_NAME)(const KParams& P, int grid, size_t smem,
                                              int max_iters, uint64_t max_ns, bool log,
-                                             cudaStream_t stream) {
+                                             cudaStream_t stream, const RootState& root,
+                                             int mode) {
   KParams p = P;
   int mi = max_iters;
   uint64_t mn = max_ns;
-  void* args[] = {&p, &mi, &mn};
+  RootState rs = root;
+  int md = mode;
+  void* args[] = {&p, &mi, &mn, &rs, &md};
   const void* f = log ? (const void*)kp_loop_kernel<KP_SYS, true>
                       : (const void*)kp_loop_kernel<KP_SYS, false>;
   return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(KP_BLOCK), args, smem, stream);
@@ -34,10 +37,15 @@ cudaError_t KP_CAT(launch_loop_, KP_SYS_NAME)(const KParams& P, int grid, size_t
 
 cudaError_t KP_CAT(launch_reset_, KP_SYS_NAME)(const KParams& P, const RootState& root,
                                               cudaStream_t stream) {
-  int blocks = (P.R + 255) / 256;
+  // about four 16-byte stores of the claim table per thread, at least one
+  // thread per region
+  const size_t n_sub = (size_t)P.R * (size_t)P.n_sub_per;
+  size_t blocks = (n_sub + 4095) / 4096;
+  const size_t by_region = ((size_t)P.R + 255) / 256;
+  if (blocks < by_region) blocks = by_region;
   if (blocks < 1) blocks = 1;
   if (blocks > 1024) blocks = 1024;
-  kp_reset_kernel<KP_SYS><<<blocks, 256, 0, stream>>>(P, root);
+  kp_reset_kernel<KP_SYS><<<(unsigned)blocks, 256, 0, stream>>>(P, root);
   return cudaGetLastError();
 }
 

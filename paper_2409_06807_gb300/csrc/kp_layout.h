@@ -62,6 +62,7 @@ struct KCtl {
   int32_t n_edges;     // trajectory extraction: edges on the chain
   int32_t work_next;   // next sample key handed out in the expand phase
   uint32_t t_done;     // region chunks whose thresholds are written, this pass
+  uint32_t reset_done; // blocks of the reset launch that finished their clears
   double score_sum;    // sum of Eq. 5 over R_avail, this pass
   // work counters since the last reset (samples, integrator steps run,
   // segment hulls tested against the obstacle set)
@@ -105,6 +106,12 @@ struct KStats {
 };
 
 // x_init of a reset, passed by value.
+// what a loop launch does around its passes
+enum {
+  KP_LOOP_RESET = 1,   // Algorithm 1's initialisation first (tables cleared, root)
+  KP_LOOP_EXTRACT = 2  // the root-to-goal chain written to the trajectory rows after
+};
+
 struct RootState {
   float x[12];
 };

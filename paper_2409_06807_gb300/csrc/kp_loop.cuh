@@ -1108,38 +1108,145 @@ __device__ __forceinline__ bool run_loop(const KParams& P, const Team& T, unsign
   return true;
 }
 
+// n bytes at p set to the 16-byte pattern v, by 16-byte stores (every table
+// slice of the arena starts on 256 bytes and is padded to a multiple of
+// 256, so the last store stays inside the slice).
+__device__ __forceinline__ void fill_slice(void* p, size_t n, uint4 v, size_t tid, size_t nth) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+  const size_t n16 = (n + 15) / 16;
+  for (size_t i = tid; i < n16; i += nth) q[i] = v;
+}
+
+template <int SYS>
+__device__ void init_root(const KParams& P, const RootState& root, bool box_free);
+
+// Whether the root's position lies in no obstacle box (closed boxes, the
+// test the hull check makes with a hull of one point), by the whole block:
+// thread t tests boxes t, t + blockDim.x, ...  Every thread of the block
+// calls it and gets the answer.
+__device__ __forceinline__ bool root_box_free(const KParams& P, const RootState& root) {
+  const float4* gb = reinterpret_cast<const float4*>(P.boxes);
+  const float px = root.x[0], py = root.x[1], pz = root.x[2];
+  bool hit = false;
+  for (int b = (int)threadIdx.x; b < P.n_boxes_pad; b += (int)blockDim.x) {
+    const float4 bl = gb[2 * b], bh = gb[2 * b + 1];
+    hit |= (px <= bh.x) & (bl.x <= px) & (py <= bh.y) & (bl.y <= py) & (pz <= bh.z) &
+           (bl.z <= pz);
+  }
+  return __syncthreads_or(hit) == 0;
+}
+
+// The region and sub-region tables of Algorithm 1's initialisation, cleared
+// by the whole team: visited 0, claims 2^32 - 1, counters 0, R_avail empty,
+// P_accept = 1 as the threshold 2^32.
+__device__ __forceinline__ void clear_tables(const KParams& P, size_t tid, size_t nth) {
+  const size_t R = (size_t)P.R, n_sub = R * (size_t)P.n_sub_per;
+  const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+  fill_slice(P.visited, n_sub, zero, tid, nth);
+  fill_slice(P.claim, n_sub * 4, make_uint4(~0u, ~0u, ~0u, ~0u), tid, nth);
+  fill_slice(P.n_valid, R * 4, zero, tid, nth);
+  fill_slice(P.n_invalid, R * 4, zero, tid, nth);
+  fill_slice(P.cov, R * 4, zero, tid, nth);
+  fill_slice(P.avail, R, zero, tid, nth);
+  fill_slice(P.thr, R * 8, make_uint4(0u, 1u, 0u, 1u), tid, nth);  // 2^32 each
+}
+
+// Algorithm 1's initialisation inside the loop launch: the team clears the
+// tables, then block 0 writes the root (which also clears the control
+// block's error word, so neither barrier here reads it).
+template <int SYS>
+__device__ __forceinline__ bool reset_in_launch(const KParams& P, const Team& T,
+                                                const RootState& root) {
+  clear_tables(P, (size_t)T.b * blockDim.x + threadIdx.x, (size_t)T.nb * blockDim.x);
+  const bool box_free = T.b == 0 ? root_box_free(P, root) : false;
+  if (!team_sync(T, P.ctl, P.wait_ns, 50, nullptr, nullptr, false)) return false;
+  if (T.b == 0 && threadIdx.x == 0) init_root<SYS>(P, root, box_free);
+  return team_sync(T, P.ctl, P.wait_ns, 51, nullptr, nullptr, false);
+}
+
+// Root-to-goal chain into P.traj rows (state 12, control 4, steps), root
+// first; ctl->n_edges its length, -1 without a goal node (rows are written
+// for at most KP_TRAJ_ROWS edges).  Run by every thread of one block:
+// thread 0 walks the chain once from the goal and keeps the node ids in
+// ids[0 .. cap), then the block writes the rows in parallel; a chain longer
+// than cap is written by thread 0 on a second walk.
+template <int SYS>
+__device__ void extract_chain_block(const KParams& P, int* ids, int cap) {
+  constexpr int D = System<SYS>::D, N = System<SYS>::N;
+  KCtl* ctl = P.ctl;
+  __shared__ int s_len;
+  if (threadIdx.x == 0) {
+    const int g = ctl->goal_node;
+    int len = -1;
+    if (g != KP_NO_GOAL && g >= 0 && g < P.t_e) {
+      len = 0;
+      for (int v = g; v > 0 && len <= P.t_e; v = P.parent[v]) {
+        if (len < cap) ids[len] = v;
+        ++len;
+      }
+    }
+    ctl->n_edges = len;
+    s_len = len;
+  }
+  __syncthreads();
+  const int len = s_len;
+  if (len <= 0 || len > KP_TRAJ_ROWS) return;
+  auto write_row = [&](int row, int v) {
+    float* out = P.traj + (size_t)row * 17;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) out[i] = i < D ? P.st[(size_t)i * P.t_e + v] : 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[12 + i] = i < N ? P.ctrl[(size_t)i * P.t_e + v] : 0.0f;
+    out[16] = (float)P.steps[v];
+  };
+  if (len <= cap) {
+    for (int e = (int)threadIdx.x; e < len; e += (int)blockDim.x) write_row(len - 1 - e, ids[e]);
+  } else if (threadIdx.x == 0) {
+    int row = len - 1;
+    for (int v = ctl->goal_node; v > 0 && row >= 0; v = P.parent[v], --row) write_row(row, v);
+  }
+}
+
 #ifndef KP_MIN_BLOCKS
 #define KP_MIN_BLOCKS 1
 #endif
-// Single-query launch: the whole grid is one team.
+// Single-query launch: the whole grid is one team.  mode: KP_LOOP_RESET
+// runs Algorithm 1's initialisation from 'root' first, KP_LOOP_EXTRACT
+// writes the root-to-goal chain after the passes (block 0, the ids kept in
+// the dynamic shared memory the passes no longer use).
 template <int SYS, bool LOG>
-__global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_loop_kernel(KParams P, int max_iters,
-                                                                         uint64_t max_ns) {
+__global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS)
+    kp_loop_kernel(KParams P, int max_iters, uint64_t max_ns, RootState root, int mode) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LoopShared sh;
   KCtl* ctl = P.ctl;
-  if (ctl->state != KP_DEV_RUNNING) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_run = 0;
-    return;
-  }
-  if (!stage_boxes(P, reinterpret_cast<float4*>(smem), sh)) return;
   const Team T{(int)blockIdx.x, (int)gridDim.x, &ctl->bar};
-  run_loop<SYS, LOG>(P, T, smem, sh, max_iters, max_ns);
+  if ((mode & KP_LOOP_RESET) && !reset_in_launch<SYS>(P, T, root)) return;
+  if (ctl->state == KP_DEV_RUNNING) {
+    if (!stage_boxes(P, reinterpret_cast<float4*>(smem), sh)) return;
+    if (!run_loop<SYS, LOG>(P, T, smem, sh, max_iters, max_ns)) return;
+  } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->n_run = 0;
+  }
+  if ((mode & KP_LOOP_EXTRACT) && blockIdx.x == 0) {
+    __syncthreads();
+    extract_chain_block<SYS>(P, reinterpret_cast<int*>(smem),
+                             (int)(((size_t)P.blob_bytes + (size_t)P.sd_bytes) / 4));
+  }
 }
 
-// Root of a query (thread 0): x_init checked (state box, no obstacle box
-// contains it) and binned; tree, decomposition and control block set to
-// Algorithm 1, initialisation.  Thresholds and cleared tables are the caller's.
+// Root of a query (thread 0): x_init checked (state box; box_free: no
+// obstacle box contains it, root_box_free) and binned; tree, decomposition
+// and control block set to Algorithm 1, initialisation.  Thresholds and
+// cleared tables are the caller's.
 template <int SYS>
-__device__ void init_root(const KParams& P, const RootState& root) {
+__device__ void init_root(const KParams& P, const RootState& root, bool box_free) {
   using Sys = System<SYS>;
   constexpr int D = Sys::D;
   KCtl* ctl = P.ctl;
   float x[D];
   for (int i = 0; i < D; ++i) x[i] = root.x[i];
-  const float4* gb = reinterpret_cast<const float4*>(P.boxes);
-  bool ok = in_state_box<D>(x, P) &&
-            !hull_hits_boxes(gb, P.n_boxes_pad, x[0], x[1], x[2], x[0], x[1], x[2]);
+  bool ok = in_state_box<D>(x, P) && box_free;
   ctl->n_run = 0;
   ctl->stop = 0;
   ctl->it_valid = 0;
@@ -1181,16 +1288,27 @@ __device__ void init_root(const KParams& P, const RootState& root) {
   ctl->state = in_goal ? KP_DEV_SOLVED : KP_DEV_RUNNING;
 }
 
-// Algorithm 1, initialisation, on the device (after the host cleared the tables):
-// every thread sets P_accept = 1 (threshold 2^32) for its regions, block 0
-// thread 0 writes the root.
+// Algorithm 1, initialisation, as a launch of its own (kp_reset and the
+// no-allocation entry): every block clears its share of the tables
+// (clear_tables); the last block to finish (a counter taken after a fence)
+// writes the root, so the root's table entries come after every clear.
 template <int SYS>
 __global__ void kp_reset_kernel(KParams P, RootState root) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.R; r += gridDim.x * blockDim.x)
-    P.thr[r] = 1ull << 32;
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  clear_tables(P, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&P.ctl->reset_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  const bool box_free = root_box_free(P, root);
+  if (threadIdx.x != 0) return;
+  __threadfence();
+  P.ctl->reset_done = 0;
   P.ctl->bar = 0;
-  init_root<SYS>(P, root);
+  init_root<SYS>(P, root, box_free);
 }
 
 }  // namespace kp

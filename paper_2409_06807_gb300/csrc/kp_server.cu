@@ -32,21 +32,12 @@ __device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t* p) {
 template <int SYS>
 __device__ __forceinline__ bool reset_query(const KParams& P, const Team& T, const RootState& root,
                                             KCtl* sctl, uint64_t wait_ns) {
-  const int tid = T.b * blockDim.x + threadIdx.x, nth = T.nb * blockDim.x;
-  const size_t n_sub = (size_t)P.R * P.n_sub_per;
-  for (size_t i = tid; i < n_sub; i += nth) {
-    P.visited[i] = 0;
-    P.claim[i] = 0xffffffffu;
-  }
-  for (int r = tid; r < P.R; r += nth) {
-    P.n_valid[r] = 0;
-    P.n_invalid[r] = 0;
-    P.cov[r] = 0;
-    P.avail[r] = 0;
-    P.thr[r] = 1ull << 32;
-  }
+  clear_tables(P, (size_t)T.b * blockDim.x + threadIdx.x, (size_t)T.nb * blockDim.x);
   if (!team_sync(T, sctl, wait_ns, 40)) return false;
-  if (T.b == 0 && threadIdx.x == 0) init_root<SYS>(P, root);
+  if (T.b == 0) {
+    const bool box_free = root_box_free(P, root);
+    if (threadIdx.x == 0) init_root<SYS>(P, root, box_free);
+  }
   return team_sync(T, sctl, wait_ns, 41);
 }
 
