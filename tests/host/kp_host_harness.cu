@@ -17,7 +17,8 @@ cudaError_t server_occupancy(size_t, int*) { return cudaErrorNotSupported; }
 cudaError_t launch_server(const KServerArgs&, int, size_t, cudaStream_t) { return cudaErrorNotSupported; }
 #define KPT_STUB_SYS(name)                                                                       \
   cudaError_t loop_occupancy_##name(bool, size_t, int*) { return cudaErrorNotSupported; }       \
-  cudaError_t launch_loop_##name(const KParams&, int, size_t, int, uint64_t, bool, cudaStream_t) { \
+  cudaError_t launch_loop_##name(const KParams&, int, size_t, int, uint64_t, bool, cudaStream_t, \
+                                 const RootState&, int) {                                      \
     return cudaErrorNotSupported;                                                              \
   }                                                                                            \
   cudaError_t launch_reset_##name(const KParams&, const RootState&, cudaStream_t) {             \
