@@ -41,27 +41,6 @@ __device__ __forceinline__ bool reset_query(const KParams& P, const Team& T, con
   return team_sync(T, sctl, wait_ns, 41);
 }
 
-// Root-to-goal chain into P.traj rows (state 12, ctrl 4, steps), root first.
-__device__ void extract_chain(const KParams& P, int D, int N) {
-  KCtl* ctl = P.ctl;
-  const int g = ctl->goal_node;
-  if (g == KP_NO_GOAL || g < 0 || g >= P.t_e) {
-    ctl->n_edges = -1;
-    return;
-  }
-  int len = 0;
-  for (int v = g; v > 0 && len <= P.t_e; v = P.parent[v]) ++len;
-  ctl->n_edges = len;
-  if (len > KP_TRAJ_ROWS) return;
-  int row = len - 1;
-  for (int v = g; v > 0 && row >= 0; v = P.parent[v], --row) {
-    float* out = P.traj + (size_t)row * 17;
-    for (int i = 0; i < 12; ++i) out[i] = i < D ? P.st[(size_t)i * P.t_e + v] : 0.0f;
-    for (int i = 0; i < 4; ++i) out[12 + i] = i < N ? P.ctrl[(size_t)i * P.t_e + v] : 0.0f;
-    out[16] = (float)P.steps[v];
-  }
-}
-
 template <int SYS>
 __device__ __forceinline__ bool run_query(const KParams& P, const Team& T, const KQuery* q,
                                           unsigned char* blob, LoopShared& sh, KCtl* sctl,
@@ -141,12 +120,25 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_server_kernel(KSer
       }
       return;
     }
+    if (b == 0) {
+      // the chain by the team's first block (the ids in the blob's shared
+      // memory, which the next query restages after its claim barrier)
+      KCtl* ctl = P.ctl;
+      if (ctl->state == KP_DEV_SOLVED) {
+        int* ids = reinterpret_cast<int*>(blob);
+        const int cap = (int)(((size_t)P.blob_bytes + (size_t)P.sd_bytes) / 4);
+        switch (P.sys) {
+          case KP_SYS_DI: extract_chain_block<KP_SYS_DI>(P, ids, cap); break;
+          case KP_SYS_DUBINS: extract_chain_block<KP_SYS_DUBINS>(P, ids, cap); break;
+          default: extract_chain_block<KP_SYS_QUAD>(P, ids, cap);
+        }
+      } else if (threadIdx.x == 0) {
+        ctl->n_edges = -1;
+      }
+      __syncthreads();
+    }
     if (b == 0 && threadIdx.x == 0) {
       KCtl* ctl = P.ctl;
-      if (ctl->state == KP_DEV_SOLVED)
-        extract_chain(P, P.sys == KP_SYS_QUAD ? 12 : 6, P.sys == KP_SYS_QUAD ? 4 : 3);
-      else
-        ctl->n_edges = -1;
       const uint32_t seq = atomicAdd(&dev->done_seq, 1u);
       KDone* d = &A.host->done[seq % KS_RING];
       d->slot = (int32_t)slot;
