@@ -955,7 +955,9 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_all / t_e2e, "unit": "samples/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 3 * per * args.steps,
+        # one launch of the persistent loop kernel per query: the reset,
+        # the passes and the trajectory extraction all run inside it
+        "gpu_launches": per * args.steps,
         "clocks": clk.summary(),
         "wall_s": t_wall,
         **extra,
