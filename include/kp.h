@@ -344,6 +344,16 @@ kp_status kp_set_wait_limit(kp_ctx *ctx, uint64_t ns);
  * the previous shape is kept). */
 kp_status kp_set_grid_limit(kp_ctx *ctx, int32_t max_blocks);
 
+/* Trajectory extraction (no counterpart in the paper: a testing aid).  A
+ * query's root-to-goal chain is written by one block after the passes:
+ * one thread walks the parent links from the goal node once and keeps the
+ * node ids in the shared memory the passes no longer use, then the block
+ * writes the rows; a chain longer than that room is written by the one
+ * thread on a second walk.  This caps the ids kept at max_ids (0 restores
+ * the room), so that tests can send short chains down the second path; the
+ * rows are the same either way.  KP_ERR_ARG if negative. */
+kp_status kp_set_extract_ids(kp_ctx *ctx, int32_t max_ids);
+
 /* Bounds-checked build (no counterpart in the paper: a testing aid).  The
  * library compiled with KP_CHECK defined (paper_2409_06807_gb300/build.py,
  * check=True) checks every array index the loop kernel derives (node ids,

@@ -1378,6 +1378,7 @@ kp_status kp_grow(kp_ctx* ctx, void* dev_arena, size_t arena_bytes, int32_t t_e)
   for (int a = 0; a < 3; ++a) P.bp_last[a] = old.bp_last[a];
   P.nch = old.nch;
   P.sd_bytes = old.sd_bytes;
+  P.extract_cap = old.extract_cap;
   P.mlp_W1 = old.mlp_W1;
   P.mlp_b1 = old.mlp_b1;
   P.mlp_W2 = old.mlp_W2;
@@ -1438,6 +1439,14 @@ kp_status kp_set_wait_limit(kp_ctx* ctx, uint64_t ns) {
   if (s != KP_OK) return s;
   if (ns < 1000) return fail(ctx, KP_ERR_ARG, "wait limit below 1 us");
   ctx->wait_ns = ns;
+  return KP_OK;
+}
+
+kp_status kp_set_extract_ids(kp_ctx* ctx, int32_t max_ids) {
+  kp_status s = check_ctx(ctx);
+  if (s != KP_OK) return s;
+  if (max_ids < 0) return fail(ctx, KP_ERR_ARG, "negative id cap");
+  ctx->P.extract_cap = max_ids;
   return KP_OK;
 }
 

@@ -175,6 +175,7 @@ struct KParams {
   int32_t n_boxes_pad;
   int32_t blob_bytes;
   int32_t sd_bytes;      // score scratch after the blob; the network tile follows
+  int32_t extract_cap;   // chain ids kept in shared memory at most (0: room only)
   int32_t bp_g[3];       // broad-phase cells along x, y, z (1 1 1: every box in one cell)
   int32_t bp_start_off;  // byte offsets inside the blob
   int32_t bp_ids_off;

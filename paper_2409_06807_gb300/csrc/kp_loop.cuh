@@ -1230,8 +1230,9 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS)
   }
   if ((mode & KP_LOOP_EXTRACT) && blockIdx.x == 0) {
     __syncthreads();
-    extract_chain_block<SYS>(P, reinterpret_cast<int*>(smem),
-                             (int)(((size_t)P.blob_bytes + (size_t)P.sd_bytes) / 4));
+    int cap = (int)(((size_t)P.blob_bytes + (size_t)P.sd_bytes) / 4);
+    if (P.extract_cap > 0 && P.extract_cap < cap) cap = P.extract_cap;
+    extract_chain_block<SYS>(P, reinterpret_cast<int*>(smem), cap);
   }
 }
 

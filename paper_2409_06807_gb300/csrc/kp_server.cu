@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(KP_BLOCK, KP_MIN_BLOCKS) kp_server_kernel(KSer
       KCtl* ctl = P.ctl;
       if (ctl->state == KP_DEV_SOLVED) {
         int* ids = reinterpret_cast<int*>(blob);
-        const int cap = (int)(((size_t)P.blob_bytes + (size_t)P.sd_bytes) / 4);
+        int cap = (int)(((size_t)P.blob_bytes + (size_t)P.sd_bytes) / 4);
+        if (P.extract_cap > 0 && P.extract_cap < cap) cap = P.extract_cap;
         switch (P.sys) {
           case KP_SYS_DI: extract_chain_block<KP_SYS_DI>(P, ids, cap); break;
           case KP_SYS_DUBINS: extract_chain_block<KP_SYS_DUBINS>(P, ids, cap); break;

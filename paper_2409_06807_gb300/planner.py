@@ -123,6 +123,7 @@ SIGNATURES = {
     "kp_set_sample_log": (C.c_int, [_vp, C.POINTER(SampleLog)]),
     "kp_set_wait_limit": (C.c_int, [_vp, C.c_uint64]),
     "kp_set_grid_limit": (C.c_int, [_vp, C.c_int32]),
+    "kp_set_extract_ids": (C.c_int, [_vp, C.c_int32]),
     "kp_selftest_wait_timeout": (C.c_int, [_vp]),
     "kp_bounds_checked": (C.c_int32, []),
     "kp_selftest_bounds": (C.c_int, [_vp]),
@@ -534,6 +535,11 @@ class Planner:
     def set_grid_limit(self, max_blocks):
         """Caps the loop launch at max_blocks blocks (0: the resident maximum)."""
         self._check(lib().kp_set_grid_limit(self._ctx, int(max_blocks)), "kp_set_grid_limit")
+
+    def set_extract_ids(self, max_ids):
+        """Caps the chain ids the trajectory extraction keeps in shared
+        memory (0: the room there); longer chains take the one-thread path."""
+        self._check(lib().kp_set_extract_ids(self._ctx, int(max_ids)), "kp_set_extract_ids")
 
     def selftest_bounds(self):
         return lib().kp_selftest_bounds(self._ctx)

@@ -284,6 +284,40 @@ def test_plan_c2_full_size(P, seed):
     _tree_invariants(w, g.export_tree(), sample_edges=300, info=info)
 
 
+def test_trajectory_extraction_both_paths(P):
+    """The root-to-goal chain is written after the passes by one block:
+    one thread walks the parent links once and keeps the node ids in shared
+    memory, then the block writes the rows; a chain longer than that room
+    goes down a one-thread second walk.  The rows equal the chain read from
+    the exported tree, and with the room capped below the chain's length
+    (the second walk) the same query gives the same bits."""
+    w = W.c2(1)
+    g = P.Planner(w)
+    st, traj = g.plan(max_iters=200)
+    assert st == P.OK
+    n = len(traj["steps"])
+    assert n >= 3
+    t = g.export_tree()
+    chain, v = [], g.info()["goal_node"]
+    while v > 0:
+        chain.append(v)
+        v = t["parent"][v]
+    chain = chain[::-1]
+    assert len(chain) == n
+    assert np.array_equal(traj["states"], t["state"][chain])
+    assert np.array_equal(traj["ctrls"], t["ctrl"][chain])
+    assert np.array_equal(traj["steps"], t["steps"][chain])
+    for cap in (1, n - 1, n):
+        g.set_extract_ids(cap)
+        st2, traj2 = g.plan(max_iters=200)
+        assert st2 == P.OK
+        for k in ("states", "ctrls", "steps"):
+            assert np.array_equal(traj2[k], traj[k]), (cap, k)
+    g.set_extract_ids(0)
+    with pytest.raises(P.KpError):
+        g.set_extract_ids(-1)
+
+
 def _tree_invariants(w, t, sample_edges=0, info=None):
     n = t["n_nodes"]
     if info is not None:
