@@ -402,8 +402,7 @@ kp_status kp_selftest_wait_timeout(kp_ctx *ctx);
  *    equal testing every box, as in kp_plan.
  *  - Work is enqueued on cuda_stream (NULL = legacy default stream) and the
  *    call blocks until it is done (it synchronises that stream and copies
- *    to pageable host memory), so it must not be called while that stream
- *    is being captured.  Returns as kp_plan (a replay mismatch of the
+ *    to pageable host memory).  Returns as kp_plan (a replay mismatch of the
  *    sample log cannot occur here: the log is off); error codes carry no
  *    message; KP_ERR_ARG also when no block of the loop kernel can be
  *    resident with this problem's shared memory. */
