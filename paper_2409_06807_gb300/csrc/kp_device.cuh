@@ -466,28 +466,6 @@ __device__ __forceinline__ bool in_state_box(const float* x, const KParams& P) {
   return ok;
 }
 
-// True when the hull [lo, hi] meets any box.  Boxes sit in shared memory as
-// float4 pairs (lo.xyz, hi.xyz), padded to a multiple of 8 with boxes that
-// can never be met.  Every lane reads the same box (broadcast); a lane
-// leaves after the group of 8 in which it found a hit, and the warp leaves
-// when all its lanes have.
-__device__ __forceinline__ bool hull_hits_boxes(const float4* __restrict__ sb, int n_pad,
-                                                float lx, float ly, float lz, float hx,
-                                                float hy, float hz) {
-  for (int b = 0; b < n_pad; b += 8) {
-    bool hit = false;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 bl = sb[2 * (b + q)];
-      const float4 bh = sb[2 * (b + q) + 1];
-      hit |= (lx <= bh.x) & (bl.x <= hx) & (ly <= bh.y) & (bl.y <= hy) & (lz <= bh.z) &
-             (bl.z <= hz);
-    }
-    if (hit) return true;
-  }
-  return false;
-}
-
 // Closed-box overlap of the hull [l, h] with box (bl, bh), on the FP32 add
 // pipe: the boxes meet iff all six differences bh - l and h - bl are >= 0,
 // i.e. iff none has its sign bit set.  Exact for finite or infinite inputs
