@@ -390,6 +390,32 @@ def test_no_obstacles_and_obstacle_swap(P):
     _revalidate(w, traj, w.x_init)
 
 
+def test_consecutive_queries_start_clean(P):
+    """A query's launch clears the tables and writes the root itself: a
+    query planned on a context that just planned other layouts (other trees
+    and obstacles) gives the same bits as on a fresh context.  The context
+    keeps the random key it was created with, so the fresh contexts take
+    that key too."""
+    seq = [W.c2(5), W.c2(6).with_(seed=5), W.c2(7).with_(seed=5)]
+    g = P.Planner(seq[0])
+    used = []
+    for w in seq:
+        g.set_obstacles(w.boxes)
+        g.w = w
+        st, traj = g.plan(max_iters=200)
+        used.append((st, traj, g.info()))
+    for w, (st, traj, info) in zip(seq, used):
+        f = P.Planner(w)
+        st2, traj2 = f.plan(max_iters=200)
+        info2 = f.info()
+        assert st == st2
+        for k in ("states", "ctrls", "steps"):
+            assert np.array_equal(traj[k], traj2[k]), k
+        for k in ("n_nodes", "n_samples", "n_steps", "iteration"):
+            assert info[k] == info2[k], k
+        f.close()
+
+
 def test_budget_iterations(P):
     w = W.c2(0)
     g = P.Planner(w)
