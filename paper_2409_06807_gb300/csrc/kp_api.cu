@@ -46,7 +46,9 @@ KP_DECLARE_SYS(quad)
 // generic kernels
 // ---------------------------------------------------------------------------
 
-// Root-to-goal chain into P.traj rows (state 12, ctrl 4, steps), root first.
+// Root-to-goal chain into P.traj rows (state 12, ctrl 4, steps), root first,
+// as a launch of its own after the no-allocation entry's loop launch (the
+// queries of a context do this inside their loop launch).
 __global__ void kp_extract_kernel(KParams P) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   KCtl* ctl = P.ctl;
