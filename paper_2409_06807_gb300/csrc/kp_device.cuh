@@ -244,6 +244,10 @@ struct System<KP_SYS_DI> {
   // (measured on the GB300: cheap steps favour large refill groups; for
   // Euler steps the whole warp, 32)
   static constexpr int REFILL_MIN = 32;
+  // smallest first key batch of a warp (keys a warp starts a pass with
+  // when the pass is small; measured on the GB300: spreading a small pass
+  // over more warps helps the RK4 systems, not the Euler one)
+  static constexpr int FIRST_BATCH_MIN = 32;
   __device__ __forceinline__ static void step(float* x, const float* u, float h,
                                               const KParams&) {
 #pragma unroll
@@ -298,6 +302,7 @@ template <>
 struct System<KP_SYS_DUBINS> {
   static constexpr int D = 6, N = 3;
   static constexpr int REFILL_MIN = 16;
+  static constexpr int FIRST_BATCH_MIN = 16;
   __device__ __forceinline__ static void f(const float* x, const float* u, float* dx) {
     float sp, cp, st, ct;
     sincos_reduced(x[3], &sp, &cp);
@@ -322,6 +327,7 @@ template <>
 struct System<KP_SYS_QUAD> {
   static constexpr int D = 12, N = 4;
   static constexpr int REFILL_MIN = 12;
+  static constexpr int FIRST_BATCH_MIN = 16;
   __device__ __forceinline__ static void f(const float* x, const float* u, const KParams& P,
                                            float* dx) {
     // phys: m g l c Ixx Iyy Izz; recip: 1/m 1/Ixx 1/Iyy 1/Izz

@@ -425,7 +425,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
   const int n_warps = T.nb * (int)(blockDim.x >> 5);
   const int gw = T.b * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
   int b0 = S / (2 * n_warps);
-  b0 = b0 < 32 ? 32 : (b0 > KP_KEY_BATCH ? KP_KEY_BATCH : b0);
+  b0 = b0 < Sys::FIRST_BATCH_MIN ? Sys::FIRST_BATCH_MIN : (b0 > KP_KEY_BATCH ? KP_KEY_BATCH : b0);
   const int static_end = n_warps * b0 < S ? n_warps * b0 : S;
   int pool_next = gw * b0 < S ? gw * b0 : S;
   int pool_end = pool_next + b0 < S ? pool_next + b0 : S;
