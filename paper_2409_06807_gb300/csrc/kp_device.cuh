@@ -248,6 +248,10 @@ struct System<KP_SYS_DI> {
   // when the pass is small; measured on the GB300: spreading a small pass
   // over more warps helps the RK4 systems, not the Euler one)
   static constexpr int FIRST_BATCH_MIN = 32;
+  // later key batches are the keys left over GUIDED_DIV x the warps (at
+  // most KP_KEY_BATCH): larger divisors hand out smaller batches towards
+  // the end of a pass (measured: 4 helps the quadrotor's long samples)
+  static constexpr int GUIDED_DIV = 2;
   __device__ __forceinline__ static void step(float* x, const float* u, float h,
                                               const KParams&) {
 #pragma unroll
@@ -303,6 +307,7 @@ struct System<KP_SYS_DUBINS> {
   static constexpr int D = 6, N = 3;
   static constexpr int REFILL_MIN = 16;
   static constexpr int FIRST_BATCH_MIN = 16;
+  static constexpr int GUIDED_DIV = 2;
   __device__ __forceinline__ static void f(const float* x, const float* u, float* dx) {
     float sp, cp, st, ct;
     sincos_reduced(x[3], &sp, &cp);
@@ -328,6 +333,7 @@ struct System<KP_SYS_QUAD> {
   static constexpr int D = 12, N = 4;
   static constexpr int REFILL_MIN = 12;
   static constexpr int FIRST_BATCH_MIN = 16;
+  static constexpr int GUIDED_DIV = 4;
   __device__ __forceinline__ static void f(const float* x, const float* u, const KParams& P,
                                            float* dx) {
     // phys: m g l c Ixx Iyy Izz; recip: 1/m 1/Ixx 1/Iyy 1/Izz

@@ -526,7 +526,7 @@ __device__ __forceinline__ void phase_expand(const KParams& P, const Team& T,
           int base = S;
           if (lane == 0 && static_end < S) {
             const int cur = static_end + *((volatile int*)&P.ctl->work_next);
-            int want = (S - cur) / (2 * n_warps);
+            int want = (S - cur) / (Sys::GUIDED_DIV * n_warps);
             want = want < n_idle_now ? n_idle_now : (want > KP_KEY_BATCH ? KP_KEY_BATCH : want);
             base = static_end + atomicAdd(&P.ctl->work_next, want);
             base = base < S ? base : S;
