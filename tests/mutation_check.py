@@ -100,6 +100,12 @@ MUTATIONS = [
      "quadrotor: gyroscopic term sign"),
     ("model.c", "double tau_x = l * (T2 - T4);", "double tau_x = l * (T3 - T1);",
      "quadrotor: roll torque from the pitch rotors"),
+    # the work count behind the roofline (oracle/work.c)
+    ("work.c", "  o->work.steps += 1;", "  o->work.steps += 2;", "work: every step counted twice"),
+    ("work.c", "    if (!(lo <= x1[i] && x1[i] <= hi)) return; /* no hull test */\n", "",
+     "work: a hull counted for a step that left the state box"),
+    ("work.c", "  o->work.samples += 1;", "  o->work.samples += 1 + (o->work.samples == 0);",
+     "work: one sample too many"),
 ]
 
 

@@ -7,6 +7,7 @@ import os
 import pytest
 
 import bench
+from oracle.kpo import Oracle
 from paper_2409_06807_gb300 import workloads as W
 
 
@@ -29,7 +30,6 @@ def test_algorithmic_work_equals_the_oracle_replay_count(make, passes, grid):
     replays seeded passes (oracle/work.c), and costs each under the same
     counting rule; the benchmark's table applied to those counts gives the
     oracle's total exactly."""
-    from oracle.kpo import Oracle
     w = make(3)
     o = Oracle(w)
     o.set_work_grid(grid)
@@ -104,3 +104,4 @@ def test_committed_traffic_records_name_a_source_hash():
         with open(os.path.join(prof, f)) as fh:
             keys = {ln.split(":", 1)[0].strip() for ln in fh if ":" in ln and not ln.startswith("#")}
         assert {"source_hash", "dram_bytes_per_launch"} <= keys, f
+
